@@ -1,0 +1,203 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each check ties the oracle to something other than itself: a brute-force
+sum written independently in Python, closed forms (constant image, box mean,
+window area, step edge of height T), invariants (convexity of the weighted
+mean, range-shift equivariance, transpose/flip symmetry) and the Gaussian
+limit of q_N (Eq. approx2). The gradient is pinned by central differences of
+the oracle's own forward and by the closed form of the linear N = 0 case.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1107_4617_gb300 import synth
+
+GAMMA1 = math.pi / 2.0  # T = 1
+
+
+def brute_force(f, r, gamma, N):
+    """Independent Python restatement of Eq. filter2 on a tiny image:
+    quadruple loop, math.cos ** N, truncated box window."""
+    H, W = f.shape
+    out = np.zeros((H, W))
+    for y in range(H):
+        for x in range(W):
+            num = eta = 0.0
+            for yy in range(max(0, y - r), min(H, y + r + 1)):
+                for xx in range(max(0, x - r), min(W, x + r + 1)):
+                    w = math.cos(gamma * (float(f[yy, xx]) - float(f[y, x]))) ** N
+                    num += w * float(f[yy, xx])
+                    eta += w
+            out[y, x] = num / eta
+    return out
+
+
+def box_sum(a, r):
+    """Truncated box sum via 2-D cumulative sums (a textbook summed-area table)."""
+    H, W = a.shape
+    S = np.zeros((H + 1, W + 1))
+    S[1:, 1:] = np.cumsum(np.cumsum(a, 0), 1)
+    y0 = np.clip(np.arange(H) - r, 0, H)
+    y1 = np.clip(np.arange(H) + r + 1, 0, H)
+    x0 = np.clip(np.arange(W) - r, 0, W)
+    x1 = np.clip(np.arange(W) + r + 1, 0, W)
+    return (S[y1][:, x1] - S[y0][:, x1] - S[y1][:, x0] + S[y0][:, x0])
+
+
+@pytest.mark.parametrize("r", [1, 3, 8])
+@pytest.mark.parametrize("N", [0, 1, 2, 5, 11])
+def test_brute_force_8x8(r, N):
+    f = np.random.default_rng(10 * r + N).uniform(0, 1, (8, 8))
+    got = oracle.bilateral(f, r, GAMMA1, N)
+    ref = brute_force(f, r, GAMMA1, N)
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-13)
+
+
+def test_brute_force_nonsquare_odd():
+    f = synth.rectangles(5, 9, seed=3).astype(np.float64)
+    for r, N in [(2, 3), (4, 8)]:
+        np.testing.assert_allclose(oracle.bilateral(f, r, GAMMA1, N),
+                                   brute_force(f, r, GAMMA1, N), rtol=0, atol=1e-13)
+
+
+def test_constant_image_unchanged():
+    f = np.full((17, 23), 0.37)
+    out, den = oracle.bilateral(f, 5, GAMMA1, 11, return_den=True)
+    np.testing.assert_allclose(out, 0.37, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(den, box_sum(np.ones_like(f), 5), rtol=0, atol=1e-12)
+
+
+def test_window_area_closed_form():
+    """N = 0: every weight is 1, so den is the clipped window area
+    (min(x+r, W-1) - max(x-r, 0) + 1) * (same in y)."""
+    H, W, r = 13, 29, 4
+    f = np.random.default_rng(1).uniform(0, 1, (H, W))
+    _, den = oracle.bilateral(f, r, GAMMA1, 0, return_den=True)
+    ys, xs = np.arange(H), np.arange(W)
+    cy = np.minimum(ys + r, H - 1) - np.maximum(ys - r, 0) + 1
+    cx = np.minimum(xs + r, W - 1) - np.maximum(xs - r, 0) + 1
+    np.testing.assert_array_equal(den, np.outer(cy, cx).astype(np.float64))
+    assert den[H // 2, W // 2] == (2 * r + 1) ** 2
+
+
+@pytest.mark.parametrize("r", [0, 2, 7])
+def test_N0_is_box_mean(r):
+    f = synth.sinusoids(31, 40, seed=2).astype(np.float64)
+    ref = box_sum(f, r) / box_sum(np.ones_like(f), r)
+    np.testing.assert_allclose(oracle.bilateral(f, r, GAMMA1, 0), ref, rtol=0, atol=1e-13)
+
+
+def test_r0_identity():
+    f = synth.rectangles(19, 21, seed=4).astype(np.float64)
+    np.testing.assert_array_equal(oracle.bilateral(f, 0, GAMMA1, 11), f)
+
+
+def test_convexity():
+    """Weights are >= 0 on [-T, T], so out(x) lies between the window's min
+    and max (a kernel is non-negative, Sec. 2)."""
+    from scipy.ndimage import maximum_filter, minimum_filter
+    f = synth.rectangles(40, 33, seed=5).astype(np.float64)
+    for r, N in [(3, 11), (6, 41), (2, 1)]:
+        out = oracle.bilateral(f, r, GAMMA1, N)
+        lo = minimum_filter(f, size=2 * r + 1, mode="nearest")
+        hi = maximum_filter(f, size=2 * r + 1, mode="nearest")
+        assert np.all(out >= lo - 1e-12) and np.all(out <= hi + 1e-12)
+
+
+def test_range_shift_equivariance():
+    f = 0.5 * synth.rectangles(24, 24, seed=6).astype(np.float64)
+    a = oracle.bilateral(f, 4, GAMMA1, 11)
+    b = oracle.bilateral(f + 0.3, 4, GAMMA1, 11)
+    np.testing.assert_allclose(b, a + 0.3, rtol=0, atol=1e-13)
+
+
+def test_transpose_and_flip_symmetry():
+    f = synth.rectangles(18, 27, seed=8).astype(np.float64)
+    out = oracle.bilateral(f, 3, GAMMA1, 5)
+    np.testing.assert_allclose(oracle.bilateral(f.T, 3, GAMMA1, 5), out.T, atol=1e-14, rtol=0)
+    np.testing.assert_allclose(oracle.bilateral(f[::-1, ::-1], 3, GAMMA1, 5),
+                               out[::-1, ::-1], atol=1e-14, rtol=0)
+
+
+def test_step_of_height_T_is_preserved():
+    """Across a step of height exactly T, cos^N(pi/2) = 0 for N >= 1, so no
+    weight crosses the edge and each side is returned unchanged."""
+    f = np.zeros((12, 16))
+    f[:, 8:] = 1.0
+    for N in (1, 2, 11):
+        np.testing.assert_allclose(oracle.bilateral(f, 5, GAMMA1, N), f, rtol=0, atol=1e-15)
+
+
+def test_gaussian_limit_of_kernel():
+    """Eq. approx2: with gamma sqrt(N) = 1/sigma, cos^N(gamma t) ->
+    exp(-t^2 / (2 sigma^2)); the sup error over [-1,1] shrinks as N grows."""
+    sigma = 0.2
+    ts = np.linspace(-1, 1, 401)
+    errs = []
+    for N in (11, 25, 50, 100, 400):
+        g = oracle.gamma_from_sigma(sigma, N)
+        w = np.array([oracle.weight(t, g, N) for t in ts])
+        errs.append(np.max(np.abs(w - np.exp(-ts ** 2 / (2 * sigma ** 2)))))
+    assert all(a > b for a, b in zip(errs, errs[1:])), errs
+    assert errs[-1] < 2e-3
+    # roughly O(1/N): quadrupling N cuts the error by at least 3x
+    assert errs[-2] / errs[-1] > 3.0
+
+
+def test_gaussian_limit_of_filter():
+    f = synth.rectangles(24, 24, seed=9).astype(np.float64)
+    ref = oracle.bilateral_gauss(f, 3, 0.2)
+    errs = []
+    for N in (11, 50, 400):
+        errs.append(np.max(np.abs(oracle.bilateral(f, 3, oracle.gamma_from_sigma(0.2, N), N) - ref)))
+    assert errs[0] > errs[1] > errs[2] and errs[2] < 1e-3
+
+
+def test_order_rule():
+    assert [oracle.resolve_N(s, 1.0) for s in (0.1, 0.15, 0.2, 0.3)] == [41, 19, 11, 5]
+    assert oracle.resolve_N(0.4, 1.0) == 3
+    assert oracle.resolve_N(0.08, 1.0) == 64
+
+
+def _loss(f, g, r, gamma, N):
+    return float(np.sum(g * oracle.bilateral(f, r, gamma, N)))
+
+
+@pytest.mark.parametrize("N", [1, 4, 11])
+def test_gradient_vs_central_differences(N):
+    rng = np.random.default_rng(N)
+    f = 0.2 + 0.6 * rng.uniform(0, 1, (9, 11))
+    g = rng.normal(0, 1, f.shape)
+    r, gamma, h = 2, GAMMA1, 1e-4
+    gf, gg = oracle.bilateral_grad(f, g, r, gamma, N)
+    for (y, x) in [(0, 0), (4, 5), (8, 10), (3, 0), (6, 9)]:
+        fp = f.copy(); fp[y, x] += h
+        fm = f.copy(); fm[y, x] -= h
+        fd = (_loss(fp, g, r, gamma, N) - _loss(fm, g, r, gamma, N)) / (2 * h)
+        assert abs(fd - gf[y, x]) <= 1e-7 * max(1.0, abs(fd)), (y, x, fd, gf[y, x])
+    fd = (_loss(f, g, r, gamma + h, N) - _loss(f, g, r, gamma - h, N)) / (2 * h)
+    assert abs(fd - gg) <= 1e-7 * max(1.0, abs(fd)), (fd, gg)
+
+
+def test_gradient_N0_closed_form():
+    """N = 0 is the linear box mean, whose adjoint is Box[g / count]."""
+    rng = np.random.default_rng(3)
+    f = rng.uniform(0, 1, (10, 13))
+    g = rng.normal(0, 1, f.shape)
+    r = 3
+    gf, gg = oracle.bilateral_grad(f, g, r, GAMMA1, 0)
+    cnt = box_sum(np.ones_like(f), r)
+    np.testing.assert_allclose(gf, box_sum(g / cnt, r), rtol=0, atol=1e-13)
+    assert gg == 0.0
+
+
+def test_points_match_full():
+    f = synth.rectangles(30, 37, seed=11).astype(np.float64)
+    full = oracle.bilateral(f, 4, GAMMA1, 11)
+    idx = np.array([0, 5, 36, 37 * 15 + 20, 30 * 37 - 1])
+    np.testing.assert_array_equal(oracle.bilateral_points(f, 4, GAMMA1, 11, idx), full.ravel()[idx])
+    part = oracle.bilateral(f, 4, GAMMA1, 11, rows=(10, 17))
+    np.testing.assert_array_equal(part, full[10:17])
