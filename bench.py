@@ -1,0 +1,387 @@
+#!/usr/bin/env python3
+"""Throughput of the constant-time raised-cosine bilateral filter on GB300.
+
+Step = one pass of the whole hot path over one synthetic image: the forward
+filter (parameters, load, stack generation, horizontal and vertical moving
+sums, recombination, ratio, saved buffers) followed by the adjoint pass
+(dL/dimage for L = sum(w * out)). Workload: 4096 x 4096 FP32 image
+(16 rectangles + N(0, 0.05^2) noise, clipped to [0, 1]), r = 10,
+sigma_r = 0.1 -> N = 41 (gamma = pi/2, T = 1).
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Prints ONE JSON line (rank 0). With N > 1 (torchrun), each rank filters its
+own image (weak scaling, no collective on the data path); the value is the
+pixels of all ranks over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+H = W = 4096
+R = 10
+SIGMA = 0.1
+T_RANGE = 1.0
+METRIC = "Mpixel/s fwd & fwd+bwd at 4096², r=10, N=40; % roofline; max err vs FP64"
+UNIT = "Mpixel/s"
+# FP32 ALU peak: 152 SMs x 128 FP32 lanes x 2 FLOP per FMA x 2.07 GHz max SM clock.
+SMS, LANES, FMAX_GHZ = 152, 128, 2.070
+FP32_PEAK_TFLOPS = SMS * LANES * 2 * FMAX_GHZ / 1e3
+L2_FLUSH_BYTES = 256 << 20
+
+
+def fwd_flops_per_px(N: int) -> int:
+    """Algorithmic FLOPs of the O(1) method per output pixel: generate the
+    2(N+1) stack values (3 per basis function + 1 multiply by f), two moving
+    sums (2 adds per plane per direction), recombine (~5 per plane incl. a_k),
+    +10 for sincos seed, ratio and store: 17(N+1) + 10."""
+    return 17 * (N + 1) + 10
+
+
+def bwd_flops_per_px(N: int) -> int:
+    """Adjoint: regenerate (4), weight by alpha/beta (2), moving sums (8),
+    adjoint combine (6) and phase partial (6) per basis function, + 30:
+    26(N+1) + 30."""
+    return 26 * (N + 1) + 30
+
+
+def src_hash() -> str:
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1107_4617_gb300", "csrc")
+    for fn in sorted(os.listdir(d)):
+        with open(os.path.join(d, fn), "rb") as fh:
+            h.update(fn.encode())
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def load_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources; else None."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(p) as fh:
+            d = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    e = d.get(kernel)
+    if not e or e.get("src_hash") != src_hash():
+        return None
+    return e.get("bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of SM clock and throttle reasons."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index),
+                 "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(sample_rows: int = 512):
+    """The FP64 oracle (forward + reference gradient) on a band of the same
+    workload, on the host cores. Returns (Mpixel/s, cores, sample text)."""
+    import numpy as np
+
+    import oracle
+    from paper_1107_4617_gb300 import synth
+    f = synth.rectangles(H, W, seed=0)[: sample_rows].astype(np.float64)
+    w = synth.weights((H, W), seed=1)[: sample_rows].astype(np.float64)
+    N = oracle.resolve_N(SIGMA, T_RANGE)
+    g = oracle.gamma_fixed(T_RANGE)
+    t0 = time.perf_counter()
+    oracle.bilateral(f, R, g, N)
+    oracle.bilateral_grad(f, w, R, g, N)
+    dt = time.perf_counter() - t0
+    px = sample_rows * W
+    return px / dt / 1e6, oracle.num_threads(), (
+        f"oracle forward + reference gradient on rows 0..{sample_rows - 1} "
+        f"({sample_rows}x{W} px) of the 4096x4096 r=10 N=41 workload, {dt:.1f} s")
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the FP64 oracle as it stands, on host cores, timed on a
+    bounded band of the workload per step."""
+    if rank != 0:
+        return
+    rows = args.ref_rows
+    for _ in range(args.warmup):
+        cpu_baseline(max(8, rows // 8))
+    vals, t_tot = [], 0.0
+    cores = 0
+    sample = ""
+    for _ in range(args.steps):
+        v, cores, sample = cpu_baseline(rows)
+        vals.append(v)
+        t_tot += rows * W / (v * 1e6)
+    value = args.steps * rows * W / t_tot / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"bilateral cos^N fwd+bwd {H}x{W} r={R} sigma_r={SIGMA} N=41 "
+                               f"(band of {rows} rows per step)", "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--ref-rows", type=int, default=256)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import numpy as np
+    import torch
+
+    import paper_1107_4617_gb300 as bf
+    from paper_1107_4617_gb300 import synth
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    bf.load()
+
+    N = bf.bf_resolve_N(SIGMA, T_RANGE)
+    f_np = synth.rectangles(H, W, seed=rank)
+    w_np = synth.weights((H, W), seed=1 + rank)
+    img = torch.from_numpy(f_np).to(dev)
+    g = torch.from_numpy(w_np).to(dev)
+    out = torch.empty((H, W), dtype=torch.float32, device=dev)
+    saved = torch.empty((3, H, W), dtype=torch.float32, device=dev)
+    gimg = torch.empty((H, W), dtype=torch.float32, device=dev)
+    flush = torch.empty((L2_FLUSH_BYTES // 4,), dtype=torch.float32, device=dev)
+    opts = bf._opts(save=True)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        bf.bf_forward(img, R, SIGMA, T_RANGE, N, out=out, opts=opts, saved=saved, stream=stream)
+        bf.bf_backward(img, out, g, saved, R, SIGMA, T_RANGE, N, grad_img=gimg, opts=opts,
+                       stream=stream)
+
+    launches_per_step = 2  # forward kernel + adjoint kernel
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    sampler = ClockSampler(dev.index if dev.index is not None else 0)
+    sampler.start()
+    time.sleep(0.3)
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    for i in range(args.steps):
+        flush.zero_()  # evict L2 between timed steps (outside the timed interval)
+        ev[i][0].record(stream)
+        bf.bf_forward(img, R, SIGMA, T_RANGE, N, out=out, opts=opts, saved=saved, stream=stream)
+        ev[i][1].record(stream)
+        bf.bf_backward(img, out, g, saved, R, SIGMA, T_RANGE, N, grad_img=gimg, opts=opts,
+                       stream=stream)
+        ev[i][2].record(stream)
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    t_fwd = sum(e[0].elapsed_time(e[1]) for e in ev) / 1e3
+    t_bwd = sum(e[1].elapsed_time(e[2]) for e in ev) / 1e3
+    t_step = t_fwd + t_bwd
+    if dist:
+        tt = torch.tensor([t_step, t_fwd, t_bwd], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_step, t_fwd, t_bwd = [float(x) for x in tt.cpu()]
+    px = H * W
+    value = world * px * args.steps / t_step / 1e6
+    fwd_value = world * px * args.steps / t_fwd / 1e6
+
+    # forward-only at N = 40 (even order, DC term), reported beside N = 41
+    e40 = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    bf.bf_forward(img, R, SIGMA, T_RANGE, 40, out=out, opts=bf._opts(), stream=stream)
+    t40 = 0.0
+    for _ in range(max(3, args.steps // 2)):
+        flush.zero_()
+        e40[0].record(stream)
+        bf.bf_forward(img, R, SIGMA, T_RANGE, 40, out=out, opts=bf._opts(), stream=stream)
+        e40[1].record(stream)
+        torch.cuda.synchronize(dev)
+        t40 += e40[0].elapsed_time(e40[1]) / 1e3
+    fwd40_value = px * max(3, args.steps // 2) / t40 / 1e6
+
+    # end to end through the C ABI from pinned host buffers
+    h_img = torch.from_numpy(f_np).pin_memory()
+    h_g = torch.from_numpy(w_np).pin_memory()
+    h_out = torch.empty((H, W), dtype=torch.float32).pin_memory()
+    h_gimg = torch.empty((H, W), dtype=torch.float32).pin_memory()
+    e2e_steps = max(3, args.steps // 2)
+
+    def e2e_step():
+        img.copy_(h_img, non_blocking=True)
+        g.copy_(h_g, non_blocking=True)
+        step()
+        h_out.copy_(out, non_blocking=True)
+        h_gimg.copy_(gimg, non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ea.record(stream)
+    for _ in range(e2e_steps):
+        e2e_step()
+    eb.record(stream)
+    torch.cuda.synchronize(dev)
+    t_e2e = ea.elapsed_time(eb) / 1e3
+    if dist:
+        tt = torch.tensor([t_e2e], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_e2e = float(tt.item())
+    e2e_value = world * px * e2e_steps / t_e2e / 1e6
+
+    # accuracy vs the FP64 oracle on sampled pixels (reported, not timed)
+    err = None
+    if rank == 0:
+        import oracle
+        bf.bf_forward(img, R, SIGMA, T_RANGE, N, out=out, opts=bf._opts(), stream=stream)
+        torch.cuda.synchronize(dev)
+        rng = np.random.default_rng(123)
+        idx = rng.integers(0, px, 512)
+        ref = oracle.bilateral_points(f_np.astype(np.float64), R, oracle.gamma_fixed(T_RANGE), N, idx)
+        got = out.cpu().numpy().ravel()[idx].astype(np.float64)
+        rel = np.abs(got - ref) / np.maximum(np.abs(ref), 1e-2 * T_RANGE)
+        err = {"max_rel": float(rel.max()), "mean_rel": float(rel.mean()),
+               "max_abs": float(np.abs(got - ref).max()), "samples": int(idx.size)}
+
+    # roofline of the dominant kernel
+    per_launch_fwd = t_fwd / args.steps
+    per_launch_bwd = t_bwd / args.steps
+    if t_bwd >= t_fwd:
+        kname, flops, dur = "bf_bwd_strip_kernel", bwd_flops_per_px(N) * px, per_launch_bwd
+    else:
+        kname, flops, dur = "bf_fwd_strip_kernel", fwd_flops_per_px(N) * px, per_launch_fwd
+    achieved = flops / dur / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": load_traffic(kname),
+                "kernel": kname,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz",
+                "fwd": {"tflops": fwd_flops_per_px(N) * px / per_launch_fwd / 1e12,
+                        "frac": fwd_flops_per_px(N) * px / per_launch_fwd / 1e12 / FP32_PEAK_TFLOPS,
+                        "ms": per_launch_fwd * 1e3},
+                "bwd": {"tflops": bwd_flops_per_px(N) * px / per_launch_bwd / 1e12,
+                        "frac": bwd_flops_per_px(N) * px / per_launch_bwd / 1e12 / FP32_PEAK_TFLOPS,
+                        "ms": per_launch_bwd * 1e3}}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, cores, sample = cpu_baseline()
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_step / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"bilateral cos^N fwd+bwd {H}x{W} r={R} sigma_r={SIGMA} N={N} "
+                                   f"T={T_RANGE}, rectangles+noise",
+                       "H": H, "W": W, "r": R, "N": N, "images_per_rank": 1,
+                       "l2": "flushed between timed steps (256 MiB write)"},
+            "fwd_mpx_s": fwd_value, "fwd_n40_mpx_s": fwd40_value,
+            "clocks": clocks,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * px * 4,
+                    "d2h_bytes_per_step": 2 * px * 4},
+            "gpu_launches": launches_per_step * args.steps,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "max_err_vs_fp64": err,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

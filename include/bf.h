@@ -1,0 +1,192 @@
+/*
+ * bf.h -- C ABI of the constant-time raised-cosine bilateral filter on one
+ * NVIDIA GB300 (sm_103a).
+ *
+ * The filter is Eq. "filter2" of Sec. 2 (bilateral filter) with a box spatial
+ * kernel over the square window |y - x|_inf <= r and the range kernel
+ * q_N(t) = cos^N(gamma t) of Sec. 3, gamma = pi / (2T). Because q_N is
+ * shiftable (Eq. "def") with N+1 basis functions, Algorithm 2 with M = 1
+ * turns the filter into moving sums (the Sum(F, x, T) of Sec. 2) of a stack of
+ * 2(N+1) pointwise transforms of the image:
+ *
+ *   cos^N(gamma (s - t)) = sum_k a_k [cos(k gamma s) cos(k gamma t)
+ *                                     + sin(k gamma s) sin(k gamma t)],
+ *   k = N, N-2, ..., N mod 2;  a_k = 2^(1-N) C(N, (N-k)/2) (k > 0),
+ *   a_0 = 2^(-N) C(N, N/2),
+ *   num(x) = sum_k a_k [C_k(x) Box(C_k f)(x) + S_k(x) Box(S_k f)(x)],
+ *   den(x) = sum_k a_k [C_k(x) Box(C_k)(x)   + S_k(x) Box(S_k)(x)],
+ *   out(x) = num(x) / den(x),   C_k = cos(k gamma f), S_k = sin(k gamma f).
+ *
+ * Border: the window is truncated to the image (sums run over in-image
+ * pixels only).
+ *
+ * Conventions shared by every call below:
+ *  - Image pointers are DEVICE pointers to row-major H x W arrays with row
+ *    pitch W elements, unless the name says _host. The caller owns every
+ *    buffer; no call allocates device memory.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream). Calls are
+ *    asynchronous on it and never synchronise the host.
+ *  - Argument checks run before any launch; on a failed check nothing is
+ *    written and the status is returned. A CUDA launch or copy error returns
+ *    BF_ERR_CUDA and its cudaError_t code is kept per host thread for
+ *    bf_last_cuda_error().
+ *  - Precondition (not checked on the hot path): max f - min f <= T. Inside
+ *    it every weight is >= 0 and den >= 1. Outside it the result is still the
+ *    exact cos^N filter, but den may approach or cross 0.
+ *  - Thread safety: all state lives in the arguments; calls from several host
+ *    threads on several streams may run concurrently.
+ */
+#ifndef BF_H_
+#define BF_H_
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Largest order N accepted (33 harmonics). */
+#define BF_N_MAX 64
+/* Largest spatial half-width r accepted (window up to 129 x 129). */
+#define BF_R_MAX 64
+
+typedef enum {
+    BF_OK = 0,
+    BF_ERR_INVALID_ARG = 1,  /* a size, pointer or parameter is out of range */
+    BF_ERR_UNSUPPORTED = 2,  /* valid request outside what is built (N > BF_N_MAX, r > BF_R_MAX) */
+    BF_ERR_CUDA = 3,         /* a CUDA runtime call failed; see bf_last_cuda_error */
+    BF_ERR_TIMEOUT = 4,      /* a bounded device wait ran out */
+    BF_ERR_INTERNAL = 5,
+    BF_ERR_NOMEM = 6         /* a caller-supplied buffer is too small */
+} bf_status;
+
+typedef enum { BF_F32 = 0, BF_BF16 = 1 } bf_dtype;
+
+typedef enum {
+    /* gamma = pi / (2T): q_N of Sec. 3 exactly. sigma_r only picks N, so
+       dL/dsigma_r is 0. */
+    BF_GAMMA_FIXED = 0,
+    /* gamma = 1 / (sigma_r sqrt(N)): the Gaussian limit (Eq. approx2) then has
+       variance sigma_r^2 exactly (the variance control of Sec. 3); N is
+       frozen by the rule, and dL/dsigma_r = -(gamma / sigma_r) dL/dgamma. */
+    BF_GAMMA_FROM_SIGMA = 1
+} bf_gamma_mode;
+
+typedef struct {
+    int kahan;            /* 1: Kahan-compensated vertical running sums */
+    int gamma_mode;       /* bf_gamma_mode */
+    int in_dtype;         /* bf_dtype of img (output is always FP32) */
+    int save_for_backward;/* 1: bf_forward fills `saved` (also implied by saved != NULL) */
+    int tile_h;           /* rows per band; 0 = built-in choice */
+    int tile_w;           /* threads per strip (multiple of 32, > 2r); 0 = built-in */
+} bf_opts;
+
+/* One image of a batch (bf_batch). img/out/den are device pointers. */
+typedef struct {
+    const void* img;      /* H x W, dtype opts->in_dtype */
+    float* out;           /* H x W */
+    int H, W;
+    int r;                /* spatial half-width, 0..BF_R_MAX */
+    int N;                /* order; <= 0 derives it from sigma_r (bf_resolve_N) */
+    float sigma_r;
+    float T;              /* range bound, > 0 */
+} bf_desc;
+
+/* Fills opts with the defaults (no Kahan, fixed gamma, FP32 input). */
+void bf_default_opts(bf_opts* opts);
+
+/* Order rule: N = ceil(1 / (gamma sigma_r)^2) with gamma = pi/(2T), from the
+   Gaussian-approximation theorem (Eq. approx2: cos^N(gamma t) ~
+   exp(-N gamma^2 t^2 / 2)) and the O(T^2/sigma^2) order threshold at the end
+   of Sec. 3. Returns -1 if sigma_r <= 0 or T <= 0. Host only. */
+int bf_resolve_N(float sigma_r, float T);
+
+/* Interpolating coefficients of q_N's shift expansion (Eq. def applied to
+   cos^N): writes a_k for the harmonics k = N mod 2, N mod 2 + 2, ..., N into
+   a[0 .. K-1] (K = N/2 + 1, in that order) in FP64 and returns K; returns -1
+   if N < 0, N > BF_N_MAX or cap < K. Host only, no GPU needed. */
+int bf_coeffs(int N, double* a, int cap);
+
+/* gamma used for (sigma_r, T, N, gamma_mode); N must already be resolved.
+   Returns a negative value on bad arguments. Host only. */
+double bf_gamma(float sigma_r, float T, int N, int gamma_mode);
+
+/* Bytes of the `saved` buffer bf_forward fills for bf_backward:
+   3 * H * W floats (den, d num / d s, d den / d s; Sec. 2 Eq. filter2
+   differentiated with respect to the centre value). */
+size_t bf_saved_bytes(int H, int W);
+
+/*
+ * Forward filter (Algorithm 2 with M = 1, box window, range kernel q_N).
+ *   img     device, H x W, dtype opts->in_dtype (FP32 or BF16).
+ *   r       half-width, 0..BF_R_MAX.   sigma_r > 0 when N <= 0 or in
+ *           BF_GAMMA_FROM_SIGMA mode.   T > 0.   N <= 0: derived from sigma_r.
+ *   out     device, H x W FP32. Must not alias img.
+ *   opts    NULL = defaults.
+ *   saved   NULL, or device buffer of bf_saved_bytes(H, W), written for
+ *           bf_backward.
+ * Errors: BF_ERR_INVALID_ARG (null pointer, H/W < 1, r < 0, T <= 0, bad
+ * sigma_r, bad opts), BF_ERR_UNSUPPORTED (N > BF_N_MAX, r > BF_R_MAX),
+ * BF_ERR_CUDA.
+ */
+bf_status bf_forward(const void* img, int H, int W, int r, float sigma_r, float T, int N,
+                     float* out, const bf_opts* opts, void* saved, void* stream);
+
+/* Workspace bytes bf_backward needs for its dL/dsigma_r reduction. */
+size_t bf_backward_workspace_bytes(int H, int W, int r, const bf_opts* opts);
+
+/*
+ * Adjoint of bf_forward for L with dL/dout = grad_out (derived from Eq.
+ * filter2; the box window is symmetric, so the adjoint is again a moving-sum
+ * pass over a stack recomputed from img, never stored).
+ *   img, out      the forward's input and output (device).
+ *   grad_out      device H x W FP32.
+ *   saved         the forward's saved buffer (device, bf_saved_bytes).
+ *   grad_img      device H x W FP32 output, or NULL.
+ *   grad_sigma    device pointer to ONE float receiving dL/dsigma_r, or NULL
+ *                 (0 in BF_GAMMA_FIXED mode).
+ *   workspace     device, >= bf_backward_workspace_bytes; may be NULL only if
+ *                 grad_sigma is NULL.
+ * Same parameters (r, sigma_r, T, N, opts) as the forward call.
+ */
+bf_status bf_backward(const void* img, const float* out, const float* grad_out,
+                      const void* saved, int H, int W, int r, float sigma_r, float T, int N,
+                      float* grad_img, float* grad_sigma, void* workspace, size_t ws_bytes,
+                      const bf_opts* opts, void* stream);
+
+/* Workspace bytes bf_batch needs for n descriptors (device tile table). */
+size_t bf_batch_workspace_bytes(const bf_desc* descs, int n, const bf_opts* opts);
+
+/*
+ * Filters n images of uneven sizes, each with its own r, sigma_r, N, in ONE
+ * persistent launch: CTAs pull tiles from a device work counter over a tile
+ * table held in `workspace`. descs is a HOST array; each image is validated
+ * like bf_forward. Equivalent to bf_batch_prepare followed by
+ * bf_batch_launch.
+ */
+bf_status bf_batch(const bf_desc* descs, int n, const bf_opts* opts, void* workspace,
+                   size_t ws_bytes, void* stream);
+
+/* Validates descs and uploads the tile table into workspace (stream-ordered
+   copy from host memory). */
+bf_status bf_batch_prepare(const bf_desc* descs, int n, const bf_opts* opts, void* workspace,
+                           size_t ws_bytes, void* stream);
+
+/* Launches the persistent batch kernel over a table bf_batch_prepare wrote
+   into workspace: a memset of the work counter and one kernel, nothing
+   else, so it can be captured into a CUDA graph and replayed. opts must
+   carry the same kahan / in_dtype as the prepare call. */
+bf_status bf_batch_launch(void* workspace, size_t ws_bytes, const bf_opts* opts, void* stream);
+
+/* Static message for a status code. */
+const char* bf_status_string(bf_status s);
+
+/* cudaError_t code of the last BF_ERR_CUDA on this host thread (0 if none);
+   returns BF_OK, or BF_ERR_INVALID_ARG if code is NULL. */
+bf_status bf_last_cuda_error(int* code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BF_H_ */

@@ -1,0 +1,342 @@
+"""Constant-time raised-cosine bilateral filter for one NVIDIA GB300 (sm_103a).
+
+Python binding of the C ABI in ``include/bf.h`` (library ``libbf.so`` built
+from ``csrc/``). The functions named ``bf_*`` mirror the C entry points one to
+one and only marshal arguments: torch supplies device memory and the CUDA
+stream, every step of the filter runs in the library's kernels. There is no
+CPU or PyTorch fallback: if the library cannot be loaded, or a tensor is not
+on a CUDA device, the call raises.
+
+``bilateral(f, r, sigma_r, ...)`` wraps forward and adjoint kernels in a
+``torch.autograd.Function`` (gradients with respect to the image and to
+sigma_r).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+__all__ = [
+    "BfError", "BfOpts", "BfDesc", "load", "lib_path",
+    "bf_forward", "bf_backward", "bf_batch", "bf_batch_prepare", "bf_batch_launch",
+    "bf_resolve_N", "bf_coeffs", "bf_gamma", "bf_saved_bytes", "bf_backward_workspace_bytes",
+    "bf_batch_workspace_bytes", "bf_status_string", "bf_last_cuda_error", "bilateral",
+    "GAMMA_FIXED", "GAMMA_FROM_SIGMA", "F32", "BF16", "N_MAX", "R_MAX",
+]
+
+GAMMA_FIXED, GAMMA_FROM_SIGMA = 0, 1
+F32, BF16 = 0, 1
+N_MAX, R_MAX = 64, 64
+
+_lock = threading.Lock()
+_lib = None
+
+
+class BfError(RuntimeError):
+    """A C-ABI call returned a status other than BF_OK."""
+
+    def __init__(self, fn: str, status: int, cuda_code: int = 0):
+        msg = f"{fn}: {_status_string(status)} (status {status})"
+        if cuda_code:
+            msg += f", cudaError {cuda_code}"
+        super().__init__(msg)
+        self.status = status
+        self.cuda_code = cuda_code
+
+
+class BfOpts(ctypes.Structure):
+    _fields_ = [("kahan", ctypes.c_int), ("gamma_mode", ctypes.c_int),
+                ("in_dtype", ctypes.c_int), ("save_for_backward", ctypes.c_int),
+                ("tile_h", ctypes.c_int), ("tile_w", ctypes.c_int)]
+
+
+class BfDesc(ctypes.Structure):
+    _fields_ = [("img", ctypes.c_void_p), ("out", ctypes.c_void_p), ("H", ctypes.c_int),
+                ("W", ctypes.c_int), ("r", ctypes.c_int), ("N", ctypes.c_int),
+                ("sigma_r", ctypes.c_float), ("T", ctypes.c_float)]
+
+
+def lib_path() -> str:
+    from . import build as _b
+    return _b.LIB
+
+
+def load():
+    """Load libbf.so, compiling it first if it is missing or stale."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        from . import build as _b
+        path = _b.LIB
+        if not _b.up_to_date():
+            try:
+                path = _b.build()
+            except Exception as e:  # no silent fallback: the product needs the library
+                raise RuntimeError(f"libbf.so is missing and could not be built: {e}") from e
+        lib = ctypes.CDLL(path)
+        c_int, c_float, c_size, vp = ctypes.c_int, ctypes.c_float, ctypes.c_size_t, ctypes.c_void_p
+        P_opts = ctypes.POINTER(BfOpts)
+        P_desc = ctypes.POINTER(BfDesc)
+        sig = {
+            "bf_default_opts": (None, [P_opts]),
+            "bf_resolve_N": (c_int, [c_float, c_float]),
+            "bf_coeffs": (c_int, [c_int, ctypes.POINTER(ctypes.c_double), c_int]),
+            "bf_gamma": (ctypes.c_double, [c_float, c_float, c_int, c_int]),
+            "bf_saved_bytes": (c_size, [c_int, c_int]),
+            "bf_forward": (c_int, [vp, c_int, c_int, c_int, c_float, c_float, c_int, vp, P_opts,
+                                   vp, vp]),
+            "bf_backward_workspace_bytes": (c_size, [c_int, c_int, c_int, P_opts]),
+            "bf_backward": (c_int, [vp, vp, vp, vp, c_int, c_int, c_int, c_float, c_float, c_int,
+                                    vp, vp, vp, c_size, P_opts, vp]),
+            "bf_batch_workspace_bytes": (c_size, [P_desc, c_int, P_opts]),
+            "bf_batch": (c_int, [P_desc, c_int, P_opts, vp, c_size, vp]),
+            "bf_batch_prepare": (c_int, [P_desc, c_int, P_opts, vp, c_size, vp]),
+            "bf_batch_launch": (c_int, [vp, c_size, P_opts, vp]),
+            "bf_status_string": (ctypes.c_char_p, [c_int]),
+            "bf_last_cuda_error": (c_int, [ctypes.POINTER(c_int)]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _status_string(s: int) -> str:
+    try:
+        return load().bf_status_string(int(s)).decode()
+    except Exception:
+        return "unknown"
+
+
+def bf_status_string(s: int) -> str:
+    return _status_string(s)
+
+
+def bf_last_cuda_error() -> int:
+    code = ctypes.c_int(0)
+    load().bf_last_cuda_error(ctypes.byref(code))
+    return int(code.value)
+
+
+def _check(fn: str, status: int):
+    if status != 0:
+        raise BfError(fn, status, bf_last_cuda_error() if status == 3 else 0)
+
+
+def _opts(kahan=False, gamma_mode=GAMMA_FIXED, in_dtype=F32, save=False, tile_h=0, tile_w=0):
+    o = BfOpts()
+    o.kahan, o.gamma_mode, o.in_dtype = int(bool(kahan)), int(gamma_mode), int(in_dtype)
+    o.save_for_backward, o.tile_h, o.tile_w = int(bool(save)), int(tile_h), int(tile_w)
+    return o
+
+
+def _stream_handle(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(int(stream.cuda_stream))
+
+
+def _dptr(t, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _in_dtype(t):
+    import torch
+    if t.dtype == torch.float32:
+        return F32
+    if t.dtype == torch.bfloat16:
+        return BF16
+    raise ValueError("image must be float32 or bfloat16")
+
+
+# ---- host-only helpers (no GPU needed) -------------------------------------
+
+def bf_resolve_N(sigma_r: float, T: float = 1.0) -> int:
+    return int(load().bf_resolve_N(float(sigma_r), float(T)))
+
+
+def bf_coeffs(N: int):
+    """a_k (FP64) for k = N mod 2, N mod 2 + 2, ..., N."""
+    buf = (ctypes.c_double * 64)()
+    K = load().bf_coeffs(int(N), buf, 64)
+    if K < 0:
+        raise ValueError(f"bf_coeffs: invalid N={N}")
+    return [buf[i] for i in range(K)]
+
+
+def bf_gamma(sigma_r: float, T: float, N: int, gamma_mode: int = GAMMA_FIXED) -> float:
+    return float(load().bf_gamma(float(sigma_r), float(T), int(N), int(gamma_mode)))
+
+
+def bf_saved_bytes(H: int, W: int) -> int:
+    return int(load().bf_saved_bytes(int(H), int(W)))
+
+
+def bf_backward_workspace_bytes(H: int, W: int, r: int, opts: BfOpts | None = None) -> int:
+    return int(load().bf_backward_workspace_bytes(int(H), int(W), int(r),
+                                                  ctypes.byref(opts) if opts else None))
+
+
+def bf_batch_workspace_bytes(descs, opts: BfOpts | None = None) -> int:
+    arr = (BfDesc * len(descs))(*descs)
+    return int(load().bf_batch_workspace_bytes(arr, len(descs), ctypes.byref(opts) if opts else None))
+
+
+# ---- device entry points ----------------------------------------------------
+
+def bf_forward(img, r: int, sigma_r: float, T: float = 1.0, N: int = 0, out=None,
+               opts: BfOpts | None = None, saved=None, stream=None):
+    """Forward filter of a 2-D CUDA tensor (float32 or bfloat16) -> float32."""
+    import torch
+    if img.dim() != 2:
+        raise ValueError("img must be 2-D (H, W)")
+    H, W = img.shape
+    if opts is None:
+        opts = _opts(in_dtype=_in_dtype(img))
+    elif opts.in_dtype != _in_dtype(img):
+        raise ValueError("opts.in_dtype does not match img.dtype")
+    if out is None:
+        out = torch.empty((H, W), dtype=torch.float32, device=img.device)
+    st = load().bf_forward(_dptr(img, "img"), H, W, int(r), float(sigma_r), float(T), int(N),
+                           _dptr(out, "out"), ctypes.byref(opts),
+                           _dptr(saved, "saved") if saved is not None else None,
+                           _stream_handle(stream))
+    _check("bf_forward", st)
+    return out
+
+
+def bf_backward(img, out, grad_out, saved, r: int, sigma_r: float, T: float = 1.0, N: int = 0,
+                grad_img=None, grad_sigma=None, workspace=None, opts: BfOpts | None = None,
+                stream=None):
+    """Adjoint pass; writes grad_img (H, W) and/or grad_sigma (1,) if given."""
+    H, W = img.shape
+    if opts is None:
+        opts = _opts(in_dtype=_in_dtype(img))
+    ws_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    st = load().bf_backward(_dptr(img, "img"), _dptr(out, "out"), _dptr(grad_out, "grad_out"),
+                            _dptr(saved, "saved"), H, W, int(r), float(sigma_r), float(T), int(N),
+                            _dptr(grad_img, "grad_img") if grad_img is not None else None,
+                            _dptr(grad_sigma, "grad_sigma") if grad_sigma is not None else None,
+                            _dptr(workspace, "workspace") if workspace is not None else None,
+                            ws_bytes, ctypes.byref(opts), _stream_handle(stream))
+    _check("bf_backward", st)
+
+
+def make_descs(imgs, outs, rs, sigmas, T=1.0, Ns=None):
+    descs = []
+    for i, (im, o) in enumerate(zip(imgs, outs)):
+        d = BfDesc()
+        d.img, d.out = _dptr(im, "img").value, _dptr(o, "out").value
+        d.H, d.W = int(im.shape[0]), int(im.shape[1])
+        d.r, d.N = int(rs[i]), int(Ns[i]) if Ns is not None else 0
+        d.sigma_r, d.T = float(sigmas[i]), float(T)
+        descs.append(d)
+    return descs
+
+
+def bf_batch_prepare(descs, workspace, opts: BfOpts | None = None, stream=None):
+    arr = (BfDesc * len(descs))(*descs)
+    ws_bytes = workspace.numel() * workspace.element_size()
+    st = load().bf_batch_prepare(arr, len(descs), ctypes.byref(opts) if opts else None,
+                                 _dptr(workspace, "workspace"), ws_bytes, _stream_handle(stream))
+    _check("bf_batch_prepare", st)
+
+
+def bf_batch_launch(workspace, opts: BfOpts | None = None, stream=None):
+    ws_bytes = workspace.numel() * workspace.element_size()
+    st = load().bf_batch_launch(_dptr(workspace, "workspace"), ws_bytes,
+                                ctypes.byref(opts) if opts else None, _stream_handle(stream))
+    _check("bf_batch_launch", st)
+
+
+def bf_batch(descs, workspace, opts: BfOpts | None = None, stream=None):
+    arr = (BfDesc * len(descs))(*descs)
+    ws_bytes = workspace.numel() * workspace.element_size()
+    st = load().bf_batch(arr, len(descs), ctypes.byref(opts) if opts else None,
+                         _dptr(workspace, "workspace"), ws_bytes, _stream_handle(stream))
+    _check("bf_batch", st)
+
+
+# ---- autograd ----------------------------------------------------------------
+
+def _make_function():
+    import torch
+
+    class BilateralCosN(torch.autograd.Function):
+        """out = bilateral(f) with range kernel cos^N; differentiable in f and
+        sigma_r (a 0-d tensor). Forward saves den and the centre derivatives;
+        the adjoint kernel recomputes the stack from f."""
+
+        @staticmethod
+        def forward(ctx, f, sigma_r, r, T, N, kahan, gamma_mode):
+            s = float(sigma_r)
+            if N <= 0:
+                N = bf_resolve_N(s, T)
+            squeeze = f.dim() == 2
+            fb = f.unsqueeze(0) if squeeze else f
+            fb = fb.contiguous()
+            B, H, W = fb.shape
+            opts = _opts(kahan=kahan, gamma_mode=gamma_mode, in_dtype=_in_dtype(fb), save=True)
+            out = torch.empty((B, H, W), dtype=torch.float32, device=f.device)
+            saved = torch.empty((B, 3, H, W), dtype=torch.float32, device=f.device)
+            for b in range(B):
+                bf_forward(fb[b], r, s, T, N, out=out[b], opts=opts, saved=saved[b])
+            ctx.save_for_backward(fb, out, saved)
+            ctx.cfg = (r, s, T, N, kahan, gamma_mode, squeeze)
+            return out[0] if squeeze else out
+
+        @staticmethod
+        def backward(ctx, g):
+            fb, out, saved = ctx.saved_tensors
+            r, s, T, N, kahan, gamma_mode, squeeze = ctx.cfg
+            g = g.unsqueeze(0) if squeeze else g
+            g = g.contiguous().float()
+            B, H, W = fb.shape
+            opts = _opts(kahan=kahan, gamma_mode=gamma_mode, in_dtype=_in_dtype(fb))
+            need_f = ctx.needs_input_grad[0]
+            need_s = ctx.needs_input_grad[1]
+            gf = torch.empty((B, H, W), dtype=torch.float32, device=fb.device) if need_f else None
+            gs = torch.zeros((B,), dtype=torch.float32, device=fb.device) if need_s else None
+            ws = None
+            if need_s:
+                nb = bf_backward_workspace_bytes(H, W, r, opts)
+                ws = torch.empty((max(1, nb // 4),), dtype=torch.float32, device=fb.device)
+            for b in range(B):
+                bf_backward(fb[b], out[b], g[b], saved[b], r, s, T, N,
+                            grad_img=gf[b] if need_f else None,
+                            grad_sigma=gs[b:b + 1] if need_s else None,
+                            workspace=ws, opts=opts)
+            if gf is not None:
+                gf = gf[0] if squeeze else gf
+                gf = gf.to(fb.dtype)
+            gsig = gs.sum() if gs is not None else None
+            return gf, gsig, None, None, None, None, None
+
+    return BilateralCosN
+
+
+_fn = None
+
+
+def bilateral(f, r: int, sigma_r, T: float = 1.0, N: int = 0, kahan: bool = False,
+              gamma_mode: int = GAMMA_FIXED):
+    """Raised-cosine bilateral filter of f ([H, W] or [B, H, W], CUDA, float32
+    or bfloat16) with a (2r+1)^2 box window. sigma_r may be a float or a 0-d
+    tensor (to get dL/dsigma_r); N <= 0 derives N from sigma_r."""
+    import torch
+    global _fn
+    if _fn is None:
+        _fn = _make_function()
+    if not isinstance(sigma_r, torch.Tensor):
+        sigma_r = torch.tensor(float(sigma_r), dtype=torch.float32)
+    return _fn.apply(f, sigma_r, int(r), float(T), int(N), bool(kahan), int(gamma_mode))

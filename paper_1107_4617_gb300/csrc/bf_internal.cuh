@@ -1,0 +1,94 @@
+// Internal declarations shared by the CUDA translation units of libbf.
+// Nothing here is part of the C ABI (include/bf.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "../../include/bf.h"
+
+namespace bf {
+
+// Harmonics of q_N's expansion: k = N mod 2, N mod 2 + 2, ..., N, so
+// K = N / 2 + 1 <= 33 for N <= 64.
+constexpr int KCAP = BF_N_MAX / 2 + 1;
+
+// Everything one filter launch needs, passed by value as the kernel
+// parameter (a_k sits in the constant parameter bank, no __constant__
+// symbol, so concurrent launches with different N never race).
+struct FwdParams {
+    const void* img;      // H x W, FP32 or BF16
+    float* out;           // H x W
+    float* sv_den;        // saved den (nullable)
+    float* sv_dnum;       // saved d num / d s   (nullable)
+    float* sv_dden;       // saved d den / d s   (nullable)
+    int H, W, r;
+    int K;                // number of harmonics
+    int kstart;           // N mod 2: frequency of harmonic 0
+    int Hb;               // output rows per band (grid.y tiles)
+    int Tw;               // output columns per strip (grid.x tiles)
+    float gamma;
+    float a[KCAP];        // a_k for harmonic i (frequency kstart + 2 i)
+};
+
+struct BwdParams {
+    const void* img;      // forward input
+    const float* out;     // forward output
+    const float* gout;    // dL/dout
+    const float* sv_den;
+    const float* sv_dnum;
+    const float* sv_dden;
+    float* gimg;          // dL/dimg (nullable)
+    float* partial;       // per-CTA sums of f * dL/dtheta (nullable)
+    int H, W, r, K, kstart, Hb, Tw;
+    float gamma;
+    float a[KCAP];
+};
+
+// One image of a batch as the persistent kernel sees it: its launch
+// parameters, its tile grid width and the index of its first tile.
+struct BatchImage {
+    FwdParams p;
+    int gx;          // strips of this image
+    int first_tile;  // prefix sum of tiles over the images before it
+    int n_tiles;     // gx * gy
+    int pad;
+};
+
+// Device tile table in the caller's workspace: header, then images.
+struct BatchTable {
+    int counter;     // next tile to hand out (reset by each launch)
+    int n_tiles;
+    int n_images;
+    int grid;        // persistent CTAs to launch
+    int kahan;
+    int in_dtype;
+    int pad[2];
+    BatchImage img[1];  // n_images entries
+};
+
+// Host-side parameter preparation shared by the entry points.
+struct Resolved {
+    int N, K, kstart;
+    double gamma;
+    double a[KCAP];
+};
+
+bf_status resolve(int r, float sigma_r, float T, int N, int gamma_mode, Resolved* out);
+bf_status set_cuda_error(cudaError_t e);
+
+// Launchers (defined in the kernel translation units).
+cudaError_t launch_forward(const FwdParams& p, int nthreads, int kahan, int in_dtype,
+                           cudaStream_t s);
+cudaError_t launch_backward(const BwdParams& p, int nthreads, int in_dtype, cudaStream_t s);
+cudaError_t launch_batch(BatchTable* tab, int grid, int kahan, int in_dtype, cudaStream_t s);
+int sm_count();
+bf_status check_opts(const bf_opts* o);
+bf_status fill_fwd_params(const void* img, float* out, void* saved, int H, int W, int r,
+                          float sigma_r, float T, int N, const bf_opts* opts, FwdParams* p,
+                          int* nt, int* gx, int* gy);
+cudaError_t launch_reduce_sigma(const float* partial, int n, float scale, float* dst,
+                                cudaStream_t s);
+
+}  // namespace bf

@@ -1,0 +1,123 @@
+"""GPU adjoint (bf_backward and the autograd wrapper) against the oracle's
+direct-form reference gradient and FP64 central differences.
+
+Gradient tolerance: max |gpu - ref| / max |ref| <= 1e-3 over the image, and
+elementwise |gpu - ref| <= 1e-3 max(|ref|, 1e-2 max|ref|).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1107_4617_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+GTOL = 1e-3
+
+
+def check_grad(got, ref):
+    got = np.asarray(got, np.float64)
+    ref = np.asarray(ref, np.float64)
+    scale = np.abs(ref).max()
+    assert np.abs(got - ref).max() <= GTOL * scale, (np.abs(got - ref).max(), scale)
+    assert np.all(np.abs(got - ref) <= GTOL * np.maximum(np.abs(ref), 1e-2 * scale))
+
+
+@pytest.mark.parametrize("H,W,r,sigma", [(64, 80, 3, 0.2), (96, 70, 7, 0.15), (40, 300, 12, 0.1),
+                                         (33, 17, 2, 0.3)])
+def test_grad_image_fixed_gamma(cuda_lib, H, W, r, sigma):
+    bf = cuda_lib
+    f = synth.rectangles(H, W, seed=H + W)
+    w = synth.weights((H, W), seed=1)
+    ft = torch.from_numpy(f).cuda().requires_grad_(True)
+    s = torch.tensor(sigma, requires_grad=True)
+    out = bf.bilateral(ft, r, s, 1.0)
+    L = (torch.from_numpy(w).cuda() * out).sum()
+    L.backward()
+    N = oracle.resolve_N(sigma, 1.0)
+    gref, _ = oracle.bilateral_grad(f.astype(np.float64), w.astype(np.float64), r, math.pi / 2, N)
+    check_grad(ft.grad.cpu().numpy(), gref)
+    assert s.grad is not None and float(s.grad) == 0.0  # gamma fixed: dL/dsigma = 0
+
+
+@pytest.mark.parametrize("sigma,r", [(0.15, 7), (0.3, 4)])
+def test_grad_sigma_from_sigma(cuda_lib, sigma, r):
+    """BF_GAMMA_FROM_SIGMA: gamma = 1/(sigma sqrt N), N frozen by the rule.
+    dL/dsigma against the oracle's dL/dgamma * dgamma/dsigma and against
+    central differences of the oracle forward in sigma."""
+    bf = cuda_lib
+    H, W = 72, 88
+    f = synth.rectangles(H, W, seed=7)
+    w = synth.weights((H, W), seed=1)
+    N = oracle.resolve_N(sigma, 1.0)
+    ft = torch.from_numpy(f).cuda().requires_grad_(True)
+    s = torch.tensor(sigma, requires_grad=True)
+    out = bf.bilateral(ft, r, s, 1.0, N=N, gamma_mode=bf.GAMMA_FROM_SIGMA)
+    (torch.from_numpy(w).cuda() * out).sum().backward()
+    g = oracle.gamma_from_sigma(sigma, N)
+    gref, dgam = oracle.bilateral_grad(f.astype(np.float64), w.astype(np.float64), r, g, N)
+    check_grad(ft.grad.cpu().numpy(), gref)
+    dsig_ref = -(g / sigma) * dgam
+    h = 1e-4
+    Lp = np.sum(w * oracle.bilateral(f, r, oracle.gamma_from_sigma(sigma + h, N), N))
+    Lm = np.sum(w * oracle.bilateral(f, r, oracle.gamma_from_sigma(sigma - h, N), N))
+    fd = (Lp - Lm) / (2 * h)
+    assert abs(dsig_ref - fd) <= 1e-6 * max(1.0, abs(fd))
+    assert abs(float(s.grad) - dsig_ref) <= GTOL * max(1.0, abs(dsig_ref)), (float(s.grad), dsig_ref)
+
+
+def test_grad_batch_differentiation_config(cuda_lib):
+    """Differentiation workload shape: a batch of 512x512 images, r=7,
+    sigma_r=0.15 (N=19); image gradient checked on 2 images against the
+    reference gradient of the oracle at sampled pixels via central
+    differences of the oracle forward."""
+    bf = cuda_lib
+    B, H, W, r, sigma = 2, 512, 512, 7, 0.15
+    f = np.stack([synth.rectangles(H, W, seed=100 + b) for b in range(B)])
+    w = synth.weights((B, H, W), seed=1)
+    ft = torch.from_numpy(f).cuda().requires_grad_(True)
+    out = bf.bilateral(ft, r, sigma, 1.0)
+    (torch.from_numpy(w).cuda() * out).sum().backward()
+    gg = ft.grad.cpu().numpy()
+    N = 19
+    rng = np.random.default_rng(5)
+    for b in range(B):
+        for _ in range(6):
+            y, x = int(rng.integers(0, H)), int(rng.integers(0, W))
+            y0, y1 = max(0, y - 2 * r), min(H, y + 2 * r + 1)
+            x0, x1 = max(0, x - 2 * r), min(W, x + 2 * r + 1)
+            # outputs affected by f[y, x] lie within r of it; their windows within 2r
+            sub = f[b, y0:y1, x0:x1].astype(np.float64)
+            wsub = w[b, y0:y1, x0:x1].astype(np.float64)
+            mask = np.zeros_like(sub)
+            yy0, yy1 = max(0, y - r) - y0, min(H, y + r + 1) - y0
+            xx0, xx1 = max(0, x - r) - x0, min(W, x + r + 1) - x0
+            mask[yy0:yy1, xx0:xx1] = 1.0
+            # interior outputs of the crop see the true window only if the crop
+            # holds their full window: true when the crop edge is the image edge
+            # or at distance >= r from them, which holds for the masked region.
+            h = 1e-4
+            sp = sub.copy(); sp[y - y0, x - x0] += h
+            sm = sub.copy(); sm[y - y0, x - x0] -= h
+            Lp = np.sum(mask * wsub * oracle.bilateral(sp, r, math.pi / 2, N))
+            Lm = np.sum(mask * wsub * oracle.bilateral(sm, r, math.pi / 2, N))
+            fd = (Lp - Lm) / (2 * h)
+            assert abs(gg[b, y, x] - fd) <= GTOL * max(1.0, abs(fd)), (b, y, x, gg[b, y, x], fd)
+
+
+def test_backward_raw_abi_grad_sigma_fixed_is_zero(cuda_lib):
+    bf = cuda_lib
+    H, W = 40, 50
+    f = torch.from_numpy(synth.rectangles(H, W, seed=2)).cuda()
+    opts = bf._opts(save=True)
+    sv = torch.empty((3, H, W), device="cuda")
+    out = bf.bf_forward(f, 3, 0.2, 1.0, 0, opts=opts, saved=sv)
+    g = torch.ones_like(out)
+    gs = torch.full((1,), 7.0, device="cuda")
+    ws = torch.empty((bf.bf_backward_workspace_bytes(H, W, 3) // 4 + 1,), device="cuda")
+    bf.bf_backward(f, out, g, sv, 3, 0.2, 1.0, 0, grad_img=None, grad_sigma=gs, workspace=ws)
+    torch.cuda.synchronize()
+    assert float(gs) == 0.0

@@ -1,0 +1,159 @@
+"""GPU parity of bf_forward against the FP64 oracle (element by element).
+
+Tolerance: |gpu - oracle| / max(|oracle|, 1e-2 T) <= 1e-4 for every pixel
+(relative error with a floor at 1% of the range bound T, so pixels near 0 do
+not divide by ~0). The oracle is the direct O(r^2) definition; the GPU runs
+the O(1) moving-sum method, so agreement tests the whole method.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1107_4617_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-4
+
+
+def rel_err(got, ref, T=1.0):
+    got = np.asarray(got, np.float64)
+    ref = np.asarray(ref, np.float64)
+    return np.abs(got - ref) / np.maximum(np.abs(ref), 1e-2 * T)
+
+
+def run_fwd(bf, img_np, r, sigma_r=0.2, T=1.0, N=0, kahan=False, dtype=torch.float32,
+            tile_h=0, tile_w=0, saved=False, guard=0):
+    dev = torch.device("cuda:0")
+    img = torch.from_numpy(np.ascontiguousarray(img_np)).to(dev).to(dtype)
+    H, W = img_np.shape
+    opts = bf._opts(kahan=kahan, in_dtype=bf.BF16 if dtype == torch.bfloat16 else bf.F32,
+                    tile_h=tile_h, tile_w=tile_w, save=saved)
+    buf = torch.full((H * W + 2 * guard,), 12345.0, dtype=torch.float32, device=dev)
+    out = buf[guard:guard + H * W].view(H, W)
+    sv = torch.empty((3, H, W), dtype=torch.float32, device=dev) if saved else None
+    bf.bf_forward(img, r, sigma_r, T, N, out=out, opts=opts, saved=sv)
+    torch.cuda.synchronize()
+    if guard:
+        b = buf.cpu().numpy()
+        assert np.all(b[:guard] == 12345.0) and np.all(b[guard + H * W:] == 12345.0), "guard band written"
+    res = out.cpu().numpy()
+    return (res, sv.cpu().numpy()) if saved else res
+
+
+def oracle_ref(img_np, r, sigma_r, T, N, gamma=None):
+    if N <= 0:
+        N = oracle.resolve_N(sigma_r, T)
+    g = oracle.gamma_fixed(T) if gamma is None else gamma
+    return oracle.bilateral(img_np.astype(np.float64), r, g, N, return_den=True)
+
+
+def test_config1_plain_forward(cuda_lib):
+    """256x256 rectangles+noise, r=5, sigma_r=0.2 -> N=11, T=1 (full image)."""
+    f = synth.rectangles(256, 256, seed=0)
+    got = run_fwd(cuda_lib, f, 5, 0.2, 1.0, 0, guard=4096)
+    ref, den = oracle_ref(f, 5, 0.2, 1.0, 0)
+    e = rel_err(got, ref)
+    assert e.max() <= TOL, e.max()
+
+
+@pytest.mark.parametrize("kind", ["rect", "sin"])
+@pytest.mark.parametrize("r,sigma", [(3, 0.1), (10, 0.2), (30, 0.3)])
+def test_sweep_small(cuda_lib, kind, r, sigma):
+    """Forward-sweep parameters (r, sigma_r -> N = 41/11/5) on 160x203 images
+    (several strips and bands, ragged tails)."""
+    f = synth.image(kind, 160, 203, seed=1)
+    got = run_fwd(cuda_lib, f, r, sigma, 1.0, 0, tile_h=48)
+    ref, _ = oracle_ref(f, r, sigma, 1.0, 0)
+    assert rel_err(got, ref).max() <= TOL
+
+
+@pytest.mark.parametrize("H,W", [(1, 1), (1, 37), (29, 1), (5, 300), (300, 7), (33, 65)])
+@pytest.mark.parametrize("r", [0, 1, 32])
+def test_degenerate_shapes(cuda_lib, H, W, r):
+    f = synth.rectangles(H, W, seed=H * 1000 + W)
+    got = run_fwd(cuda_lib, f, r, 0.2, 1.0, 0, guard=256)
+    ref, _ = oracle_ref(f, r, 0.2, 1.0, 0)
+    assert rel_err(got, ref).max() <= TOL
+
+
+@pytest.mark.parametrize("N", [0, 1, 2, 3, 40, 41, 64])
+def test_orders(cuda_lib, N):
+    f = synth.rectangles(97, 131, seed=N)
+    got = run_fwd(cuda_lib, f, 4, 0.2, 1.0, N)
+    ref, _ = oracle_ref(f, 4, 0.2, 1.0, N)
+    assert rel_err(got, ref).max() <= TOL
+
+
+def test_r0_identity_and_constant(cuda_lib):
+    f = synth.rectangles(64, 70, seed=3)
+    got = run_fwd(cuda_lib, f, 0, 0.1, 1.0, 0)
+    np.testing.assert_allclose(got, f, rtol=0, atol=2e-6)
+    c = np.full((50, 77), 0.625, np.float32)
+    got = run_fwd(cuda_lib, c, 7, 0.1, 1.0, 0)
+    np.testing.assert_allclose(got, 0.625, rtol=0, atol=1e-5)
+
+
+def test_range_bound_T(cuda_lib):
+    """T != 1: an image in [0, 4] filtered with T = 4 equals 4x the [0, 1]
+    image filtered with T = 1."""
+    f = synth.rectangles(80, 90, seed=5)
+    a = run_fwd(cuda_lib, f, 5, 0.2, 1.0, 0)
+    b = run_fwd(cuda_lib, 4.0 * f, 5, 0.8, 4.0, 0)
+    ref, _ = oracle_ref(4.0 * f, 5, 0.8, 4.0, 0)
+    assert rel_err(b, ref, T=4.0).max() <= TOL
+    np.testing.assert_allclose(b, 4.0 * a, rtol=0, atol=4e-5)
+
+
+@pytest.mark.parametrize("tile_w,tile_h", [(64, 16), (128, 40), (256, 300)])
+def test_tile_overrides(cuda_lib, tile_w, tile_h):
+    f = synth.sinusoids(120, 250, seed=9)
+    got = run_fwd(cuda_lib, f, 9, 0.15, 1.0, 0, tile_h=tile_h, tile_w=tile_w)
+    ref, _ = oracle_ref(f, 9, 0.15, 1.0, 0)
+    assert rel_err(got, ref).max() <= TOL
+
+
+def test_kahan_forward(cuda_lib):
+    f = synth.rectangles(300, 180, seed=11)
+    got = run_fwd(cuda_lib, f, 30, 0.1, 1.0, 0, kahan=True)
+    ref, _ = oracle_ref(f, 30, 0.1, 1.0, 0)
+    assert rel_err(got, ref).max() <= TOL
+
+
+def test_bf16_input(cuda_lib):
+    """BF16-stored input: parity against the oracle on the BF16-decoded image."""
+    f = synth.rectangles(200, 150, seed=12)
+    fb = torch.from_numpy(f).to(torch.bfloat16).float().numpy()
+    got = run_fwd(cuda_lib, f, 6, 0.1, 1.0, 0, dtype=torch.bfloat16)
+    ref, _ = oracle_ref(fb, 6, 0.1, 1.0, 0)
+    assert rel_err(got, ref).max() <= TOL
+
+
+def test_saved_buffers(cuda_lib):
+    """den saved by the forward equals the oracle's normaliser; den >= 1."""
+    f = synth.rectangles(90, 110, seed=13)
+    got, sv = run_fwd(cuda_lib, f, 5, 0.2, 1.0, 0, saved=True)
+    ref, den = oracle_ref(f, 5, 0.2, 1.0, 0)
+    assert rel_err(got, ref).max() <= TOL
+    np.testing.assert_allclose(sv[0], den, rtol=2e-5, atol=0)
+    assert sv[0].min() >= 1.0 - 1e-5
+
+
+def test_full_size_sampled_headline(cuda_lib):
+    """4096x4096, r=10, sigma_r=0.1 -> N=41 in the default launch
+    configuration: 3000 sampled pixels (plus the four corners and edge
+    midpoints) against the oracle, and den >= 1 everywhere."""
+    H = W = 4096
+    f = synth.rectangles(H, W, seed=0)
+    got, sv = run_fwd(cuda_lib, f, 10, 0.1, 1.0, 0, saved=True)
+    rng = np.random.default_rng(42)
+    idx = np.concatenate([rng.integers(0, H * W, 3000),
+                          [0, W - 1, (H - 1) * W, H * W - 1, W // 2, (H // 2) * W, (H // 2) * W + W - 1,
+                           (H - 1) * W + W // 2]])
+    ref = oracle.bilateral_points(f.astype(np.float64), 10, math.pi / 2, 41, idx)
+    assert rel_err(got.ravel()[idx], ref).max() <= TOL
+    assert sv[0].min() >= 1.0 - 1e-4
+    assert np.isfinite(got).all()

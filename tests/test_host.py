@@ -1,0 +1,133 @@
+"""CPU-side checks of the C-ABI library: it loads, exports every symbol
+include/bf.h declares, and its host-only parameter rules match the
+mathematics (no GPU compute is called here)."""
+import ctypes
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_1107_4617_gb300 as bf
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not h.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", h)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names += re.findall(r"\b(bf_[a-z0-9_]+)\s*\(", src)
+    return sorted(set(names))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = bf.load()
+    names = declared_functions()
+    assert "bf_forward" in names and "bf_backward" in names and "bf_batch" in names
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_no_oracle_in_product_sources():
+    """The product path never imports or links the oracle."""
+    pkg = os.path.join(ROOT, "paper_1107_4617_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for fn in files:
+            if fn.endswith((".py", ".cu", ".cuh", ".h")):
+                txt = open(os.path.join(dirpath, fn)).read()
+                assert "import oracle" not in txt and "from oracle" not in txt, fn
+                assert "bf_oracle" not in txt, fn
+
+
+@pytest.mark.parametrize("N", list(range(0, 65)))
+def test_coefficients_reproduce_cos_power(N):
+    """sum_k a_k cos(k theta) == cos(theta)^N (binomial expansion of q_N, Sec. 3,
+    written with the shift identity of Sec. 1)."""
+    a = bf.bf_coeffs(N)
+    assert len(a) == N // 2 + 1
+    th = np.linspace(-math.pi, math.pi, 1001)
+    ks = (N % 2) + 2 * np.arange(len(a))
+    series = sum(ai * np.cos(k * th) for ai, k in zip(a, ks))
+    np.testing.assert_allclose(series, np.cos(th) ** N, rtol=0, atol=1e-14)
+    assert abs(sum(a) - 1.0) < 1e-14  # q_N(0) = 1
+    assert all(ai > 0 for ai in a)
+
+
+def test_coefficients_shift_identity():
+    """cos^N(s - t) = sum_k a_k [C_k(s)C_k(t) + S_k(s)S_k(t)] (Eq. def)."""
+    rng = np.random.default_rng(0)
+    s, t = rng.uniform(0, math.pi / 2, 200), rng.uniform(0, math.pi / 2, 200)
+    for N in (1, 2, 11, 40, 41, 64):
+        a = bf.bf_coeffs(N)
+        ks = (N % 2) + 2 * np.arange(len(a))
+        lhs = np.cos(s - t) ** N
+        rhs = sum(ai * (np.cos(k * s) * np.cos(k * t) + np.sin(k * s) * np.sin(k * t))
+                  for ai, k in zip(a, ks))
+        np.testing.assert_allclose(rhs, lhs, rtol=0, atol=1e-13)
+
+
+def test_invalid_coefficients():
+    with pytest.raises(ValueError):
+        bf.bf_coeffs(-1)
+    with pytest.raises(ValueError):
+        bf.bf_coeffs(65)
+
+
+def test_order_rule_and_gamma():
+    assert [bf.bf_resolve_N(s, 1.0) for s in (0.1, 0.15, 0.2, 0.3, 0.4, 0.08)] == [41, 19, 11, 5, 3, 64]
+    assert bf.bf_resolve_N(0.2, 2.0) == bf.bf_resolve_N(0.1, 1.0)  # scale invariance sigma/T
+    assert bf.bf_resolve_N(0.0, 1.0) == -1
+    assert bf.bf_resolve_N(0.1, 0.0) == -1
+    assert bf.bf_gamma(0.1, 1.0, 41, bf.GAMMA_FIXED) == pytest.approx(math.pi / 2)
+    assert bf.bf_gamma(0.15, 1.0, 19, bf.GAMMA_FROM_SIGMA) == pytest.approx(1 / (0.15 * math.sqrt(19)))
+    # variance control keeps gamma below pi/(2T), so the kernel stays >= 0 on [-T, T]
+    for s in (0.08, 0.1, 0.15, 0.2, 0.3, 0.4):
+        N = bf.bf_resolve_N(s, 1.0)
+        assert bf.bf_gamma(s, 1.0, N, bf.GAMMA_FROM_SIGMA) <= math.pi / 2 + 1e-12
+
+
+def test_sizes():
+    assert bf.bf_saved_bytes(4, 5) == 3 * 4 * 5 * 4
+    assert bf.bf_saved_bytes(0, 5) == 0
+
+
+def test_argument_checks_return_before_any_launch():
+    lib = bf.load()
+    o = bf.BfOpts()
+    lib.bf_default_opts(ctypes.byref(o))
+    p = ctypes.c_void_p(0x1000)
+    q = ctypes.c_void_p(0x2000)
+    # null image / output, bad sizes, bad r, bad T, bad sigma: BF_ERR_INVALID_ARG (1)
+    assert lib.bf_forward(None, 4, 4, 1, 0.2, 1.0, 0, q, ctypes.byref(o), None, None) == 1
+    assert lib.bf_forward(p, 0, 4, 1, 0.2, 1.0, 0, q, ctypes.byref(o), None, None) == 1
+    assert lib.bf_forward(p, 4, 4, -1, 0.2, 1.0, 0, q, ctypes.byref(o), None, None) == 1
+    assert lib.bf_forward(p, 4, 4, 1, 0.2, 0.0, 0, q, ctypes.byref(o), None, None) == 1
+    assert lib.bf_forward(p, 4, 4, 1, 0.0, 1.0, 0, q, ctypes.byref(o), None, None) == 1
+    assert lib.bf_forward(p, 4, 4, 1, 0.2, 1.0, 0, p, ctypes.byref(o), None, None) == 1  # aliasing
+    # out of the built range: BF_ERR_UNSUPPORTED (2)
+    assert lib.bf_forward(p, 4, 4, 1, 0.2, 1.0, 65, q, ctypes.byref(o), None, None) == 2
+    assert lib.bf_forward(p, 4, 4, 65, 0.2, 1.0, 3, q, ctypes.byref(o), None, None) == 2
+    assert lib.bf_forward(p, 4, 4, 1, 0.05, 1.0, 0, q, ctypes.byref(o), None, None) == 2  # N=163
+    # bad opts
+    o.in_dtype = 7
+    assert lib.bf_forward(p, 4, 4, 1, 0.2, 1.0, 0, q, ctypes.byref(o), None, None) == 1
+    lib.bf_default_opts(ctypes.byref(o))
+    o.tile_w = 48
+    assert lib.bf_forward(p, 4, 4, 1, 0.2, 1.0, 0, q, ctypes.byref(o), None, None) == 1
+    # backward: missing saved buffer; grad_sigma without workspace -> NOMEM (6)
+    assert lib.bf_backward(p, q, q, None, 4, 4, 1, 0.2, 1.0, 0, q, None, None, 0, None, None) == 1
+    lib.bf_default_opts(ctypes.byref(o))
+    assert lib.bf_backward(p, q, q, q, 4, 4, 1, 0.2, 1.0, 0, None, q, None, 0,
+                           ctypes.byref(o), None) == 6
+    # batch: empty list
+    assert lib.bf_batch(None, 0, None, p, 64, None) == 1
+
+
+def test_status_strings():
+    for s in range(7):
+        assert isinstance(bf.bf_status_string(s), str) and bf.bf_status_string(s)
