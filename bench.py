@@ -192,6 +192,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ref-rows", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernels-only", action="store_true",
+                    help="time the device step only (no e2e, N=40, CPU or accuracy legs); "
+                         "used for profiler captures")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -274,6 +277,16 @@ def main():
     px = H * W
     value = world * px * args.steps / t_step / 1e6
     fwd_value = world * px * args.steps / t_fwd / 1e6
+
+    if args.kernels_only:
+        if rank == 0:
+            print(json.dumps({"kernels_only": True, "value": value, "unit": UNIT,
+                              "fwd_ms": 1e3 * t_fwd / args.steps,
+                              "bwd_ms": 1e3 * t_bwd / args.steps}), flush=True)
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
 
     # forward-only at N = 40 (even order, DC term), reported beside N = 41
     e40 = [torch.cuda.Event(enable_timing=True) for _ in range(2)]

@@ -96,6 +96,34 @@ static bf_status choose_tiles(int H, int W, int r, const bf_opts* o, Tiles* t) {
     return BF_OK;
 }
 
+// The skewed-strip engine serves r <= 32, K <= SYS_KMAX and plain (not
+// Kahan) sums; thread count 64, 96 or 128 (one thread per strip column,
+// Tw = Wi - 2r outputs). Bands: about two resident CTAs per SM.
+static bool sys_tiles(int H, int W, int r, int K, const bf_opts* o, Tiles* t) {
+    if (K > SYS_KMAX || (o && o->kahan)) return false;
+    int wi = SYS_MAX_THREADS;
+    if (o && o->tile_w > 0) {
+        if (o->tile_w > SYS_MAX_THREADS || o->tile_w % 32 != 0) return false;
+        wi = o->tile_w;
+    }
+    if (wi - 2 * r < 16) return false;
+    t->nt = wi;
+    t->Tw = wi - 2 * r;
+    t->gx = (W + t->Tw - 1) / t->Tw;
+    if (o && o->tile_h > 0) {
+        t->Hb = o->tile_h;
+    } else {
+        const int target = 2 * sm_count();
+        int nb = (target + t->gx - 1) / t->gx;
+        if (nb < 1) nb = 1;
+        int hb = (H + nb - 1) / nb;
+        if (hb < 32) hb = 32;
+        t->Hb = hb;
+    }
+    t->gy = (H + t->Hb - 1) / t->Hb;
+    return true;
+}
+
 bf_status check_opts(const bf_opts* o) {
     if (!o) return BF_OK;
     if (o->in_dtype != BF_F32 && o->in_dtype != BF_BF16) return BF_ERR_INVALID_ARG;
@@ -185,17 +213,33 @@ bf_status bf_forward(const void* img, int H, int W, int r, float sigma_r, float 
     bf_status st = fill_fwd_params(img, out, saved, H, W, r, sigma_r, T, N, opts, &p, &nt,
                                    &gx, &gy);
     if (st != BF_OK) return st;
-    cudaError_t e = launch_forward(p, nt, opts ? opts->kahan : 0,
-                                   opts ? opts->in_dtype : BF_F32, (cudaStream_t)stream);
+    const int in_dtype = opts ? opts->in_dtype : BF_F32;
+    Tiles t;
+    cudaError_t e;
+    if (sys_tiles(H, W, r, p.K, opts, &t)) {
+        SysParams q;
+        memset(&q, 0, sizeof(q));
+        q.img = img; q.out = out;
+        q.sv_den = p.sv_den; q.sv_dnum = p.sv_dnum; q.sv_dden = p.sv_dden;
+        q.H = H; q.W = W; q.r = r; q.K = p.K; q.kstart = p.kstart; q.Hb = t.Hb; q.Tw = t.Tw;
+        q.gamma = p.gamma;
+        for (int i = 0; i < p.K; ++i) q.a[i] = p.a[i];
+        e = launch_sys(q, false, saved != nullptr, in_dtype, t.nt, t.gx, t.gy,
+                       (cudaStream_t)stream);
+    } else {
+        e = launch_forward(p, nt, opts ? opts->kahan : 0, in_dtype, (cudaStream_t)stream);
+    }
     if (e != cudaSuccess) return set_cuda_error(e);
     return BF_OK;
 }
 
 size_t bf_backward_workspace_bytes(int H, int W, int r, const bf_opts* opts) {
     if (H < 1 || W < 1 || r < 0 || r > BF_R_MAX) return 0;
-    Tiles t;
+    Tiles t, u;
     if (choose_tiles(H, W, r, opts, &t) != BF_OK) return 0;
-    return (size_t)t.gx * t.gy * sizeof(float);
+    size_t n = (size_t)t.gx * t.gy;
+    if (sys_tiles(H, W, r, 1, opts, &u) && (size_t)u.gx * u.gy > n) n = (size_t)u.gx * u.gy;
+    return n * sizeof(float);
 }
 
 bf_status bf_backward(const void* img, const float* out, const float* grad_out,
@@ -211,10 +255,14 @@ bf_status bf_backward(const void* img, const float* out, const float* grad_out,
     st = resolve(r, sigma_r, T, N, gm, &rs);
     if (st != BF_OK) return st;
     Tiles t;
-    st = choose_tiles(H, W, r, opts, &t);
-    if (st != BF_OK) return st;
+    const bool use_sys = sys_tiles(H, W, r, rs.K, opts, &t);
+    if (!use_sys) {
+        st = choose_tiles(H, W, r, opts, &t);
+        if (st != BF_OK) return st;
+    }
     const size_t need = (size_t)t.gx * t.gy * sizeof(float);
-    if (grad_sigma && (!workspace || ws_bytes < need)) return BF_ERR_NOMEM;
+    if (grad_sigma && gm == BF_GAMMA_FROM_SIGMA && (!workspace || ws_bytes < need))
+        return BF_ERR_NOMEM;
 
     cudaStream_t s = (cudaStream_t)stream;
     if (grad_sigma && gm == BF_GAMMA_FIXED) {
@@ -236,7 +284,20 @@ bf_status bf_backward(const void* img, const float* out, const float* grad_out,
     p.H = H; p.W = W; p.r = r; p.K = rs.K; p.kstart = rs.kstart; p.Hb = t.Hb; p.Tw = t.Tw;
     p.gamma = (float)rs.gamma;
     for (int i = 0; i < rs.K; ++i) p.a[i] = (float)rs.a[i];
-    cudaError_t e = launch_backward(p, t.nt, opts ? opts->in_dtype : BF_F32, s);
+    cudaError_t e;
+    if (use_sys) {
+        SysParams q;
+        memset(&q, 0, sizeof(q));
+        q.img = img; q.fout = out; q.gout = grad_out;
+        q.bden = p.sv_den; q.bdnum = p.sv_dnum; q.bdden = p.sv_dden;
+        q.gimg = grad_img; q.partial = p.partial;
+        q.H = H; q.W = W; q.r = r; q.K = p.K; q.kstart = p.kstart; q.Hb = t.Hb; q.Tw = t.Tw;
+        q.gamma = p.gamma;
+        for (int i = 0; i < p.K; ++i) q.a[i] = p.a[i];
+        e = launch_sys(q, true, false, opts ? opts->in_dtype : BF_F32, t.nt, t.gx, t.gy, s);
+    } else {
+        e = launch_backward(p, t.nt, opts ? opts->in_dtype : BF_F32, s);
+    }
     if (e != cudaSuccess) return set_cuda_error(e);
     if (want_sigma) {
         // dL/dsigma_r = dL/dgamma * dgamma/dsigma_r, gamma = 1/(sigma_r sqrt N).

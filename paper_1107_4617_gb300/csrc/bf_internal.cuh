@@ -46,6 +46,32 @@ struct BwdParams {
     float a[KCAP];
 };
 
+// Skewed-strip engine (bf_sys.cu): forward and adjoint share one kernel
+// template. Up to SYS_KMAX harmonics are kept in registers (8 floats each).
+constexpr int SYS_KMAX = 21;
+constexpr int SYS_MAX_THREADS = 128;
+
+struct SysParams {
+    const void* img;
+    float* out;                 // forward output
+    float* sv_den;              // forward saved buffers (SAVE)
+    float* sv_dnum;
+    float* sv_dden;
+    const float* fout;          // adjoint: forward output
+    const float* gout;          // adjoint: dL/dout
+    const float* bden;          // adjoint: saved den, d num/ds, d den/ds
+    const float* bdnum;
+    const float* bdden;
+    float* gimg;                // adjoint: dL/dimg (nullable)
+    float* partial;             // adjoint: per-CTA sum of f * dL/dtheta (nullable)
+    int H, W, r, K, kstart, Hb, Tw;
+    float gamma;
+    float a[KCAP];
+};
+
+cudaError_t launch_sys(const SysParams& p, bool bwd, bool save, int in_dtype, int wi, int gx,
+                       int gy, cudaStream_t s);
+
 // One image of a batch as the persistent kernel sees it: its launch
 // parameters, its tile grid width and the index of its first tile.
 struct BatchImage {

@@ -32,7 +32,8 @@ def test_batch_matches_single_and_oracle(cuda_lib):
         hb = max(128, 4 * s["r"])
         single = bf.bf_forward(im, s["r"], s["sigma_r"], 1.0, 0, opts=bf._opts(tile_h=hb))
         torch.cuda.synchronize()
-        assert torch.max(torch.abs(single - o)).item() <= 1e-6
+        # same filter, possibly a different tile engine: agree to FP32 rounding
+        assert torch.max(torch.abs(single - o)).item() <= 1e-5
         N = oracle.resolve_N(s["sigma_r"], 1.0)
         ref = oracle.bilateral(im.cpu().numpy().astype(np.float64), s["r"], math.pi / 2, N)
         e = np.abs(o.cpu().numpy() - ref) / np.maximum(np.abs(ref), 1e-2)

@@ -122,6 +122,7 @@ def test_argument_checks_return_before_any_launch():
     # backward: missing saved buffer; grad_sigma without workspace -> NOMEM (6)
     assert lib.bf_backward(p, q, q, None, 4, 4, 1, 0.2, 1.0, 0, q, None, None, 0, None, None) == 1
     lib.bf_default_opts(ctypes.byref(o))
+    o.gamma_mode = bf.GAMMA_FROM_SIGMA
     assert lib.bf_backward(p, q, q, q, 4, 4, 1, 0.2, 1.0, 0, None, q, None, 0,
                            ctypes.byref(o), None) == 6
     # batch: empty list
