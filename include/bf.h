@@ -154,6 +154,44 @@ bf_status bf_backward(const void* img, const float* out, const float* grad_out,
                       float* grad_img, float* grad_sigma, void* workspace, size_t ws_bytes,
                       const bf_opts* opts, void* stream);
 
+/* Capacity of the fixed scratch array bf_backward_noalloc uses: this many
+   per-CTA partial sums (64 KiB per device). */
+#define BF_NOALLOC_MAX_PARTIALS 16384
+
+/*
+ * bf_backward for callers that cannot allocate device memory. The paper has
+ * no counterpart; this is a deployment variant of the adjoint above.
+ *
+ * Who needs it: code that may not call cudaMalloc, e.g. a plugin inside a
+ * host application that owns all GPU memory through its own pool and forbids
+ * libraries from allocating, or a latency-critical loop that cannot afford
+ * an allocation's implicit device synchronisation. Such a caller still owns
+ * and passes every input and output, but no workspace: the per-CTA
+ * dL/dsigma_r partial sums go to a fixed array compiled into the library
+ * (BF_NOALLOC_MAX_PARTIALS floats), which every GPU that loads the library
+ * holds until the process exits.
+ *
+ * Arguments and results are those of bf_backward without workspace/ws_bytes.
+ * Errors: as bf_backward, plus BF_ERR_UNSUPPORTED when the image needs more
+ * partial slots than the array holds (bf_backward_workspace_bytes(H, W, r,
+ * opts) > BF_NOALLOC_MAX_PARTIALS * sizeof(float)), checked before any
+ * launch.
+ *
+ * Set-up: the first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current) and keeps it; make that
+ * first call before any stream capture. It allocates nothing: no cudaMalloc,
+ * cudaFree or allocating library routine.
+ *
+ * Sharing: every call on a device uses the same array, which keeps the last
+ * call's contents. No slot needs to start at zero (each call writes every
+ * slot it reads), but calls whose executions overlap on the GPU (e.g. on two
+ * streams at once) race on the array: serialise them.
+ */
+bf_status bf_backward_noalloc(const void* img, const float* out, const float* grad_out,
+                              const void* saved, int H, int W, int r, float sigma_r, float T,
+                              int N, float* grad_img, float* grad_sigma, const bf_opts* opts,
+                              void* stream);
+
 /* Workspace bytes bf_batch needs for n descriptors (device tile table). */
 size_t bf_batch_workspace_bytes(const bf_desc* descs, int n, const bf_opts* opts);
 

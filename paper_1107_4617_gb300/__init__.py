@@ -340,3 +340,27 @@ def bilateral(f, r: int, sigma_r, T: float = 1.0, N: int = 0, kahan: bool = Fals
     if not isinstance(sigma_r, torch.Tensor):
         sigma_r = torch.tensor(float(sigma_r), dtype=torch.float32)
     return _fn.apply(f, sigma_r, int(r), float(T), int(N), bool(kahan), int(gamma_mode))
+
+
+def bf_backward_noalloc(img, out, grad_out, saved, r: int, sigma_r: float, T: float = 1.0,
+                        N: int = 0, grad_img=None, grad_sigma=None, opts: BfOpts | None = None,
+                        stream=None):
+    """bf_backward for callers that cannot allocate device memory: the
+    dL/dsigma_r partial sums use a fixed scratch array inside the library
+    instead of a caller workspace. The first call on a device looks up that
+    array's address; calls that overlap on the GPU share it and race."""
+    lib = load()
+    f = lib.bf_backward_noalloc
+    vp, c_int, c_float = ctypes.c_void_p, ctypes.c_int, ctypes.c_float
+    f.restype = c_int
+    f.argtypes = [vp, vp, vp, vp, c_int, c_int, c_int, c_float, c_float, c_int, vp, vp,
+                  ctypes.POINTER(BfOpts), vp]
+    H, W = img.shape
+    if opts is None:
+        opts = _opts(in_dtype=_in_dtype(img))
+    st = f(_dptr(img, "img"), _dptr(out, "out"), _dptr(grad_out, "grad_out"),
+           _dptr(saved, "saved"), H, W, int(r), float(sigma_r), float(T), int(N),
+           _dptr(grad_img, "grad_img") if grad_img is not None else None,
+           _dptr(grad_sigma, "grad_sigma") if grad_sigma is not None else None,
+           ctypes.byref(opts), _stream_handle(stream))
+    _check("bf_backward_noalloc", st)
