@@ -101,7 +101,7 @@ static bf_status choose_tiles(int H, int W, int r, const bf_opts* o, Tiles* t) {
 // Tw = Wi - 2r outputs). Bands: about two resident CTAs per SM.
 static bool sys_tiles(int H, int W, int r, int K, const bf_opts* o, Tiles* t) {
     if (K > SYS_KMAX || (o && o->kahan)) return false;
-    int wi = SYS_MAX_THREADS;
+    int wi = 128;
     if (o && o->tile_w > 0) {
         if (o->tile_w > SYS_MAX_THREADS || o->tile_w % 32 != 0) return false;
         wi = o->tile_w;
@@ -223,7 +223,10 @@ bf_status bf_forward(const void* img, int H, int W, int r, float sigma_r, float 
         q.sv_den = p.sv_den; q.sv_dnum = p.sv_dnum; q.sv_dden = p.sv_dden;
         q.H = H; q.W = W; q.r = r; q.K = p.K; q.kstart = p.kstart; q.Hb = t.Hb; q.Tw = t.Tw;
         q.gamma = p.gamma;
-        for (int i = 0; i < p.K; ++i) q.a[i] = p.a[i];
+        for (int i = 0; i < p.K; ++i) {
+            q.a[i] = p.a[i];
+            q.ak[i] = p.a[i] * (float)(p.kstart + 2 * i);
+        }
         e = launch_sys(q, false, saved != nullptr, in_dtype, t.nt, t.gx, t.gy,
                        (cudaStream_t)stream);
     } else {
@@ -293,7 +296,10 @@ bf_status bf_backward(const void* img, const float* out, const float* grad_out,
         q.gimg = grad_img; q.partial = p.partial;
         q.H = H; q.W = W; q.r = r; q.K = p.K; q.kstart = p.kstart; q.Hb = t.Hb; q.Tw = t.Tw;
         q.gamma = p.gamma;
-        for (int i = 0; i < p.K; ++i) q.a[i] = p.a[i];
+        for (int i = 0; i < p.K; ++i) {
+            q.a[i] = p.a[i];
+            q.ak[i] = p.a[i] * (float)(p.kstart + 2 * i);
+        }
         e = launch_sys(q, true, false, opts ? opts->in_dtype : BF_F32, t.nt, t.gx, t.gy, s);
     } else {
         e = launch_backward(p, t.nt, opts ? opts->in_dtype : BF_F32, s);

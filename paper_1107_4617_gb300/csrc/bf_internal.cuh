@@ -66,7 +66,8 @@ struct SysParams {
     float* partial;             // adjoint: per-CTA sum of f * dL/dtheta (nullable)
     int H, W, r, K, kstart, Hb, Tw;
     float gamma;
-    float a[KCAP];
+    float a[KCAP];   // a_k of harmonic i
+    float ak[KCAP];  // k * a_k (centre-derivative terms)
 };
 
 cudaError_t launch_sys(const SysParams& p, bool bwd, bool save, int in_dtype, int wi, int gx,
