@@ -35,29 +35,42 @@ __device__ __forceinline__ float ld_img(const __nv_bfloat16* p, size_t i) {
     return __bfloat162float(p[i]);
 }
 
-// Rotation state of one pixel stream: z = current harmonic (cos, sin),
-// w = (cos 2 theta, sin 2 theta). A masked stream has z = 0.
-struct Rot {
-    float zc, zs, wc, ws;
+// Rotation state of one pixel stream, two harmonics at a time (packed FP32
+// pairs): zc/zs hold (cos, sin) of harmonics k and k+2; both advance by
+// w^2 = e^{4 i theta} per pair. c2, s2, ns2 = (cos 4theta, sin 4theta,
+// -sin 4theta) duplicated in both halves. A masked stream has z = 0.
+struct Rot2 {
+    float2 zc, zs, c2, s2, ns2;
 };
 
-__device__ __forceinline__ Rot seed(float f, float gamma, int kstart, bool on) {
+__device__ __forceinline__ Rot2 seed2(float f, float gamma, int kstart, bool on) {
     float sn, cs;
     __sincosf(gamma * f, &sn, &cs);
-    Rot s;
-    s.wc = (cs - sn) * (cs + sn);
-    s.ws = 2.0f * sn * cs;
-    s.zc = on ? (kstart ? cs : 1.0f) : 0.0f;
-    s.zs = on ? (kstart ? sn : 0.0f) : 0.0f;
-    return s;
+    const float wc = (cs - sn) * (cs + sn);   // e^{2 i theta}
+    const float ws = 2.0f * sn * cs;
+    const float z0c = kstart ? cs : 1.0f;     // harmonic kstart
+    const float z0s = kstart ? sn : 0.0f;
+    const float z1c = fmaf(z0c, wc, -z0s * ws);  // harmonic kstart + 2
+    const float z1s = fmaf(z0s, wc, z0c * ws);
+    const float w2c = fmaf(wc, wc, -ws * ws);    // e^{4 i theta}
+    const float w2s = 2.0f * wc * ws;
+    Rot2 r;
+    r.zc = on ? make_float2(z0c, z1c) : make_float2(0.f, 0.f);
+    r.zs = on ? make_float2(z0s, z1s) : make_float2(0.f, 0.f);
+    r.c2 = make_float2(w2c, w2c);
+    r.s2 = make_float2(w2s, w2s);
+    r.ns2 = make_float2(-w2s, -w2s);
+    return r;
 }
 
-__device__ __forceinline__ void rot(Rot& s) {
-    const float c = fmaf(s.zc, s.wc, -s.zs * s.ws);
-    const float n = fmaf(s.zs, s.wc, s.zc * s.ws);
+__device__ __forceinline__ void rot2(Rot2& s) {
+    const float2 c = __ffma2_rn(s.zs, s.ns2, __fmul2_rn(s.zc, s.c2));
+    const float2 n = __ffma2_rn(s.zc, s.s2, __fmul2_rn(s.zs, s.c2));
     s.zc = c;
     s.zs = n;
 }
+
+__device__ __forceinline__ float2 dup(float v) { return make_float2(v, v); }
 
 // Predicated shared store (lane 31's hand-off to the next warp): one
 // instruction, no branch inside the unrolled harmonic loop.
@@ -129,15 +142,17 @@ __device__ __forceinline__ Geo geometry(const SysParams& p, int tau, int span, i
 
 }  // namespace
 
-// 128-thread strips, two resident CTAs per SM.
-template <int KC, bool BWD, bool SAVE, typename Tin>
+// 128-thread strips, two resident CTAs per SM. KP = harmonic pairs.
+template <int KP, bool BWD, bool SAVE, typename Tin>
 __global__ void __launch_bounds__(SYS_MAX_THREADS, 2) bf_sys_kernel(SysParams p) {
     extern __shared__ float4 smem[];
     const int Wi = blockDim.x;
     const int NW = Wi >> 5;
-    float4* sbuf = smem;                    // [KC][Wi]: S of each lane, last step
-    float4* xfer = smem + KC * Wi;          // [2][NW][KC]: lane 31 -> next warp's lane 0
-    float4* zero = xfer + 2 * NW * KC;      // [KC]: carry-in of the first lane
+    // S of each lane at the last step: [KP][2][Wi] float4, i.e. per harmonic
+    // pair (x_k, x_k+2, y_k, y_k+2) and (z_k, z_k+2, w_k, w_k+2)
+    float4* sbuf = smem;
+    float4* xfer = smem + 2 * KP * Wi;        // [2][NW][KP][2]: lane 31 -> next warp
+    float4* zero = xfer + 2 * NW * 2 * KP;    // [KP][2]: carry-in of the first lane
     const Tin* img = static_cast<const Tin*>(p.img);
     const int j = threadIdx.x;
     const int lane = j & 31;
@@ -155,12 +170,14 @@ __global__ void __launch_bounds__(SYS_MAX_THREADS, 2) bf_sys_kernel(SysParams p)
     const int span = rows + 2 * r;        // local steps of one thread
     const int steps = span + Wi - 1;
 
-    for (int i = threadIdx.x; i < KC * Wi + 2 * NW * KC + KC; i += Wi)
+    for (int i = threadIdx.x; i < 2 * KP * Wi + 4 * NW * KP + 2 * KP; i += Wi)
         smem[i] = make_float4(0.f, 0.f, 0.f, 0.f);
 
-    float4 D[KC];
+    float2 Dx[KP], Dy[KP], Dz[KP], Dw[KP];
 #pragma unroll
-    for (int i = 0; i < KC; ++i) D[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int i = 0; i < KP; ++i) {
+        Dx[i] = make_float2(0.f, 0.f); Dy[i] = Dx[i]; Dz[i] = Dx[i]; Dw[i] = Dx[i];
+    }
     float gsum = 0.f;
 
     // pixel values of the current step, loaded during the previous one
@@ -188,98 +205,96 @@ __global__ void __launch_bounds__(SYS_MAX_THREADS, 2) bf_sys_kernel(SysParams p)
             load_px<BWD, Tin>(v3, p, img, g.m3, g.q3);
             load_px<BWD, Tin>(vc, p, img, g.out, g.qo);
 
-            Rot s0 = seed(c0.f, p.gamma, p.kstart, gc.m0);
-            Rot s1 = seed(c1.f, p.gamma, p.kstart, gc.m1);
-            Rot s2 = seed(c2v.f, p.gamma, p.kstart, gc.m2);
-            Rot s3 = seed(c3.f, p.gamma, p.kstart, gc.m3);
-            Rot sc = seed(cc.f, p.gamma, p.kstart, gc.out);
-            // plane weights with the stream's sign: + own enter, - second enter,
-            // - own leave, + second leave
-            float u0, u1, u2, u3, b0 = 0.f, b1 = 0.f, b2 = 0.f, b3 = 0.f, ac = 0.f, bc = 0.f;
+            Rot2 s0 = seed2(c0.f, p.gamma, p.kstart, gc.m0);
+            Rot2 s1 = seed2(c1.f, p.gamma, p.kstart, gc.m1);
+            Rot2 s2 = seed2(c2v.f, p.gamma, p.kstart, gc.m2);
+            Rot2 s3 = seed2(c3.f, p.gamma, p.kstart, gc.m3);
+            Rot2 sc = seed2(cc.f, p.gamma, p.kstart, gc.out);
+            // plane weights (u: first two planes, v: last two) with the stream's
+            // sign: + own enter, - second enter, - own leave, + second leave
+            float2 U0, U1, U2, U3, V0, V1, V2, V3;
+            float ac = 0.f, bc = 0.f;
             if constexpr (!BWD) {
-                u0 = c0.f; u1 = -c1.f; u2 = -c2v.f; u3 = c3.f;
+                U0 = dup(c0.f); U1 = dup(-c1.f); U2 = dup(-c2v.f); U3 = dup(c3.f);
+                V0 = dup(1.f); V1 = dup(-1.f); V2 = dup(-1.f); V3 = dup(1.f);
             } else {
                 const float a0 = __fdividef(c0.g, c0.den), a1 = __fdividef(c1.g, c1.den);
                 const float a2 = __fdividef(c2v.g, c2v.den), a3 = __fdividef(c3.g, c3.den);
-                u0 = a0; u1 = -a1; u2 = -a2; u3 = a3;
-                b0 = -a0 * c0.out; b1 = a1 * c1.out; b2 = a2 * c2v.out; b3 = -a3 * c3.out;
+                U0 = dup(a0); U1 = dup(-a1); U2 = dup(-a2); U3 = dup(a3);
+                V0 = dup(-a0 * c0.out); V1 = dup(a1 * c1.out);
+                V2 = dup(a2 * c2v.out); V3 = dup(-a3 * c3.out);
                 ac = __fdividef(cc.g, cc.den);
                 bc = -ac * cc.out;
             }
+            const float2 FC = dup(cc.f);
 
             // where this lane reads its left neighbour's S of the previous step
             const float4* rd;
             int rstride;
             if (lane != 0) { rd = sbuf + (j - 1); rstride = Wi; }
-            else if (w != 0) { rd = xfer + (((t + 1) & 1) * NW + (w - 1)) * KC; rstride = 1; }
+            else if (w != 0) { rd = xfer + (((t + 1) & 1) * NW + (w - 1)) * 2 * KP; rstride = 1; }
             else { rd = zero; rstride = 1; }
             float4* wr = sbuf + j;
-            float4* wx = xfer + ((t & 1) * NW + w) * KC;
+            float4* wx = xfer + ((t & 1) * NW + w) * 2 * KP;
             const bool carry = (lane == 31) && (w + 1 < NW);
 
-            float n0 = 0.f, n1 = 0.f, d0 = 0.f, d1 = 0.f, e0 = 0.f, e1 = 0.f, h0 = 0.f, h1 = 0.f;
-            // carry-ins are read two harmonics ahead: a slot of harmonic i is only
-            // rewritten after the __syncwarp of iteration i, so earlier reads are safe
-            float4 sin_a = rd[0];
-            float4 sin_b = (KC > 1) ? rd[rstride] : make_float4(0.f, 0.f, 0.f, 0.f);
+            float2 NUM = make_float2(0.f, 0.f), DEN = NUM, DNUM = NUM, DDEN = NUM;
+            // carry-ins read one pair ahead: a slot of pair i is only rewritten
+            // after the __syncwarp of iteration i, so earlier reads are safe
+            float4 ina = rd[0], inb = rd[rstride];
 #pragma unroll
-            for (int i = 0; i < KC; ++i) {
-                {
-                    const float4 sin = sin_a;
-                    sin_a = sin_b;
-                    if (i + 2 < KC) sin_b = rd[(i + 2) * rstride];
-                    float4 d = D[i];
-                    d.x = fmaf(s0.zc, u0, d.x); d.x = fmaf(s1.zc, u1, d.x);
-                    d.x = fmaf(s2.zc, u2, d.x); d.x = fmaf(s3.zc, u3, d.x);
-                    d.y = fmaf(s0.zs, u0, d.y); d.y = fmaf(s1.zs, u1, d.y);
-                    d.y = fmaf(s2.zs, u2, d.y); d.y = fmaf(s3.zs, u3, d.y);
-                    if constexpr (!BWD) {
-                        d.z = ((d.z + s0.zc) - s1.zc) - s2.zc + s3.zc;
-                        d.w = ((d.w + s0.zs) - s1.zs) - s2.zs + s3.zs;
-                    } else {
-                        d.z = fmaf(s0.zc, b0, d.z); d.z = fmaf(s1.zc, b1, d.z);
-                        d.z = fmaf(s2.zc, b2, d.z); d.z = fmaf(s3.zc, b3, d.z);
-                        d.w = fmaf(s0.zs, b0, d.w); d.w = fmaf(s1.zs, b1, d.w);
-                        d.w = fmaf(s2.zs, b2, d.w); d.w = fmaf(s3.zs, b3, d.w);
+            for (int i = 0; i < KP; ++i) {
+                const float4 A = ina, B = inb;
+                if (i + 1 < KP) { ina = rd[(2 * i + 2) * rstride]; inb = rd[(2 * i + 3) * rstride]; }
+                float2 dx = Dx[i], dy = Dy[i], dz = Dz[i], dw = Dw[i];
+                dx = __ffma2_rn(s0.zc, U0, dx); dx = __ffma2_rn(s1.zc, U1, dx);
+                dx = __ffma2_rn(s2.zc, U2, dx); dx = __ffma2_rn(s3.zc, U3, dx);
+                dy = __ffma2_rn(s0.zs, U0, dy); dy = __ffma2_rn(s1.zs, U1, dy);
+                dy = __ffma2_rn(s2.zs, U2, dy); dy = __ffma2_rn(s3.zs, U3, dy);
+                dz = __ffma2_rn(s0.zc, V0, dz); dz = __ffma2_rn(s1.zc, V1, dz);
+                dz = __ffma2_rn(s2.zc, V2, dz); dz = __ffma2_rn(s3.zc, V3, dz);
+                dw = __ffma2_rn(s0.zs, V0, dw); dw = __ffma2_rn(s1.zs, V1, dw);
+                dw = __ffma2_rn(s2.zs, V2, dw); dw = __ffma2_rn(s3.zs, V3, dw);
+                Dx[i] = dx; Dy[i] = dy; Dz[i] = dz; Dw[i] = dw;
+                const float2 hx = __fadd2_rn(make_float2(A.x, A.y), dx);
+                const float2 hy = __fadd2_rn(make_float2(A.z, A.w), dy);
+                const float2 hz = __fadd2_rn(make_float2(B.x, B.y), dz);
+                const float2 hw = __fadd2_rn(make_float2(B.z, B.w), dw);
+                __syncwarp();  // every lane has read its neighbour's slots before they change
+                const float4 oa = make_float4(hx.x, hx.y, hy.x, hy.y);
+                const float4 ob = make_float4(hz.x, hz.y, hw.x, hw.y);
+                wr[(2 * i) * Wi] = oa;
+                wr[(2 * i + 1) * Wi] = ob;
+                st_shared_if(wx + 2 * i, oa, carry);
+                st_shared_if(wx + 2 * i + 1, ob, carry);
+                const float2 A2 = make_float2(p.a[2 * i], p.a[2 * i + 1]);
+                const float2 AK2 = make_float2(p.ak[2 * i], p.ak[2 * i + 1]);
+                const float2 nzs = __fmul2_rn(sc.zs, dup(-1.f));
+                if constexpr (!BWD) {
+                    NUM = __ffma2_rn(A2, __ffma2_rn(sc.zc, hx, __fmul2_rn(sc.zs, hy)), NUM);
+                    DEN = __ffma2_rn(A2, __ffma2_rn(sc.zc, hz, __fmul2_rn(sc.zs, hw)), DEN);
+                    if constexpr (SAVE) {
+                        DNUM = __ffma2_rn(AK2, __ffma2_rn(sc.zc, hy, __fmul2_rn(nzs, hx)), DNUM);
+                        DDEN = __ffma2_rn(AK2, __ffma2_rn(sc.zc, hw, __fmul2_rn(nzs, hz)), DDEN);
                     }
-                    D[i] = d;
-                    float4 h;
-                    h.x = sin.x + d.x; h.y = sin.y + d.y; h.z = sin.z + d.z; h.w = sin.w + d.w;
-                    __syncwarp();  // every lane has read its neighbour's slot before it changes
-                    wr[i * Wi] = h;
-                    st_shared_if(wx + i, h, carry);
-                    const float a = p.a[i];
-                    const float ak = p.ak[i];
-                    float& N_ = (i & 1) ? n1 : n0;
-                    float& Dn = (i & 1) ? d1 : d0;
-                    if constexpr (!BWD) {
-                        N_ = fmaf(a, fmaf(sc.zc, h.x, sc.zs * h.y), N_);   // num
-                        Dn = fmaf(a, fmaf(sc.zc, h.z, sc.zs * h.w), Dn);   // den
-                        if constexpr (SAVE) {
-                            float& E_ = (i & 1) ? e1 : e0;
-                            float& F_ = (i & 1) ? h1 : h0;
-                            E_ = fmaf(ak, fmaf(sc.zc, h.y, -sc.zs * h.x), E_);  // d num / d s
-                            F_ = fmaf(ak, fmaf(sc.zc, h.w, -sc.zs * h.z), F_);  // d den / d s
-                        }
-                    } else {
-                        // h = (Box[alpha C], Box[alpha S], Box[beta C], Box[beta S])
-                        N_ = fmaf(a, fmaf(h.x, sc.zc, h.y * sc.zs), N_);
-                        const float pp = fmaf(h.y, sc.zc, -h.x * sc.zs);
-                        const float qq = fmaf(h.w, sc.zc, -h.z * sc.zs);
-                        Dn = fmaf(ak, fmaf(cc.f, pp, qq), Dn);
-                    }
-                    rot(s0); rot(s1); rot(s2); rot(s3); rot(sc);
+                } else {
+                    // h = (Box[alpha C], Box[alpha S], Box[beta C], Box[beta S])
+                    NUM = __ffma2_rn(A2, __ffma2_rn(hx, sc.zc, __fmul2_rn(hy, sc.zs)), NUM);
+                    const float2 pp = __ffma2_rn(hy, sc.zc, __fmul2_rn(hx, nzs));
+                    const float2 qq = __ffma2_rn(hw, sc.zc, __fmul2_rn(hz, nzs));
+                    DEN = __ffma2_rn(AK2, __ffma2_rn(FC, pp, qq), DEN);
                 }
+                rot2(s0); rot2(s1); rot2(s2); rot2(s3); rot2(sc);
             }
             if (gc.out) {
                 const size_t o = gc.qo;
-                const float num = n0 + n1, den = d0 + d1;
+                const float num = NUM.x + NUM.y, den = DEN.x + DEN.y;
                 if constexpr (!BWD) {
                     p.out[o] = num / den;
                     if constexpr (SAVE) {
                         p.sv_den[o] = den;
-                        p.sv_dnum[o] = e0 + e1;
-                        p.sv_dden[o] = h0 + h1;
+                        p.sv_dnum[o] = DNUM.x + DNUM.y;
+                        p.sv_dden[o] = DDEN.x + DDEN.y;
                     }
                 } else {
                     const float gt = den + ac * __ldg(p.bdnum + o) + bc * __ldg(p.bdden + o);
@@ -304,24 +319,24 @@ __global__ void __launch_bounds__(SYS_MAX_THREADS, 2) bf_sys_kernel(SysParams p)
     }
 }
 
-// Harmonic counts with their own instantiation; other K run on the next
+// Harmonic-pair counts with their own instantiation; other K run on the next
 // larger one with zero coefficients for the extra harmonics.
-static int sys_kc(int K) {
-    static const int kcs[] = {1, 2, 3, 4, 6, 8, 11, 14, 17, 21};
-    for (int kc : kcs)
-        if (K <= kc) return kc;
+static int sys_kp(int K) {
+    static const int kps[] = {1, 2, 3, 4, 6, 8, 11};
+    for (int kp : kps)
+        if (2 * kp >= K) return kp;
     return -1;
 }
 
 size_t sys_smem_bytes(int K, int wi) {
-    const int kc = sys_kc(K);
-    return sizeof(float4) * ((size_t)kc * wi + 2 * (size_t)(wi / 32) * kc + kc);
+    const int kp = sys_kp(K);
+    return sizeof(float4) * (2 * (size_t)kp * wi + 4 * (size_t)(wi / 32) * kp + 2 * kp);
 }
 
-template <int KC, bool BWD, bool SAVE, typename Tin>
+template <int KP, bool BWD, bool SAVE, typename Tin>
 static cudaError_t sys_launch(const SysParams& p, int wi, int gx, int gy, cudaStream_t s) {
-    auto kern = bf_sys_kernel<KC, BWD, SAVE, Tin>;
-    const size_t smem = sizeof(float4) * ((size_t)KC * wi + 2 * (size_t)(wi / 32) * KC + KC);
+    auto kern = bf_sys_kernel<KP, BWD, SAVE, Tin>;
+    const size_t smem = sizeof(float4) * (2 * (size_t)KP * wi + 4 * (size_t)(wi / 32) * KP + 2 * KP);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
@@ -332,7 +347,7 @@ static cudaError_t sys_launch(const SysParams& p, int wi, int gx, int gy, cudaSt
 
 template <bool BWD, bool SAVE, typename Tin>
 static cudaError_t sys_launch_k(const SysParams& p, int wi, int gx, int gy, cudaStream_t s) {
-    switch (sys_kc(p.K)) {
+    switch (sys_kp(p.K)) {
         case 1: return sys_launch<1, BWD, SAVE, Tin>(p, wi, gx, gy, s);
         case 2: return sys_launch<2, BWD, SAVE, Tin>(p, wi, gx, gy, s);
         case 3: return sys_launch<3, BWD, SAVE, Tin>(p, wi, gx, gy, s);
@@ -340,9 +355,6 @@ static cudaError_t sys_launch_k(const SysParams& p, int wi, int gx, int gy, cuda
         case 6: return sys_launch<6, BWD, SAVE, Tin>(p, wi, gx, gy, s);
         case 8: return sys_launch<8, BWD, SAVE, Tin>(p, wi, gx, gy, s);
         case 11: return sys_launch<11, BWD, SAVE, Tin>(p, wi, gx, gy, s);
-        case 14: return sys_launch<14, BWD, SAVE, Tin>(p, wi, gx, gy, s);
-        case 17: return sys_launch<17, BWD, SAVE, Tin>(p, wi, gx, gy, s);
-        case 21: return sys_launch<21, BWD, SAVE, Tin>(p, wi, gx, gy, s);
     }
     return cudaErrorInvalidValue;
 }
@@ -351,7 +363,7 @@ cudaError_t launch_sys(const SysParams& p_in, bool bwd, bool save, int in_dtype,
                        int gy, cudaStream_t s) {
     if (p_in.K > SYS_KMAX || wi > SYS_MAX_THREADS || wi % 32 != 0) return cudaErrorInvalidValue;
     SysParams p = p_in;
-    for (int i = p.K; i < sys_kc(p.K); ++i) { p.a[i] = 0.f; p.ak[i] = 0.f; }  // padding harmonics
+    for (int i = p.K; i < 2 * sys_kp(p.K); ++i) { p.a[i] = 0.f; p.ak[i] = 0.f; }  // padding
     if (in_dtype == BF_BF16) {
         if (bwd) return sys_launch_k<true, false, __nv_bfloat16>(p, wi, gx, gy, s);
         return save ? sys_launch_k<false, true, __nv_bfloat16>(p, wi, gx, gy, s)
