@@ -82,6 +82,14 @@ __device__ __forceinline__ void st_shared_if(float4* dst, float4 v, bool pred) {
         :: "r"(a), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "r"((int)pred) : "memory");
 }
 
+// Rows ahead of the current entering row that are pulled into L2.
+constexpr int PREFETCH_ROWS = 8;
+
+template <typename T>
+__device__ __forceinline__ void prefetch_l2(const T* ptr) {
+    asm volatile("prefetch.global.L2 [%0];" :: "l"(ptr));
+}
+
 // Per-pixel values a stream needs, loaded one step ahead.
 template <bool BWD>
 struct Px;
@@ -197,6 +205,14 @@ __global__ void __launch_bounds__(SYS_MAX_THREADS, 2) bf_sys_kernel(SysParams p)
         if (warp_last >= 0 && warp_first < span) {
             const Geo gc = g;  // geometry of this step
             const Px<BWD> c0 = v0, c1 = v1, c2v = v2, c3 = v3, cc = vc;
+            // pull the entering row of a later step into L2 (no registers held):
+            // the other four streams re-read pixels the strip touched recently
+            {
+                const int ef = y0 - r + (t + PREFETCH_ROWS - j);
+                // (forward only: the adjoint's four extra streams made it slower)
+                if (!BWD && own_in && ef >= 0 && ef < p.H)
+                    prefetch_l2(static_cast<const Tin*>(p.img) + (size_t)ef * p.W + cw);
+            }
             // prefetch the next step's pixels; their latency hides under this step
             g = geometry(p, t + 1 - j, span, y0, cw, c2, co, own_in, sec_in, out_lane);
             load_px<BWD, Tin>(v0, p, img, g.m0, g.q0);

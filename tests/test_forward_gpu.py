@@ -157,3 +157,4 @@ def test_full_size_sampled_headline(cuda_lib):
     assert rel_err(got.ravel()[idx], ref).max() <= TOL
     assert sv[0].min() >= 1.0 - 1e-4
     assert np.isfinite(got).all()
+
