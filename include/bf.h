@@ -124,7 +124,9 @@ size_t bf_saved_bytes(int H, int W);
  *   out     device, H x W FP32. Must not alias img.
  *   opts    NULL = defaults.
  *   saved   NULL, or device buffer of bf_saved_bytes(H, W), written for
- *           bf_backward.
+ *           bf_backward. When N > 43 (or opts->kahan with N > 23) the
+ *           harmonics run in chunks that accumulate in this buffer; without
+ *           it such calls take a slower single-pass kernel.
  * Errors: BF_ERR_INVALID_ARG (null pointer, H/W < 1, r < 0, T <= 0, bad
  * sigma_r, bad opts), BF_ERR_UNSUPPORTED (N > BF_N_MAX, r > BF_R_MAX),
  * BF_ERR_CUDA.
@@ -132,8 +134,12 @@ size_t bf_saved_bytes(int H, int W);
 bf_status bf_forward(const void* img, int H, int W, int r, float sigma_r, float T, int N,
                      float* out, const bf_opts* opts, void* saved, void* stream);
 
-/* Workspace bytes bf_backward needs for its dL/dsigma_r reduction. */
-size_t bf_backward_workspace_bytes(int H, int W, int r, const bf_opts* opts);
+/* Workspace bytes bf_backward needs for the same (H, W, r, sigma_r, T, N,
+   opts): the per-CTA dL/dsigma_r partial sums and, when the harmonics of q_N
+   run in several chunks (N > 43), two H x W float accumulators. 0 on bad
+   arguments. */
+size_t bf_backward_workspace_bytes(int H, int W, int r, float sigma_r, float T, int N,
+                                   const bf_opts* opts);
 
 /*
  * Adjoint of bf_forward for L with dL/dout = grad_out (derived from Eq.
@@ -146,7 +152,7 @@ size_t bf_backward_workspace_bytes(int H, int W, int r, const bf_opts* opts);
  *   grad_sigma    device pointer to ONE float receiving dL/dsigma_r, or NULL
  *                 (0 in BF_GAMMA_FIXED mode).
  *   workspace     device, >= bf_backward_workspace_bytes; may be NULL only if
- *                 grad_sigma is NULL.
+ *                 grad_sigma is NULL (or gamma is fixed) and N <= 43.
  * Same parameters (r, sigma_r, T, N, opts) as the forward call.
  */
 bf_status bf_backward(const void* img, const float* out, const float* grad_out,
@@ -172,10 +178,11 @@ bf_status bf_backward(const void* img, const float* out, const float* grad_out,
  * holds until the process exits.
  *
  * Arguments and results are those of bf_backward without workspace/ws_bytes.
- * Errors: as bf_backward, plus BF_ERR_UNSUPPORTED when the image needs more
- * partial slots than the array holds (bf_backward_workspace_bytes(H, W, r,
- * opts) > BF_NOALLOC_MAX_PARTIALS * sizeof(float)), checked before any
- * launch.
+ * Errors: as bf_backward, plus BF_ERR_UNSUPPORTED when the call needs more
+ * scratch than the array holds (bf_backward_workspace_bytes(H, W, r, sigma_r,
+ * T, N, opts) > BF_NOALLOC_MAX_PARTIALS * sizeof(float); this includes every
+ * N > 43, whose harmonic chunks need image-sized accumulators), checked
+ * before any launch.
  *
  * Set-up: the first call on each device looks up the array's device address
  * (cudaGetSymbolAddress, with that device current) and keeps it; make that

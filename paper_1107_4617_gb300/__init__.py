@@ -87,7 +87,8 @@ def load():
             "bf_saved_bytes": (c_size, [c_int, c_int]),
             "bf_forward": (c_int, [vp, c_int, c_int, c_int, c_float, c_float, c_int, vp, P_opts,
                                    vp, vp]),
-            "bf_backward_workspace_bytes": (c_size, [c_int, c_int, c_int, P_opts]),
+            "bf_backward_workspace_bytes": (c_size, [c_int, c_int, c_int, c_float, c_float, c_int,
+                                                     P_opts]),
             "bf_backward": (c_int, [vp, vp, vp, vp, c_int, c_int, c_int, c_float, c_float, c_int,
                                     vp, vp, vp, c_size, P_opts, vp]),
             "bf_batch_workspace_bytes": (c_size, [P_desc, c_int, P_opts]),
@@ -182,8 +183,10 @@ def bf_saved_bytes(H: int, W: int) -> int:
     return int(load().bf_saved_bytes(int(H), int(W)))
 
 
-def bf_backward_workspace_bytes(H: int, W: int, r: int, opts: BfOpts | None = None) -> int:
-    return int(load().bf_backward_workspace_bytes(int(H), int(W), int(r),
+def bf_backward_workspace_bytes(H: int, W: int, r: int, sigma_r: float = 0.2, T: float = 1.0,
+                                N: int = 0, opts: BfOpts | None = None) -> int:
+    return int(load().bf_backward_workspace_bytes(int(H), int(W), int(r), float(sigma_r),
+                                                  float(T), int(N),
                                                   ctypes.byref(opts) if opts else None))
 
 
@@ -308,9 +311,9 @@ def _make_function():
             gf = torch.empty((B, H, W), dtype=torch.float32, device=fb.device) if need_f else None
             gs = torch.zeros((B,), dtype=torch.float32, device=fb.device) if need_s else None
             ws = None
-            if need_s:
-                nb = bf_backward_workspace_bytes(H, W, r, opts)
-                ws = torch.empty((max(1, nb // 4),), dtype=torch.float32, device=fb.device)
+            nb = bf_backward_workspace_bytes(H, W, r, s, T, N, opts)
+            if nb > 0:
+                ws = torch.empty((max(1, (nb + 3) // 4),), dtype=torch.float32, device=fb.device)
             for b in range(B):
                 bf_backward(fb[b], out[b], g[b], saved[b], r, s, T, N,
                             grad_img=gf[b] if need_f else None,

@@ -96,12 +96,12 @@ static bf_status choose_tiles(int H, int W, int r, const bf_opts* o, Tiles* t) {
     return BF_OK;
 }
 
-// The skewed-strip engine serves r <= 32, K <= SYS_KMAX and plain (not
-// Kahan) sums; thread count 64, 96 or 128 (one thread per strip column,
-// Tw = Wi - 2r outputs). Bands: about two resident CTAs per SM.
-static bool sys_tiles(int H, int W, int r, int K, const bf_opts* o, Tiles* t) {
-    if (K > SYS_KMAX || (o && o->kahan)) return false;
-    int wi = 128;
+// The skewed-strip engine (bf_sys.cu) serves every request whose strip of
+// Wi threads keeps at least 16 output columns (Wi - 2r >= 16): 128-thread
+// strips for r <= 20 (two CTAs per SM), 256-thread strips above (one CTA per
+// SM, less halo). Bands: one wave of resident CTAs.
+static bool sys_tiles(int H, int W, int r, const bf_opts* o, Tiles* t) {
+    int wi = (r <= 20) ? 128 : 256;
     if (o && o->tile_w > 0) {
         if (o->tile_w > SYS_MAX_THREADS || o->tile_w % 32 != 0) return false;
         wi = o->tile_w;
@@ -113,7 +113,7 @@ static bool sys_tiles(int H, int W, int r, int K, const bf_opts* o, Tiles* t) {
     if (o && o->tile_h > 0) {
         t->Hb = o->tile_h;
     } else {
-        const int target = 2 * sm_count();
+        const int target = (wi <= 128 ? 2 : 1) * sm_count();
         int nb = (target + t->gx - 1) / t->gx;
         if (nb < 1) nb = 1;
         int hb = (H + nb - 1) / nb;
@@ -122,6 +122,20 @@ static bool sys_tiles(int H, int W, int r, int K, const bf_opts* o, Tiles* t) {
     }
     t->gy = (H + t->Hb - 1) / t->Hb;
     return true;
+}
+
+static void fill_sys(const FwdParams& p, SysParams* q) {
+    memset(q, 0, sizeof(*q));
+    q->img = p.img;
+    q->H = p.H; q->W = p.W; q->r = p.r; q->K = p.K; q->kstart = p.kstart;
+    q->Hb = 0; q->Tw = 0;
+    q->k0 = p.kstart;
+    q->gamma = p.gamma;
+    q->gpi = (float)((double)p.gamma / M_PI);
+    for (int i = 0; i < p.K; ++i) {
+        q->a[i] = p.a[i];
+        q->ak[i] = p.a[i] * (float)(p.kstart + 2 * i);
+    }
 }
 
 bf_status check_opts(const bf_opts* o) {
@@ -214,35 +228,58 @@ bf_status bf_forward(const void* img, int H, int W, int r, float sigma_r, float 
                                    &gx, &gy);
     if (st != BF_OK) return st;
     const int in_dtype = opts ? opts->in_dtype : BF_F32;
+    const bool kahan = opts && opts->kahan;
     Tiles t;
     cudaError_t e;
-    if (sys_tiles(H, W, r, p.K, opts, &t)) {
+    // harmonic chunks accumulate in the saved buffers, so chunking needs them
+    if (sys_tiles(H, W, r, opts, &t) && (sys_chunks(p.K, kahan) == 1 || saved)) {
         SysParams q;
-        memset(&q, 0, sizeof(q));
-        q.img = img; q.out = out;
+        fill_sys(p, &q);
+        q.out = out;
         q.sv_den = p.sv_den; q.sv_dnum = p.sv_dnum; q.sv_dden = p.sv_dden;
-        q.H = H; q.W = W; q.r = r; q.K = p.K; q.kstart = p.kstart; q.Hb = t.Hb; q.Tw = t.Tw;
-        q.gamma = p.gamma;
-        for (int i = 0; i < p.K; ++i) {
-            q.a[i] = p.a[i];
-            q.ak[i] = p.a[i] * (float)(p.kstart + 2 * i);
-        }
-        e = launch_sys(q, false, saved != nullptr, in_dtype, t.nt, t.gx, t.gy,
+        q.Hb = t.Hb; q.Tw = t.Tw;
+        e = launch_sys(q, saved ? 1 : 0, kahan, in_dtype, t.nt, t.gx, t.gy,
                        (cudaStream_t)stream);
     } else {
-        e = launch_forward(p, nt, opts ? opts->kahan : 0, in_dtype, (cudaStream_t)stream);
+        e = launch_forward(p, nt, kahan ? 1 : 0, in_dtype, (cudaStream_t)stream);
     }
     if (e != cudaSuccess) return set_cuda_error(e);
     return BF_OK;
 }
 
-size_t bf_backward_workspace_bytes(int H, int W, int r, const bf_opts* opts) {
-    if (H < 1 || W < 1 || r < 0 || r > BF_R_MAX) return 0;
-    Tiles t, u;
-    if (choose_tiles(H, W, r, opts, &t) != BF_OK) return 0;
-    size_t n = (size_t)t.gx * t.gy;
-    if (sys_tiles(H, W, r, 1, opts, &u) && (size_t)u.gx * u.gy > n) n = (size_t)u.gx * u.gy;
-    return n * sizeof(float);
+// Backward workspace layout: per-CTA partial sums, then (when the harmonics
+// run in chunks) two H x W float accumulators.
+struct BwdWs {
+    size_t partial_bytes, acc_offset, total;
+    bool chunked;
+};
+
+static bf_status bwd_ws(int H, int W, int r, int K, const bf_opts* opts, BwdWs* ws, Tiles* t,
+                        bool* use_sys) {
+    *use_sys = sys_tiles(H, W, r, opts, t);
+    if (!*use_sys) {
+        bf_status st = choose_tiles(H, W, r, opts, t);
+        if (st != BF_OK) return st;
+    }
+    ws->partial_bytes = (size_t)t->gx * t->gy * sizeof(float);
+    ws->chunked = *use_sys && sys_chunks(K, false) > 1;
+    ws->acc_offset = (ws->partial_bytes + 255) & ~(size_t)255;
+    ws->total = ws->chunked ? ws->acc_offset + 2 * (size_t)H * W * sizeof(float)
+                            : ws->partial_bytes;
+    return BF_OK;
+}
+
+size_t bf_backward_workspace_bytes(int H, int W, int r, float sigma_r, float T, int N,
+                                   const bf_opts* opts) {
+    if (H < 1 || W < 1 || check_opts(opts) != BF_OK) return 0;
+    const int gm = opts ? opts->gamma_mode : BF_GAMMA_FIXED;
+    Resolved rs;
+    if (resolve(r, sigma_r, T, N, gm, &rs) != BF_OK) return 0;
+    BwdWs ws;
+    Tiles t;
+    bool use_sys = false;
+    if (bwd_ws(H, W, r, rs.K, opts, &ws, &t, &use_sys) != BF_OK) return 0;
+    return ws.total;
 }
 
 bf_status bf_backward(const void* img, const float* out, const float* grad_out,
@@ -258,14 +295,12 @@ bf_status bf_backward(const void* img, const float* out, const float* grad_out,
     st = resolve(r, sigma_r, T, N, gm, &rs);
     if (st != BF_OK) return st;
     Tiles t;
-    const bool use_sys = sys_tiles(H, W, r, rs.K, opts, &t);
-    if (!use_sys) {
-        st = choose_tiles(H, W, r, opts, &t);
-        if (st != BF_OK) return st;
-    }
-    const size_t need = (size_t)t.gx * t.gy * sizeof(float);
-    if (grad_sigma && gm == BF_GAMMA_FROM_SIGMA && (!workspace || ws_bytes < need))
-        return BF_ERR_NOMEM;
+    BwdWs ws;
+    bool use_sys = false;
+    st = bwd_ws(H, W, r, rs.K, opts, &ws, &t, &use_sys);
+    if (st != BF_OK) return st;
+    const bool need_ws = ws.chunked || (grad_sigma && gm == BF_GAMMA_FROM_SIGMA);
+    if (need_ws && (!workspace || ws_bytes < ws.total)) return BF_ERR_NOMEM;
 
     cudaStream_t s = (cudaStream_t)stream;
     if (grad_sigma && gm == BF_GAMMA_FIXED) {
@@ -289,18 +324,23 @@ bf_status bf_backward(const void* img, const float* out, const float* grad_out,
     for (int i = 0; i < rs.K; ++i) p.a[i] = (float)rs.a[i];
     cudaError_t e;
     if (use_sys) {
+        FwdParams fp;
+        memset(&fp, 0, sizeof(fp));
+        fp.img = img; fp.H = H; fp.W = W; fp.r = r; fp.K = p.K; fp.kstart = p.kstart;
+        fp.gamma = p.gamma;
+        for (int i = 0; i < p.K; ++i) fp.a[i] = p.a[i];
         SysParams q;
-        memset(&q, 0, sizeof(q));
-        q.img = img; q.fout = out; q.gout = grad_out;
+        fill_sys(fp, &q);
+        q.fout = out; q.gout = grad_out;
         q.bden = p.sv_den; q.bdnum = p.sv_dnum; q.bdden = p.sv_dden;
         q.gimg = grad_img; q.partial = p.partial;
-        q.H = H; q.W = W; q.r = r; q.K = p.K; q.kstart = p.kstart; q.Hb = t.Hb; q.Tw = t.Tw;
-        q.gamma = p.gamma;
-        for (int i = 0; i < p.K; ++i) {
-            q.a[i] = p.a[i];
-            q.ak[i] = p.a[i] * (float)(p.kstart + 2 * i);
+        if (ws.chunked) {
+            float* acc = reinterpret_cast<float*>(static_cast<char*>(workspace) + ws.acc_offset);
+            q.acc_gv = acc;
+            q.acc_gt = acc + (size_t)H * W;
         }
-        e = launch_sys(q, true, false, opts ? opts->in_dtype : BF_F32, t.nt, t.gx, t.gy, s);
+        q.Hb = t.Hb; q.Tw = t.Tw;
+        e = launch_sys(q, 2, false, opts ? opts->in_dtype : BF_F32, t.nt, t.gx, t.gy, s);
     } else {
         e = launch_backward(p, t.nt, opts ? opts->in_dtype : BF_F32, s);
     }

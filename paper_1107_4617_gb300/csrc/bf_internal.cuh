@@ -48,8 +48,7 @@ struct BwdParams {
 
 // Skewed-strip engine (bf_sys.cu): forward and adjoint share one kernel
 // template. Up to SYS_KMAX harmonics are kept in registers (8 floats each).
-constexpr int SYS_KMAX = 21;
-constexpr int SYS_MAX_THREADS = 128;
+constexpr int SYS_MAX_THREADS = 256;
 
 struct SysParams {
     const void* img;
@@ -64,14 +63,32 @@ struct SysParams {
     const float* bdden;
     float* gimg;                // adjoint: dL/dimg (nullable)
     float* partial;             // adjoint: per-CTA sum of f * dL/dtheta (nullable)
+    float* acc_den;             // forward chunk accumulator for den when not saving
+    float* acc_gv;              // adjoint chunk accumulators (value and phase parts)
+    float* acc_gt;
     int H, W, r, K, kstart, Hb, Tw;
+    int k0;          // frequency of this launch's first harmonic
+    int acc;         // 0 all harmonics; 1 first, 2 middle, 3 last harmonic chunk
     float gamma;
-    float a[KCAP];   // a_k of harmonic i
+    float gpi;       // gamma / pi
+    float a[KCAP];   // a_k of harmonic i (of this chunk)
     float ak[KCAP];  // k * a_k (centre-derivative terms)
 };
 
-cudaError_t launch_sys(const SysParams& p, bool bwd, bool save, int in_dtype, int wi, int gx,
+// Largest harmonic pairs per launch (registers); more harmonics run in chunks.
+constexpr int SYS_KP_MAX = 11;
+constexpr int SYS_KP_KAHAN = 6;
+
+// mode: 0 forward, 1 forward + saved buffers, 2 adjoint.
+cudaError_t launch_sys(const SysParams& p, int mode, bool kahan, int in_dtype, int wi, int gx,
                        int gy, cudaStream_t s);
+int sys_chunks(int K, bool kahan);
+cudaError_t launch_sys_w128(const SysParams& p, int mode, int dtype, int kp, int wi, int gx,
+                            int gy, cudaStream_t s);
+cudaError_t launch_sys_w256(const SysParams& p, int mode, int dtype, int kp, int wi, int gx,
+                            int gy, cudaStream_t s);
+cudaError_t launch_sys_kahan(const SysParams& p, int mode, int dtype, int kp, int wi, int gx,
+                             int gy, cudaStream_t s);
 
 // One image of a batch as the persistent kernel sees it: its launch
 // parameters, its tile grid width and the index of its first tile.

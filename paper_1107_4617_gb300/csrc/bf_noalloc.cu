@@ -54,8 +54,8 @@ extern "C" bf_status bf_backward_noalloc(const void* img, const float* out,
                                          int r, float sigma_r, float T, int N, float* grad_img,
                                          float* grad_sigma, const bf_opts* opts, void* stream) {
     const size_t cap = sizeof(float) * (size_t)BF_NOALLOC_MAX_PARTIALS;
-    const size_t need = bf_backward_workspace_bytes(H, W, r, opts);
-    if (need > cap) return BF_ERR_UNSUPPORTED;  // image needs more partial slots than the array holds
+    const size_t need = bf_backward_workspace_bytes(H, W, r, sigma_r, T, N, opts);
+    if (need > cap) return BF_ERR_UNSUPPORTED;  // call needs more scratch than the array holds
     void* scratch = nullptr;
     bf_status st = scratch_address(&scratch);
     if (st != BF_OK) return st;

@@ -117,7 +117,22 @@ def test_backward_raw_abi_grad_sigma_fixed_is_zero(cuda_lib):
     out = bf.bf_forward(f, 3, 0.2, 1.0, 0, opts=opts, saved=sv)
     g = torch.ones_like(out)
     gs = torch.full((1,), 7.0, device="cuda")
-    ws = torch.empty((bf.bf_backward_workspace_bytes(H, W, 3) // 4 + 1,), device="cuda")
+    ws = torch.empty((bf.bf_backward_workspace_bytes(H, W, 3, 0.2, 1.0, 0) // 4 + 1,), device="cuda")
     bf.bf_backward(f, out, g, sv, 3, 0.2, 1.0, 0, grad_img=None, grad_sigma=gs, workspace=ws)
     torch.cuda.synchronize()
     assert float(gs) == 0.0
+
+
+@pytest.mark.parametrize("H,W,r,sigma", [(70, 90, 5, 0.085), (50, 300, 30, 0.2)])
+def test_grad_chunked_and_wide(cuda_lib, H, W, r, sigma):
+    """N > 43 (harmonic chunks with workspace accumulators) and r = 30
+    (256-thread strips) through the autograd wrapper."""
+    bf = cuda_lib
+    f = synth.rectangles(H, W, seed=H * 7 + W)
+    w = synth.weights((H, W), seed=3)
+    ft = torch.from_numpy(f).cuda().requires_grad_(True)
+    out = bf.bilateral(ft, r, sigma, 1.0)
+    (torch.from_numpy(w).cuda() * out).sum().backward()
+    N = oracle.resolve_N(sigma, 1.0)
+    gref, _ = oracle.bilateral_grad(f.astype(np.float64), w.astype(np.float64), r, math.pi / 2, N)
+    check_grad(ft.grad.cpu().numpy(), gref)

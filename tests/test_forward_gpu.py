@@ -158,3 +158,35 @@ def test_full_size_sampled_headline(cuda_lib):
     assert sv[0].min() >= 1.0 - 1e-4
     assert np.isfinite(got).all()
 
+
+
+@pytest.mark.parametrize("N", [44, 50, 64])
+def test_chunked_harmonics_with_saved(cuda_lib, N):
+    """N > 43 runs the harmonics in chunks that accumulate in the saved
+    buffers; result, den and the centre derivatives match a single pass."""
+    f = synth.rectangles(150, 170, seed=N)
+    got, sv = run_fwd(cuda_lib, f, 6, 0.2, 1.0, N, saved=True)
+    ref, den = oracle_ref(f, 6, 0.2, 1.0, N)
+    assert rel_err(got, ref).max() <= TOL
+    np.testing.assert_allclose(sv[0], den, rtol=2e-5, atol=0)
+
+
+@pytest.mark.parametrize("r", [21, 30, 45, 56])
+def test_wide_strips_large_r(cuda_lib, r):
+    """r > 20 takes 256-thread strips (less halo)."""
+    f = synth.sinusoids(260, 333, seed=r)
+    got = run_fwd(cuda_lib, f, r, 0.1, 1.0, 0)
+    ref, _ = oracle_ref(f, r, 0.1, 1.0, 0)
+    assert rel_err(got, ref).max() <= TOL
+
+
+@pytest.mark.parametrize("saved", [False, True])
+def test_kahan_precision_form(cuda_lib, saved):
+    """Kahan-compensated running sums at r=30, N=41 (the precision workload's
+    parameters) on a tall image: with saved buffers the compensated skewed-strip
+    engine (harmonic chunks), without them the single-pass kernel."""
+    f = synth.rectangles(900, 140, seed=21)
+    res = run_fwd(cuda_lib, f, 30, 0.1, 1.0, 0, kahan=True, saved=saved, tile_h=900)
+    got = res[0] if saved else res
+    ref, _ = oracle_ref(f, 30, 0.1, 1.0, 0)
+    assert rel_err(got, ref).max() <= TOL

@@ -37,7 +37,7 @@ def _reference(bf, f, g, out, sv, r, sigma, N, opts):
     H, W = f.shape
     gi = torch.empty_like(f)
     gs = torch.zeros((1,), device=f.device)
-    ws = torch.empty((bf.bf_backward_workspace_bytes(H, W, r, opts) // 4 + 1,), device=f.device)
+    ws = torch.empty((bf.bf_backward_workspace_bytes(H, W, r, sigma, 1.0, N, opts) // 4 + 1,), device=f.device)
     bf.bf_backward(f, out, g, sv, r, sigma, 1.0, N, grad_img=gi, grad_sigma=gs, workspace=ws,
                    opts=opts)
     return gi, gs
@@ -85,7 +85,7 @@ def test_noalloc_rejects_oversize(cuda_lib):
     # a grid with more CTAs than the fixed array holds partial slots (checked
     # before any launch: the pointers are never dereferenced)
     o = bf._opts(gamma_mode=bf.GAMMA_FROM_SIGMA, tile_h=16, tile_w=64)
-    need = bf.bf_backward_workspace_bytes(1 << 20, 4096, 10, o)
+    need = bf.bf_backward_workspace_bytes(1 << 20, 4096, 10, 0.2, 1.0, 0, o)
     assert need > 4 * 16384
     vp = ctypes.c_void_p
     fn = lib.bf_backward_noalloc
