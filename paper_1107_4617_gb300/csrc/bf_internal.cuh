@@ -112,6 +112,40 @@ struct BatchTable {
     BatchImage img[1];  // n_images entries
 };
 
+// Batch on the skewed-strip engine: per image up to two harmonic chunks
+// (K <= 33), each with its own launch parameters (coefficients of that chunk,
+// first frequency, accumulation mode).
+constexpr int SYS_BATCH_MAX_CHUNKS = 2;
+
+struct SysBatchImage {
+    SysParams ch[SYS_BATCH_MAX_CHUNKS];
+    int kp[SYS_BATCH_MAX_CHUNKS];  // harmonic-pair instantiation of each chunk
+    int nch;
+    int gx;
+    int first_tile;
+    int n_tiles;
+};
+
+// Work of one persistent launch (one strip width): image range and tiles.
+struct SysBatchGroup {
+    int n_tiles;
+    int img0;       // first image of the group in the image array
+    int n_images;
+    int wi;         // threads per strip
+};
+
+struct SysBatchTable {
+    int counters[4];  // next tile of each group (reset by every launch)
+    int magic;
+    int in_dtype;
+    int pad[2];
+    SysBatchGroup g[2];  // 128-thread and 256-thread strips
+    SysBatchImage img[1];  // all images, group 0 first
+};
+
+cudaError_t launch_sys_batch(SysBatchTable* tab, int group, int wi, int grid, int in_dtype,
+                             cudaStream_t s);
+
 // Host-side parameter preparation shared by the entry points.
 struct Resolved {
     int N, K, kstart;

@@ -77,3 +77,23 @@ def test_batch_validation_rejects_bad_descriptor(cuda_lib):
     small = torch.empty((4,), device="cuda")
     with pytest.raises(bf.BfError):
         bf.bf_batch(descs, small)
+
+
+def test_batch_kahan_and_bf16(cuda_lib):
+    """Kahan-compensated batch (single-pass kernel queue) and a BF16-input
+    batch (skewed-strip engine) against the oracle."""
+    bf = cuda_lib
+    specs = synth.batch_specs(6, seed=9, side_lo=20, side_hi=160)
+    for opts, dt in [(bf._opts(kahan=True), torch.float32), (bf._opts(in_dtype=bf.BF16), torch.bfloat16)]:
+        imgs = [torch.from_numpy(synth.rectangles(s["H"], s["W"], seed=s["seed"])).cuda().to(dt)
+                for s in specs]
+        outs = [torch.full(im.shape, -7.0, device="cuda") for im in imgs]
+        descs = bf.make_descs(imgs, outs, [s["r"] for s in specs], [s["sigma_r"] for s in specs])
+        ws = torch.empty((bf.bf_batch_workspace_bytes(descs, opts) // 4 + 1,), device="cuda")
+        bf.bf_batch(descs, ws, opts)
+        torch.cuda.synchronize()
+        for s, im, o in zip(specs, imgs, outs):
+            N = oracle.resolve_N(s["sigma_r"], 1.0)
+            ref = oracle.bilateral(im.float().cpu().numpy().astype(np.float64), s["r"], math.pi / 2, N)
+            e = np.abs(o.cpu().numpy() - ref) / np.maximum(np.abs(ref), 1e-2)
+            assert e.max() <= 1e-4, (s, e.max())
