@@ -39,6 +39,9 @@ UNIT = "Mpixel/s"
 SMS, LANES, FMAX_GHZ = 152, 128, 2.070
 FP32_PEAK_TFLOPS = SMS * LANES * 2 * FMAX_GHZ / 1e3
 L2_FLUSH_BYTES = 256 << 20
+# kernels the bench's two launches run (N = 41 -> 11 harmonic pairs, 128-thread strips)
+FWD_KERNEL = "bf_sys_kernel<11, 0, 1, 0, 128, float> (forward, saved buffers)"
+ADJ_KERNEL = "bf_sys_kernel<11, 1, 0, 0, 128, float> (adjoint)"
 
 
 def fwd_flops_per_px(N: int) -> int:
@@ -154,6 +157,160 @@ def cpu_baseline(sample_rows: int = 512):
         f"({sample_rows}x{W} px) of the 4096x4096 r=10 N=41 workload, {dt:.1f} s")
 
 
+def _time_ms(fn, flush, stream, reps=3):
+    """Median device time of fn() over reps calls, L2 flushed before each."""
+    import torch
+    ts = []
+    for _ in range(reps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    ts.sort()
+    return ts[len(ts) // 2]
+
+
+def _err_stats(got, ref, T=1.0):
+    import numpy as np
+    got = np.asarray(got, np.float64)
+    ref = np.asarray(ref, np.float64)
+    d = np.abs(got - ref)
+    rel = d / np.maximum(np.abs(ref), 1e-2 * T)
+    return {"max_abs": float(d.max()), "mean_abs": float(d.mean()), "max_rel": float(rel.max()),
+            "samples": int(d.size)}
+
+
+def extras(dev, flush, stream):
+    """The precision, batching and differentiation workloads, each timed on the
+    device and checked against the FP64 oracle on sampled pixels."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import paper_1107_4617_gb300 as bf
+    from paper_1107_4617_gb300 import synth
+    res = {}
+    rng = np.random.default_rng(7)
+
+    # precision: 8192^2, r=30, sigma_r=0.1 (N=41): plain / Kahan / BF16-stored input
+    Hp = 8192
+    f_np = synth.rectangles(Hp, Hp, seed=0)
+    img = torch.from_numpy(f_np).to(dev)
+    img16 = img.to(torch.bfloat16)
+    out = torch.empty_like(img)
+    sv = torch.empty((3, Hp, Hp), device=dev)
+    N = bf.bf_resolve_N(0.1, 1.0)
+    idx = rng.integers(0, Hp * Hp, 256)
+    ref = oracle.bilateral_points(f_np.astype(np.float64), 30, oracle.gamma_fixed(1.0), N, idx)
+    f16 = img16.float().cpu().numpy()
+    ref16 = oracle.bilateral_points(f16.astype(np.float64), 30, oracle.gamma_fixed(1.0), N, idx)
+    prec = {}
+    for name, x, opts, saved, r_ in [
+            ("plain", img, bf._opts(), None, ref),
+            ("kahan", img, bf._opts(kahan=True, save=True), sv, ref),
+            ("bf16_input", img16, bf._opts(in_dtype=bf.BF16), None, ref16)]:
+        call = lambda: bf.bf_forward(x, 30, 0.1, 1.0, N, out=out, opts=opts, saved=saved,
+                                     stream=stream)
+        call()
+        ms = _time_ms(call, flush, stream)
+        got = out.cpu().numpy().ravel()[idx]
+        e = _err_stats(got, r_)
+        if name == "bf16_input":
+            e["vs_fp64_of_fp32_image"] = _err_stats(got, ref)
+        prec[name] = {"ms": ms, "mpx_s": Hp * Hp / ms / 1e3, "err_vs_fp64": e}
+    res["precision_8192sq_r30_N41"] = prec
+    del img, img16, out, sv
+
+    # batching: 256 uneven images, one graph-replayed persistent launch vs 256 launches
+    specs = synth.batch_specs(256, seed=7)
+    imgs = [torch.from_numpy(synth.rectangles(sp["H"], sp["W"], seed=sp["seed"])).to(dev)
+            for sp in specs]
+    outs = [torch.empty_like(im) for im in imgs]
+    descs = bf.make_descs(imgs, outs, [sp["r"] for sp in specs], [sp["sigma_r"] for sp in specs])
+    opts = bf._opts()
+    ws = torch.empty(((bf.bf_batch_workspace_bytes(descs, opts) + 3) // 4,), device=dev)
+    bs = torch.cuda.Stream(device=dev)  # graph capture needs a non-default stream
+    torch.cuda.synchronize()
+    with torch.cuda.stream(bs):
+        bf.bf_batch_prepare(descs, ws, opts, stream=bs)
+        bf.bf_batch_launch(ws, opts, stream=bs)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=bs):
+            bf.bf_batch_launch(ws, opts, stream=bs)
+        px = sum(sp["H"] * sp["W"] for sp in specs)
+        ms_graph = _time_ms(lambda: g.replay(), flush, bs)
+
+    def separate():
+        for sp, im, o in zip(specs, imgs, outs):
+            bf.bf_forward(im, sp["r"], sp["sigma_r"], 1.0, 0, out=o, stream=stream)
+    separate()
+    ms_sep = _time_ms(separate, flush, stream)
+    with torch.cuda.stream(bs):
+        g.replay()
+    torch.cuda.synchronize()
+    errs = []
+    for k in rng.choice(len(specs), 8, replace=False):
+        sp = specs[int(k)]
+        n = sp["H"] * sp["W"]
+        ii = rng.integers(0, n, 64)
+        rr = oracle.bilateral_points(imgs[k].cpu().numpy().astype(np.float64), sp["r"],
+                                     oracle.gamma_fixed(1.0), oracle.resolve_N(sp["sigma_r"], 1.0), ii)
+        errs.append(_err_stats(outs[k].cpu().numpy().ravel()[ii], rr))
+    res["batch_256_uneven"] = {
+        "megapixels": px / 1e6, "persistent_graph_ms": ms_graph,
+        "persistent_graph_mpx_s": px / ms_graph / 1e3, "separate_launches_ms": ms_sep,
+        "separate_launches_mpx_s": px / ms_sep / 1e3,
+        "err_vs_fp64": {"max_rel": max(e["max_rel"] for e in errs),
+                        "max_abs": max(e["max_abs"] for e in errs), "images_checked": len(errs)}}
+    del imgs, outs, ws, g
+
+    # differentiation: 16 x 512^2, r=7, sigma_r=0.15 (N=19), L = sum(w * out)
+    B, Hd, r = 16, 512, 7
+    fb = np.stack([synth.rectangles(Hd, Hd, seed=100 + b) for b in range(B)])
+    wb = synth.weights((B, Hd, Hd), seed=1)
+    ft = torch.from_numpy(fb).to(dev)
+    wt = torch.from_numpy(wb).to(dev)
+    Nd = bf.bf_resolve_N(0.15, 1.0)
+    outd = torch.empty_like(ft)
+    svd = torch.empty((B, 3, Hd, Hd), device=dev)
+    gi = torch.empty_like(ft)
+    sopt = bf._opts(save=True)
+
+    def fwd_bwd():
+        for b in range(B):
+            bf.bf_forward(ft[b], r, 0.15, 1.0, Nd, out=outd[b], opts=sopt, saved=svd[b], stream=stream)
+            bf.bf_backward(ft[b], outd[b], wt[b], svd[b], r, 0.15, 1.0, Nd, grad_img=gi[b],
+                           opts=sopt, stream=stream)
+    fwd_bwd()
+    ms_d = _time_ms(fwd_bwd, flush, stream)
+    # gradient at sampled pixels vs central differences of the FP64 oracle on a crop
+    gg = gi.cpu().numpy()
+    gerr = 0.0
+    for _ in range(6):
+        b, y, x = int(rng.integers(0, B)), int(rng.integers(0, Hd)), int(rng.integers(0, Hd))
+        y0, y1 = max(0, y - 2 * r), min(Hd, y + 2 * r + 1)
+        x0, x1 = max(0, x - 2 * r), min(Hd, x + 2 * r + 1)
+        sub = fb[b, y0:y1, x0:x1].astype(np.float64)
+        wsub = wb[b, y0:y1, x0:x1].astype(np.float64)
+        mask = np.zeros_like(sub)
+        mask[max(0, y - r) - y0:min(Hd, y + r + 1) - y0, max(0, x - r) - x0:min(Hd, x + r + 1) - x0] = 1
+        h = 1e-4
+        sp_, sm_ = sub.copy(), sub.copy()
+        sp_[y - y0, x - x0] += h
+        sm_[y - y0, x - x0] -= h
+        fd = (np.sum(mask * wsub * oracle.bilateral(sp_, r, oracle.gamma_fixed(1.0), Nd)) -
+              np.sum(mask * wsub * oracle.bilateral(sm_, r, oracle.gamma_fixed(1.0), Nd))) / (2 * h)
+        gerr = max(gerr, abs(gg[b, y, x] - fd) / max(1.0, abs(fd)))
+    res["differentiation_16x512sq_r7_N19"] = {
+        "fwd_bwd_ms": ms_d, "fwd_bwd_mpx_s": B * Hd * Hd / ms_d / 1e3,
+        "grad_max_rel_err_vs_fp64_fd": gerr}
+    return res
+
+
 def run_reference(args, rank, world):
     """Reference arm: the FP64 oracle as it stands, on host cores, timed on a
     bounded band of the workload per step."""
@@ -192,6 +349,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ref-rows", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the precision / batching / differentiation workloads")
     ap.add_argument("--kernels-only", action="store_true",
                     help="time the device step only (no e2e, N=40, CPU or accuracy legs); "
                          "used for profiler captures")
@@ -351,20 +510,27 @@ def main():
     per_launch_fwd = t_fwd / args.steps
     per_launch_bwd = t_bwd / args.steps
     if t_bwd >= t_fwd:
-        kname, flops, dur = "bf_bwd_strip_kernel", bwd_flops_per_px(N) * px, per_launch_bwd
+        kname, flops, dur = ADJ_KERNEL, bwd_flops_per_px(N) * px, per_launch_bwd
     else:
-        kname, flops, dur = "bf_fwd_strip_kernel", fwd_flops_per_px(N) * px, per_launch_fwd
+        kname, flops, dur = FWD_KERNEL, fwd_flops_per_px(N) * px, per_launch_fwd
     achieved = flops / dur / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP32_PEAK_TFLOPS, "traffic": load_traffic(kname),
                 "kernel": kname,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz",
-                "fwd": {"tflops": fwd_flops_per_px(N) * px / per_launch_fwd / 1e12,
+                "fwd": {"kernel": FWD_KERNEL, "traffic": load_traffic(FWD_KERNEL),
+                        "tflops": fwd_flops_per_px(N) * px / per_launch_fwd / 1e12,
                         "frac": fwd_flops_per_px(N) * px / per_launch_fwd / 1e12 / FP32_PEAK_TFLOPS,
                         "ms": per_launch_fwd * 1e3},
-                "bwd": {"tflops": bwd_flops_per_px(N) * px / per_launch_bwd / 1e12,
+                "bwd": {"kernel": ADJ_KERNEL, "traffic": load_traffic(ADJ_KERNEL),
+                        "tflops": bwd_flops_per_px(N) * px / per_launch_bwd / 1e12,
                         "frac": bwd_flops_per_px(N) * px / per_launch_bwd / 1e12 / FP32_PEAK_TFLOPS,
                         "ms": per_launch_bwd * 1e3}}
+
+    extra = None
+    if rank == 0 and world == 1 and not args.no_extras:
+        del h_img, h_g, h_out, h_gimg
+        extra = extras(dev, flush, stream)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -389,6 +555,7 @@ def main():
             "roofline": roofline,
             "cpu_baseline": cpu,
             "max_err_vs_fp64": err,
+            "workloads": extra,
         }
         print(json.dumps(line), flush=True)
     if dist:
