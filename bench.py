@@ -280,11 +280,10 @@ def extras(dev, flush, stream):
     gi = torch.empty_like(ft)
     sopt = bf._opts(save=True)
 
-    def fwd_bwd():
-        for b in range(B):
-            bf.bf_forward(ft[b], r, 0.15, 1.0, Nd, out=outd[b], opts=sopt, saved=svd[b], stream=stream)
-            bf.bf_backward(ft[b], outd[b], wt[b], svd[b], r, 0.15, 1.0, Nd, grad_img=gi[b],
-                           opts=sopt, stream=stream)
+    def fwd_bwd():  # one [B, H, W] launch each for the forward and the adjoint
+        bf.bf_forward3d(ft, r, 0.15, 1.0, Nd, out=outd, opts=sopt, saved=svd, stream=stream)
+        bf.bf_backward3d(ft, outd, wt, svd, r, 0.15, 1.0, Nd, grad_img=gi, opts=sopt,
+                         stream=stream)
     fwd_bwd()
     ms_d = _time_ms(fwd_bwd, flush, stream)
     # gradient at sampled pixels vs central differences of the FP64 oracle on a crop

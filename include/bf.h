@@ -160,6 +160,29 @@ bf_status bf_backward(const void* img, const float* out, const float* grad_out,
                       float* grad_img, float* grad_sigma, void* workspace, size_t ws_bytes,
                       const bf_opts* opts, void* stream);
 
+/*
+ * bf_forward over B images of equal size in one launch: img, out are
+ * contiguous [B, H, W] arrays (dtype as in bf_forward), saved (NULL or
+ * B * bf_saved_bytes(H, W)) is [B][3][H][W]. Same parameters, errors and
+ * precondition as bf_forward, for every image.
+ */
+bf_status bf_forward3d(const void* img, int B, int H, int W, int r, float sigma_r, float T, int N,
+                       float* out, const bf_opts* opts, void* saved, void* stream);
+
+/* Workspace bytes of bf_backward3d (B images of H x W). */
+size_t bf_backward3d_workspace_bytes(int B, int H, int W, int r, float sigma_r, float T, int N,
+                                     const bf_opts* opts);
+
+/*
+ * bf_backward over B images in one launch ([B, H, W] arrays, saved as written
+ * by bf_forward3d). grad_sigma receives ONE float: dL/dsigma_r summed over
+ * the B images. Same errors as bf_backward.
+ */
+bf_status bf_backward3d(const void* img, const float* out, const float* grad_out,
+                        const void* saved, int B, int H, int W, int r, float sigma_r, float T,
+                        int N, float* grad_img, float* grad_sigma, void* workspace,
+                        size_t ws_bytes, const bf_opts* opts, void* stream);
+
 /* Capacity of the fixed scratch array bf_backward_noalloc uses: this many
    per-CTA partial sums (64 KiB per device). */
 #define BF_NOALLOC_MAX_PARTIALS 16384

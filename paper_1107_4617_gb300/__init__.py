@@ -19,7 +19,8 @@ import threading
 
 __all__ = [
     "BfError", "BfOpts", "BfDesc", "load", "lib_path",
-    "bf_forward", "bf_backward", "bf_batch", "bf_batch_prepare", "bf_batch_launch",
+    "bf_forward", "bf_backward", "bf_forward3d", "bf_backward3d", "bf_batch", "bf_batch_prepare",
+    "bf_batch_launch", "bf_backward3d_workspace_bytes",
     "bf_resolve_N", "bf_coeffs", "bf_gamma", "bf_saved_bytes", "bf_backward_workspace_bytes",
     "bf_batch_workspace_bytes", "bf_status_string", "bf_last_cuda_error", "bilateral",
     "GAMMA_FIXED", "GAMMA_FROM_SIGMA", "F32", "BF16", "N_MAX", "R_MAX",
@@ -89,6 +90,12 @@ def load():
                                    vp, vp]),
             "bf_backward_workspace_bytes": (c_size, [c_int, c_int, c_int, c_float, c_float, c_int,
                                                      P_opts]),
+            "bf_backward3d_workspace_bytes": (c_size, [c_int, c_int, c_int, c_int, c_float,
+                                                       c_float, c_int, P_opts]),
+            "bf_forward3d": (c_int, [vp, c_int, c_int, c_int, c_int, c_float, c_float, c_int, vp,
+                                     P_opts, vp, vp]),
+            "bf_backward3d": (c_int, [vp, vp, vp, vp, c_int, c_int, c_int, c_int, c_float, c_float,
+                                      c_int, vp, vp, vp, c_size, P_opts, vp]),
             "bf_backward": (c_int, [vp, vp, vp, vp, c_int, c_int, c_int, c_float, c_float, c_int,
                                     vp, vp, vp, c_size, P_opts, vp]),
             "bf_batch_workspace_bytes": (c_size, [P_desc, c_int, P_opts]),
@@ -235,6 +242,52 @@ def bf_backward(img, out, grad_out, saved, r: int, sigma_r: float, T: float = 1.
     _check("bf_backward", st)
 
 
+def bf_backward3d_workspace_bytes(B: int, H: int, W: int, r: int, sigma_r: float = 0.2,
+                                  T: float = 1.0, N: int = 0, opts: BfOpts | None = None) -> int:
+    return int(load().bf_backward3d_workspace_bytes(int(B), int(H), int(W), int(r),
+                                                    float(sigma_r), float(T), int(N),
+                                                    ctypes.byref(opts) if opts else None))
+
+
+def bf_forward3d(img, r: int, sigma_r: float, T: float = 1.0, N: int = 0, out=None,
+                 opts: BfOpts | None = None, saved=None, stream=None):
+    """Forward filter of a [B, H, W] CUDA tensor in one launch -> float32."""
+    import torch
+    if img.dim() != 3:
+        raise ValueError("img must be 3-D (B, H, W)")
+    B, H, W = img.shape
+    if opts is None:
+        opts = _opts(in_dtype=_in_dtype(img))
+    elif opts.in_dtype != _in_dtype(img):
+        raise ValueError("opts.in_dtype does not match img.dtype")
+    if out is None:
+        out = torch.empty((B, H, W), dtype=torch.float32, device=img.device)
+    st = load().bf_forward3d(_dptr(img, "img"), B, H, W, int(r), float(sigma_r), float(T), int(N),
+                             _dptr(out, "out"), ctypes.byref(opts),
+                             _dptr(saved, "saved") if saved is not None else None,
+                             _stream_handle(stream))
+    _check("bf_forward3d", st)
+    return out
+
+
+def bf_backward3d(img, out, grad_out, saved, r: int, sigma_r: float, T: float = 1.0, N: int = 0,
+                  grad_img=None, grad_sigma=None, workspace=None, opts: BfOpts | None = None,
+                  stream=None):
+    """Adjoint of bf_forward3d; grad_sigma (1,) receives the sum over images."""
+    B, H, W = img.shape
+    if opts is None:
+        opts = _opts(in_dtype=_in_dtype(img))
+    ws_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    st = load().bf_backward3d(_dptr(img, "img"), _dptr(out, "out"), _dptr(grad_out, "grad_out"),
+                              _dptr(saved, "saved"), B, H, W, int(r), float(sigma_r), float(T),
+                              int(N),
+                              _dptr(grad_img, "grad_img") if grad_img is not None else None,
+                              _dptr(grad_sigma, "grad_sigma") if grad_sigma is not None else None,
+                              _dptr(workspace, "workspace") if workspace is not None else None,
+                              ws_bytes, ctypes.byref(opts), _stream_handle(stream))
+    _check("bf_backward3d", st)
+
+
 def make_descs(imgs, outs, rs, sigmas, T=1.0, Ns=None):
     descs = []
     for i, (im, o) in enumerate(zip(imgs, outs)):
@@ -292,8 +345,7 @@ def _make_function():
             opts = _opts(kahan=kahan, gamma_mode=gamma_mode, in_dtype=_in_dtype(fb), save=True)
             out = torch.empty((B, H, W), dtype=torch.float32, device=f.device)
             saved = torch.empty((B, 3, H, W), dtype=torch.float32, device=f.device)
-            for b in range(B):
-                bf_forward(fb[b], r, s, T, N, out=out[b], opts=opts, saved=saved[b])
+            bf_forward3d(fb, r, s, T, N, out=out, opts=opts, saved=saved)
             ctx.save_for_backward(fb, out, saved)
             ctx.cfg = (r, s, T, N, kahan, gamma_mode, squeeze)
             return out[0] if squeeze else out
@@ -309,20 +361,17 @@ def _make_function():
             need_f = ctx.needs_input_grad[0]
             need_s = ctx.needs_input_grad[1]
             gf = torch.empty((B, H, W), dtype=torch.float32, device=fb.device) if need_f else None
-            gs = torch.zeros((B,), dtype=torch.float32, device=fb.device) if need_s else None
+            gs = torch.zeros((1,), dtype=torch.float32, device=fb.device) if need_s else None
             ws = None
-            nb = bf_backward_workspace_bytes(H, W, r, s, T, N, opts)
+            nb = bf_backward3d_workspace_bytes(B, H, W, r, s, T, N, opts)
             if nb > 0:
                 ws = torch.empty((max(1, (nb + 3) // 4),), dtype=torch.float32, device=fb.device)
-            for b in range(B):
-                bf_backward(fb[b], out[b], g[b], saved[b], r, s, T, N,
-                            grad_img=gf[b] if need_f else None,
-                            grad_sigma=gs[b:b + 1] if need_s else None,
-                            workspace=ws, opts=opts)
+            bf_backward3d(fb, out, g, saved, r, s, T, N, grad_img=gf, grad_sigma=gs,
+                          workspace=ws, opts=opts)
             if gf is not None:
                 gf = gf[0] if squeeze else gf
                 gf = gf.to(fb.dtype)
-            gsig = gs.sum() if gs is not None else None
+            gsig = gs[0] if gs is not None else None
             return gf, gsig, None, None, None, None, None
 
     return BilateralCosN

@@ -220,17 +220,20 @@ size_t bf_saved_bytes(int H, int W) {
     return (size_t)3 * (size_t)H * (size_t)W * sizeof(float);
 }
 
-bf_status bf_forward(const void* img, int H, int W, int r, float sigma_r, float T, int N,
-                     float* out, const bf_opts* opts, void* saved, void* stream) {
+static bf_status forward_impl(const void* img, int B, int H, int W, int r, float sigma_r,
+                              float T, int N, float* out, const bf_opts* opts, void* saved,
+                              void* stream) {
+    if (B < 1) return BF_ERR_INVALID_ARG;
     FwdParams p;
     int nt = 0, gx = 0, gy = 0;
     bf_status st = fill_fwd_params(img, out, saved, H, W, r, sigma_r, T, N, opts, &p, &nt,
                                    &gx, &gy);
     if (st != BF_OK) return st;
     const int in_dtype = opts ? opts->in_dtype : BF_F32;
+    const size_t esz = in_dtype == BF_BF16 ? 2 : 4;
     const bool kahan = opts && opts->kahan;
     Tiles t;
-    cudaError_t e;
+    cudaError_t e = cudaSuccess;
     // harmonic chunks accumulate in the saved buffers, so chunking needs them
     if (sys_tiles(H, W, r, opts, &t) && (sys_chunks(p.K, kahan) == 1 || saved)) {
         SysParams q;
@@ -238,10 +241,22 @@ bf_status bf_forward(const void* img, int H, int W, int r, float sigma_r, float 
         q.out = out;
         q.sv_den = p.sv_den; q.sv_dnum = p.sv_dnum; q.sv_dden = p.sv_dden;
         q.Hb = t.Hb; q.Tw = t.Tw;
+        q.B = B;
         e = launch_sys(q, saved ? 1 : 0, kahan, in_dtype, t.nt, t.gx, t.gy,
                        (cudaStream_t)stream);
     } else {
-        e = launch_forward(p, nt, kahan ? 1 : 0, in_dtype, (cudaStream_t)stream);
+        const size_t hw = (size_t)H * W;
+        for (int b = 0; b < B && e == cudaSuccess; ++b) {
+            FwdParams pb = p;
+            pb.img = static_cast<const char*>(img) + b * hw * esz;
+            pb.out = out + b * hw;
+            if (saved) {
+                pb.sv_den = p.sv_den + b * 3 * hw;
+                pb.sv_dnum = p.sv_dnum + b * 3 * hw;
+                pb.sv_dden = p.sv_dden + b * 3 * hw;
+            }
+            e = launch_forward(pb, nt, kahan ? 1 : 0, in_dtype, (cudaStream_t)stream);
+        }
     }
     if (e != cudaSuccess) return set_cuda_error(e);
     return BF_OK;
@@ -254,39 +269,39 @@ struct BwdWs {
     bool chunked;
 };
 
-static bf_status bwd_ws(int H, int W, int r, int K, const bf_opts* opts, BwdWs* ws, Tiles* t,
-                        bool* use_sys) {
+static bf_status bwd_ws(int B, int H, int W, int r, int K, const bf_opts* opts, BwdWs* ws,
+                        Tiles* t, bool* use_sys) {
     *use_sys = sys_tiles(H, W, r, opts, t);
     if (!*use_sys) {
         bf_status st = choose_tiles(H, W, r, opts, t);
         if (st != BF_OK) return st;
     }
-    ws->partial_bytes = (size_t)t->gx * t->gy * sizeof(float);
+    ws->partial_bytes = (size_t)t->gx * t->gy * B * sizeof(float);
     ws->chunked = *use_sys && sys_chunks(K, false) > 1;
     ws->acc_offset = (ws->partial_bytes + 255) & ~(size_t)255;
-    ws->total = ws->chunked ? ws->acc_offset + 2 * (size_t)H * W * sizeof(float)
+    ws->total = ws->chunked ? ws->acc_offset + 2 * (size_t)B * H * W * sizeof(float)
                             : ws->partial_bytes;
     return BF_OK;
 }
 
-size_t bf_backward_workspace_bytes(int H, int W, int r, float sigma_r, float T, int N,
-                                   const bf_opts* opts) {
-    if (H < 1 || W < 1 || check_opts(opts) != BF_OK) return 0;
+static size_t backward_ws_impl(int B, int H, int W, int r, float sigma_r, float T, int N,
+                               const bf_opts* opts) {
+    if (B < 1 || H < 1 || W < 1 || check_opts(opts) != BF_OK) return 0;
     const int gm = opts ? opts->gamma_mode : BF_GAMMA_FIXED;
     Resolved rs;
     if (resolve(r, sigma_r, T, N, gm, &rs) != BF_OK) return 0;
     BwdWs ws;
     Tiles t;
     bool use_sys = false;
-    if (bwd_ws(H, W, r, rs.K, opts, &ws, &t, &use_sys) != BF_OK) return 0;
+    if (bwd_ws(B, H, W, r, rs.K, opts, &ws, &t, &use_sys) != BF_OK) return 0;
     return ws.total;
 }
 
-bf_status bf_backward(const void* img, const float* out, const float* grad_out,
-                      const void* saved, int H, int W, int r, float sigma_r, float T, int N,
-                      float* grad_img, float* grad_sigma, void* workspace, size_t ws_bytes,
-                      const bf_opts* opts, void* stream) {
-    if (!img || !out || !grad_out || !saved || H < 1 || W < 1) return BF_ERR_INVALID_ARG;
+static bf_status backward_impl(const void* img, const float* out, const float* grad_out,
+                               const void* saved, int B, int H, int W, int r, float sigma_r,
+                               float T, int N, float* grad_img, float* grad_sigma, void* workspace,
+                               size_t ws_bytes, const bf_opts* opts, void* stream) {
+    if (!img || !out || !grad_out || !saved || B < 1 || H < 1 || W < 1) return BF_ERR_INVALID_ARG;
     if (!grad_img && !grad_sigma) return BF_ERR_INVALID_ARG;
     bf_status st = check_opts(opts);
     if (st != BF_OK) return st;
@@ -297,7 +312,7 @@ bf_status bf_backward(const void* img, const float* out, const float* grad_out,
     Tiles t;
     BwdWs ws;
     bool use_sys = false;
-    st = bwd_ws(H, W, r, rs.K, opts, &ws, &t, &use_sys);
+    st = bwd_ws(B, H, W, r, rs.K, opts, &ws, &t, &use_sys);
     if (st != BF_OK) return st;
     const bool need_ws = ws.chunked || (grad_sigma && gm == BF_GAMMA_FROM_SIGMA);
     if (need_ws && (!workspace || ws_bytes < ws.total)) return BF_ERR_NOMEM;
@@ -340,18 +355,68 @@ bf_status bf_backward(const void* img, const float* out, const float* grad_out,
             q.acc_gt = acc + (size_t)H * W;
         }
         q.Hb = t.Hb; q.Tw = t.Tw;
+        q.B = B;
         e = launch_sys(q, 2, false, opts ? opts->in_dtype : BF_F32, t.nt, t.gx, t.gy, s);
     } else {
-        e = launch_backward(p, t.nt, opts ? opts->in_dtype : BF_F32, s);
+        const size_t esz = (opts && opts->in_dtype == BF_BF16) ? 2 : 4;
+        e = cudaSuccess;
+        for (int b = 0; b < B && e == cudaSuccess; ++b) {
+            BwdParams pb = p;
+            pb.img = static_cast<const char*>(img) + b * n * esz;
+            pb.out = out + b * n;
+            pb.gout = grad_out + b * n;
+            pb.sv_den = p.sv_den + b * 3 * n;
+            pb.sv_dnum = p.sv_dnum + b * 3 * n;
+            pb.sv_dden = p.sv_dden + b * 3 * n;
+            pb.gimg = grad_img ? grad_img + b * n : nullptr;
+            pb.partial = p.partial ? p.partial + (size_t)b * t.gx * t.gy : nullptr;
+            e = launch_backward(pb, t.nt, opts ? opts->in_dtype : BF_F32, s);
+        }
     }
     if (e != cudaSuccess) return set_cuda_error(e);
     if (want_sigma) {
         // dL/dsigma_r = dL/dgamma * dgamma/dsigma_r, gamma = 1/(sigma_r sqrt N).
         const float scale = (float)(-rs.gamma / (double)sigma_r);
-        e = launch_reduce_sigma(p.partial, t.gx * t.gy, scale, grad_sigma, s);
+        e = launch_reduce_sigma(p.partial, t.gx * t.gy * B, scale, grad_sigma, s);
         if (e != cudaSuccess) return set_cuda_error(e);
     }
     return BF_OK;
+}
+
+size_t bf_backward_workspace_bytes(int H, int W, int r, float sigma_r, float T, int N,
+                                   const bf_opts* opts) {
+    return backward_ws_impl(1, H, W, r, sigma_r, T, N, opts);
+}
+
+size_t bf_backward3d_workspace_bytes(int B, int H, int W, int r, float sigma_r, float T, int N,
+                                     const bf_opts* opts) {
+    return backward_ws_impl(B, H, W, r, sigma_r, T, N, opts);
+}
+
+bf_status bf_forward(const void* img, int H, int W, int r, float sigma_r, float T, int N,
+                     float* out, const bf_opts* opts, void* saved, void* stream) {
+    return forward_impl(img, 1, H, W, r, sigma_r, T, N, out, opts, saved, stream);
+}
+
+bf_status bf_forward3d(const void* img, int B, int H, int W, int r, float sigma_r, float T, int N,
+                       float* out, const bf_opts* opts, void* saved, void* stream) {
+    return forward_impl(img, B, H, W, r, sigma_r, T, N, out, opts, saved, stream);
+}
+
+bf_status bf_backward(const void* img, const float* out, const float* grad_out,
+                      const void* saved, int H, int W, int r, float sigma_r, float T, int N,
+                      float* grad_img, float* grad_sigma, void* workspace, size_t ws_bytes,
+                      const bf_opts* opts, void* stream) {
+    return backward_impl(img, out, grad_out, saved, 1, H, W, r, sigma_r, T, N, grad_img,
+                         grad_sigma, workspace, ws_bytes, opts, stream);
+}
+
+bf_status bf_backward3d(const void* img, const float* out, const float* grad_out,
+                        const void* saved, int B, int H, int W, int r, float sigma_r, float T,
+                        int N, float* grad_img, float* grad_sigma, void* workspace,
+                        size_t ws_bytes, const bf_opts* opts, void* stream) {
+    return backward_impl(img, out, grad_out, saved, B, H, W, r, sigma_r, T, N, grad_img,
+                         grad_sigma, workspace, ws_bytes, opts, stream);
 }
 
 const char* bf_status_string(bf_status s) {

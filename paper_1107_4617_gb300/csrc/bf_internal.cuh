@@ -67,6 +67,7 @@ struct SysParams {
     float* acc_gv;              // adjoint chunk accumulators (value and phase parts)
     float* acc_gt;
     int H, W, r, K, kstart, Hb, Tw;
+    int B;           // images of a [B, H, W] launch (grid.z); 0 or 1 = one image
     int k0;          // frequency of this launch's first harmonic
     int acc;         // 0 all harmonics; 1 first, 2 middle, 3 last harmonic chunk
     float gamma;

@@ -119,19 +119,21 @@ struct Px<true> {
     float f, g, den, out;
 };
 
+// zo / zs: element offsets of this image in the image-sized and the saved
+// (3 planes per image) buffers of a [B, H, W] launch.
 template <bool BWD, typename Tin>
 __device__ __forceinline__ void load_px(Px<BWD>& v, const SysParams& p, const Tin* img, bool on,
-                                        size_t q) {
+                                        size_t q, size_t zo, size_t zs) {
     if (!on) {
         v.f = 0.f;
         if constexpr (BWD) { v.g = 0.f; v.den = 1.f; v.out = 0.f; }
         return;
     }
-    v.f = ld_img(img, q);
+    v.f = ld_img(img, q + zo);
     if constexpr (BWD) {
-        v.g = __ldg(p.gout + q);
-        v.den = __ldg(p.bden + q);
-        v.out = __ldg(p.fout + q);
+        v.g = __ldg(p.gout + q + zo);
+        v.den = __ldg(p.bden + q + zs);
+        v.out = __ldg(p.fout + q + zo);
     }
 }
 
@@ -175,8 +177,8 @@ __host__ __device__ constexpr int sys_smem_slots(int KP, int Wi) {
 // Called uniformly by every thread of the CTA. gsum accumulates f * dL/dtheta
 // (adjoint, last chunk only). KAHAN compensates the vertical running sums.
 template <int KP, bool BWD, bool SAVE, bool KAHAN, typename Tin>
-__device__ __forceinline__ void sys_tile(const SysParams& p, int bx, int by, float4* smem,
-                                         float& gsum) {
+__device__ __forceinline__ void sys_tile(const SysParams& p, int bx, int by, size_t zo, size_t zs,
+                                         float4* smem, float& gsum) {
     const int Wi = blockDim.x;
     const int NW = Wi >> 5;
     // S of each lane at the last step: [KP][2][Wi] float4, i.e. per harmonic
@@ -216,11 +218,11 @@ __device__ __forceinline__ void sys_tile(const SysParams& p, int bx, int by, flo
     Px<BWD> v0, v1, v2, v3, vc;
     // a warp is first active at step 32 w; start its prefetch chain there
     Geo g = geometry(p, w * 32 - j, span, y0, cw, c2, co, own_in, sec_in, out_lane);
-    load_px<BWD, Tin>(v0, p, img, g.m0, g.q0);
-    load_px<BWD, Tin>(v1, p, img, g.m1, g.q1);
-    load_px<BWD, Tin>(v2, p, img, g.m2, g.q2);
-    load_px<BWD, Tin>(v3, p, img, g.m3, g.q3);
-    load_px<BWD, Tin>(vc, p, img, g.out, g.qo);
+    load_px<BWD, Tin>(v0, p, img, g.m0, g.q0, zo, zs);
+    load_px<BWD, Tin>(v1, p, img, g.m1, g.q1, zo, zs);
+    load_px<BWD, Tin>(v2, p, img, g.m2, g.q2, zo, zs);
+    load_px<BWD, Tin>(v3, p, img, g.m3, g.q3, zo, zs);
+    load_px<BWD, Tin>(vc, p, img, g.out, g.qo, zo, zs);
     __syncthreads();
 
     for (int t = 0; t < steps; ++t) {
@@ -235,15 +237,15 @@ __device__ __forceinline__ void sys_tile(const SysParams& p, int bx, int by, flo
                 const int ef = y0 - r + (t + PREFETCH_ROWS - j);
                 // (forward only: the adjoint's four extra streams made it slower)
                 if (!BWD && own_in && ef >= 0 && ef < p.H)
-                    prefetch_l2(static_cast<const Tin*>(p.img) + (size_t)ef * p.W + cw);
+                    prefetch_l2(static_cast<const Tin*>(p.img) + zo + (size_t)ef * p.W + cw);
             }
             // prefetch the next step's pixels; their latency hides under this step
             g = geometry(p, t + 1 - j, span, y0, cw, c2, co, own_in, sec_in, out_lane);
-            load_px<BWD, Tin>(v0, p, img, g.m0, g.q0);
-            load_px<BWD, Tin>(v1, p, img, g.m1, g.q1);
-            load_px<BWD, Tin>(v2, p, img, g.m2, g.q2);
-            load_px<BWD, Tin>(v3, p, img, g.m3, g.q3);
-            load_px<BWD, Tin>(vc, p, img, g.out, g.qo);
+            load_px<BWD, Tin>(v0, p, img, g.m0, g.q0, zo, zs);
+            load_px<BWD, Tin>(v1, p, img, g.m1, g.q1, zo, zs);
+            load_px<BWD, Tin>(v2, p, img, g.m2, g.q2, zo, zs);
+            load_px<BWD, Tin>(v3, p, img, g.m3, g.q3, zo, zs);
+            load_px<BWD, Tin>(vc, p, img, g.out, g.qo, zo, zs);
 
             Rot2 s0 = seed2(c0.f, p.gamma, p.gpi, p.k0, gc.m0);
             Rot2 s1 = seed2(c1.f, p.gamma, p.gpi, p.k0, gc.m1);
@@ -354,26 +356,27 @@ __device__ __forceinline__ void sys_tile(const SysParams& p, int bx, int by, flo
                 rot2(s0); rot2(s1); rot2(s2); rot2(s3); rot2(sc);
             }
             if (gc.out) {
-                const size_t o = gc.qo;
+                const size_t o = gc.qo + zo;   // image-sized buffers
+                const size_t os = gc.qo + zs;  // saved buffers
                 float num = NUM.x + NUM.y, den = DEN.x + DEN.y;
                 // chunked harmonics: partial sums live in the output buffers
                 // between chunks (acc: 0 single, 1 first, 2 middle, 3 last)
                 const int acc = p.acc;
                 if constexpr (!BWD) {
                     float dn = DNUM.x + DNUM.y, dd = DDEN.x + DDEN.y;
-                    float* dbuf = SAVE ? p.sv_den : p.acc_den;
+                    float* dbuf = SAVE ? p.sv_den + zs : p.acc_den + zo;
                     if (acc >= 2) {
                         num += p.out[o];
-                        den += dbuf[o];
-                        if constexpr (SAVE) { dn += p.sv_dnum[o]; dd += p.sv_dden[o]; }
+                        den += dbuf[gc.qo];
+                        if constexpr (SAVE) { dn += p.sv_dnum[os]; dd += p.sv_dden[os]; }
                     }
                     p.out[o] = (acc == 0 || acc == 3) ? num / den : num;
-                    if (SAVE || acc != 0) dbuf[o] = den;
-                    if constexpr (SAVE) { p.sv_dnum[o] = dn; p.sv_dden[o] = dd; }
+                    if (SAVE || acc != 0) dbuf[gc.qo] = den;
+                    if constexpr (SAVE) { p.sv_dnum[os] = dn; p.sv_dden[os] = dd; }
                 } else {
                     if (acc >= 2) { num += p.acc_gv[o]; den += p.acc_gt[o]; }
                     if (acc == 0 || acc == 3) {
-                        const float gt = den + ac * __ldg(p.bdnum + o) + bc * __ldg(p.bdden + o);
+                        const float gt = den + ac * __ldg(p.bdnum + os) + bc * __ldg(p.bdden + os);
                         if (p.gimg) p.gimg[o] = num + p.gamma * gt;
                         gsum = fmaf(cc.f, gt, gsum);
                     } else {
@@ -410,18 +413,23 @@ template <int KP, bool BWD, bool SAVE, bool KAHAN, int WMAX, typename Tin>
 __global__ void __launch_bounds__(WMAX, 256 / WMAX) bf_sys_kernel(SysParams p) {
     extern __shared__ float4 smem[];
     float gsum = 0.f;
-    sysd::sys_tile<KP, BWD, SAVE, KAHAN, Tin>(p, blockIdx.x, blockIdx.y, smem, gsum);
-    if (BWD && p.partial) sysd::cta_sum_to(gsum, p.partial, blockIdx.y * gridDim.x + blockIdx.x);
+    const size_t z = blockIdx.z;  // image of a [B, H, W] launch
+    const size_t hw = (size_t)p.H * p.W;
+    sysd::sys_tile<KP, BWD, SAVE, KAHAN, Tin>(p, blockIdx.x, blockIdx.y, z * hw, z * 3 * hw, smem,
+                                              gsum);
+    if (BWD && p.partial)
+        sysd::cta_sum_to(gsum, p.partial, (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x);
 }
 
 template <int KP, bool BWD, bool SAVE, bool KAHAN, int WMAX, typename Tin>
 cudaError_t sys_launch_one(const SysParams& p, int wi, int gx, int gy, cudaStream_t s) {
+    const int gz = p.B > 0 ? p.B : 1;
     auto kern = bf_sys_kernel<KP, BWD, SAVE, KAHAN, WMAX, Tin>;
     const size_t smem = sizeof(float4) * (size_t)sysd::sys_smem_slots(KP, wi);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<dim3(gx, gy), wi, smem, s>>>(p);
+    kern<<<dim3(gx, gy, gz), wi, smem, s>>>(p);
     return cudaGetLastError();
 }
 

@@ -136,3 +136,42 @@ def test_grad_chunked_and_wide(cuda_lib, H, W, r, sigma):
     N = oracle.resolve_N(sigma, 1.0)
     gref, _ = oracle.bilateral_grad(f.astype(np.float64), w.astype(np.float64), r, math.pi / 2, N)
     check_grad(ft.grad.cpu().numpy(), gref)
+
+
+@pytest.mark.parametrize("kahan_fallback", [False, True])
+def test_3d_launch_matches_per_image(cuda_lib, kahan_fallback):
+    """bf_forward3d / bf_backward3d over [B, H, W] equal B single-image calls
+    (skewed-strip engine with grid.z, and the per-image single-pass fallback)."""
+    bf = cuda_lib
+    B, H, W, r, sigma = 3, 70, 130, 6, 0.15
+    f = torch.from_numpy(np.stack([synth.rectangles(H, W, seed=40 + b) for b in range(B)])).cuda()
+    g = torch.from_numpy(synth.weights((B, H, W), seed=2)).cuda()
+    N = oracle.resolve_N(sigma, 1.0)
+    opts = bf._opts(save=not kahan_fallback, kahan=kahan_fallback, gamma_mode=bf.GAMMA_FROM_SIGMA)
+    sv = torch.empty((B, 3, H, W), device="cuda")
+    out3 = bf.bf_forward3d(f, r, sigma, 1.0, N, opts=opts, saved=None if kahan_fallback else sv)
+    for b in range(B):
+        o1 = bf.bf_forward(f[b], r, sigma, 1.0, N, opts=opts, saved=None if kahan_fallback else sv[b])
+        torch.cuda.synchronize()
+        assert torch.max(torch.abs(o1 - out3[b])).item() <= 1e-6
+    if kahan_fallback:
+        return
+    bf.bf_forward3d(f, r, sigma, 1.0, N, out=out3, opts=opts, saved=sv)
+    gi = torch.empty_like(f)
+    gs = torch.zeros((1,), device="cuda")
+    ws = torch.empty((bf.bf_backward3d_workspace_bytes(B, H, W, r, sigma, 1.0, N, opts) // 4 + 1,),
+                     device="cuda")
+    bf.bf_backward3d(f, out3, g, sv, r, sigma, 1.0, N, grad_img=gi, grad_sigma=gs, workspace=ws,
+                     opts=opts)
+    total = 0.0
+    for b in range(B):
+        gi1 = torch.empty_like(f[b])
+        gs1 = torch.zeros((1,), device="cuda")
+        ws1 = torch.empty((bf.bf_backward_workspace_bytes(H, W, r, sigma, 1.0, N, opts) // 4 + 1,),
+                          device="cuda")
+        bf.bf_backward(f[b], out3[b], g[b], sv[b], r, sigma, 1.0, N, grad_img=gi1, grad_sigma=gs1,
+                       workspace=ws1, opts=opts)
+        torch.cuda.synchronize()
+        assert torch.max(torch.abs(gi1 - gi[b])).item() <= 1e-6 * max(1.0, gi1.abs().max().item())
+        total += float(gs1)
+    assert abs(float(gs) - total) <= 1e-4 * max(1.0, abs(total))
