@@ -369,6 +369,7 @@ def main():
     import torch
 
     import paper_1107_4617_gb300 as bf
+    from paper_1107_4617_gb300 import dist as bdist
     from paper_1107_4617_gb300 import synth
 
     dist = None
@@ -428,13 +429,14 @@ def main():
     t_fwd = sum(e[0].elapsed_time(e[1]) for e in ev) / 1e3
     t_bwd = sum(e[1].elapsed_time(e[2]) for e in ev) / 1e3
     t_step = t_fwd + t_bwd
-    if dist:
-        tt = torch.tensor([t_step, t_fwd, t_bwd], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_step, t_fwd, t_bwd = [float(x) for x in tt.cpu()]
+    # each rank filters its own image: no collective on the data path, only
+    # the slowest rank's time
     px = H * W
-    value = world * px * args.steps / t_step / 1e6
-    fwd_value = world * px * args.steps / t_fwd / 1e6
+    value = bdist.throughput(px * args.steps, t_step, dev) / 1e6
+    fwd_value = bdist.throughput(px * args.steps, t_fwd, dev) / 1e6
+    t_step = bdist.max_over_ranks(t_step, dev)
+    t_fwd = bdist.max_over_ranks(t_fwd, dev)
+    t_bwd = bdist.max_over_ranks(t_bwd, dev)
 
     if args.kernels_only:
         if rank == 0:
@@ -485,11 +487,7 @@ def main():
     eb.record(stream)
     torch.cuda.synchronize(dev)
     t_e2e = ea.elapsed_time(eb) / 1e3
-    if dist:
-        tt = torch.tensor([t_e2e], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_e2e = float(tt.item())
-    e2e_value = world * px * e2e_steps / t_e2e / 1e6
+    e2e_value = bdist.throughput(px * e2e_steps, t_e2e, dev) / 1e6
 
     # accuracy vs the FP64 oracle on sampled pixels (reported, not timed)
     err = None
