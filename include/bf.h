@@ -79,6 +79,10 @@ typedef struct {
     int save_for_backward;/* 1: bf_forward fills `saved` (also implied by saved != NULL) */
     int tile_h;           /* rows per band; 0 = built-in choice */
     int tile_w;           /* threads per strip (multiple of 32, > 2r); 0 = built-in */
+    int kp_max;           /* most harmonic pairs per launch, 1..11; 0 = 11. Fewer pairs
+                             mean fewer registers per thread; the harmonics then run
+                             in chunks, which accumulate in `saved` (forward) or the
+                             workspace (adjoint) */
 } bf_opts;
 
 /* One image of a batch (bf_batch). img/out/den are device pointers. */

@@ -49,7 +49,7 @@ class BfError(RuntimeError):
 class BfOpts(ctypes.Structure):
     _fields_ = [("kahan", ctypes.c_int), ("gamma_mode", ctypes.c_int),
                 ("in_dtype", ctypes.c_int), ("save_for_backward", ctypes.c_int),
-                ("tile_h", ctypes.c_int), ("tile_w", ctypes.c_int)]
+                ("tile_h", ctypes.c_int), ("tile_w", ctypes.c_int), ("kp_max", ctypes.c_int)]
 
 
 class BfDesc(ctypes.Structure):
@@ -135,10 +135,12 @@ def _check(fn: str, status: int):
         raise BfError(fn, status, bf_last_cuda_error() if status == 3 else 0)
 
 
-def _opts(kahan=False, gamma_mode=GAMMA_FIXED, in_dtype=F32, save=False, tile_h=0, tile_w=0):
+def _opts(kahan=False, gamma_mode=GAMMA_FIXED, in_dtype=F32, save=False, tile_h=0, tile_w=0,
+          kp_max=0):
     o = BfOpts()
     o.kahan, o.gamma_mode, o.in_dtype = int(bool(kahan)), int(gamma_mode), int(in_dtype)
     o.save_for_backward, o.tile_h, o.tile_w = int(bool(save)), int(tile_h), int(tile_w)
+    o.kp_max = int(kp_max)
     return o
 
 

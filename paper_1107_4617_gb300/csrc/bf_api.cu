@@ -98,10 +98,11 @@ static bf_status choose_tiles(int H, int W, int r, const bf_opts* o, Tiles* t) {
 
 // The skewed-strip engine (bf_sys.cu) serves every request whose strip of
 // Wi threads keeps at least 16 output columns (Wi - 2r >= 16): 128-thread
-// strips for r <= 20 (two CTAs per SM), 256-thread strips above (one CTA per
-// SM, less halo). Bands: one wave of resident CTAs.
+// strips up to r = 40 (two CTAs per SM: measured faster than wider strips
+// with one CTA per SM even at r = 30, where half the lanes are halo),
+// 256-thread strips above. Bands: one wave of resident CTAs.
 static bool sys_tiles(int H, int W, int r, const bf_opts* o, Tiles* t) {
-    int wi = (r <= 20) ? 128 : 256;
+    int wi = (r <= 40) ? 128 : 256;
     if (o && o->tile_w > 0) {
         if (o->tile_w > SYS_MAX_THREADS || o->tile_w % 32 != 0) return false;
         wi = o->tile_w;
@@ -144,6 +145,7 @@ bf_status check_opts(const bf_opts* o) {
     if (o->gamma_mode != BF_GAMMA_FIXED && o->gamma_mode != BF_GAMMA_FROM_SIGMA)
         return BF_ERR_INVALID_ARG;
     if (o->tile_h < 0 || o->tile_w < 0) return BF_ERR_INVALID_ARG;
+    if (o->kp_max < 0 || o->kp_max > SYS_KP_MAX) return BF_ERR_INVALID_ARG;
     return BF_OK;
 }
 
@@ -235,7 +237,8 @@ static bf_status forward_impl(const void* img, int B, int H, int W, int r, float
     Tiles t;
     cudaError_t e = cudaSuccess;
     // harmonic chunks accumulate in the saved buffers, so chunking needs them
-    if (sys_tiles(H, W, r, opts, &t) && (sys_chunks(p.K, kahan) == 1 || saved)) {
+    const int kpm = opts ? opts->kp_max : 0;
+    if (sys_tiles(H, W, r, opts, &t) && (sys_chunks(p.K, kahan, kpm) == 1 || saved)) {
         SysParams q;
         fill_sys(p, &q);
         q.out = out;
@@ -243,7 +246,7 @@ static bf_status forward_impl(const void* img, int B, int H, int W, int r, float
         q.Hb = t.Hb; q.Tw = t.Tw;
         q.B = B;
         e = launch_sys(q, saved ? 1 : 0, kahan, in_dtype, t.nt, t.gx, t.gy,
-                       (cudaStream_t)stream);
+                       (cudaStream_t)stream, kpm);
     } else {
         const size_t hw = (size_t)H * W;
         for (int b = 0; b < B && e == cudaSuccess; ++b) {
@@ -277,7 +280,7 @@ static bf_status bwd_ws(int B, int H, int W, int r, int K, const bf_opts* opts, 
         if (st != BF_OK) return st;
     }
     ws->partial_bytes = (size_t)t->gx * t->gy * B * sizeof(float);
-    ws->chunked = *use_sys && sys_chunks(K, false) > 1;
+    ws->chunked = *use_sys && sys_chunks(K, false, opts ? opts->kp_max : 0) > 1;
     ws->acc_offset = (ws->partial_bytes + 255) & ~(size_t)255;
     ws->total = ws->chunked ? ws->acc_offset + 2 * (size_t)B * H * W * sizeof(float)
                             : ws->partial_bytes;
@@ -356,7 +359,8 @@ static bf_status backward_impl(const void* img, const float* out, const float* g
         }
         q.Hb = t.Hb; q.Tw = t.Tw;
         q.B = B;
-        e = launch_sys(q, 2, false, opts ? opts->in_dtype : BF_F32, t.nt, t.gx, t.gy, s);
+        e = launch_sys(q, 2, false, opts ? opts->in_dtype : BF_F32, t.nt, t.gx, t.gy, s,
+                       opts ? opts->kp_max : 0);
     } else {
         const size_t esz = (opts && opts->in_dtype == BF_BF16) ? 2 : 4;
         e = cudaSuccess;

@@ -46,7 +46,7 @@ static size_t sys_table_bytes(int n) {
 // Strip width of an image on the skewed-strip engine (same rule as a single
 // image), or 0 when the strip would keep fewer than 16 output columns.
 static int sys_width(int r, const bf_opts* o) {
-    int wi = (r <= 20) ? 128 : 256;
+    int wi = (r <= 40) ? 128 : 256;
     if (o && o->tile_w > 0) wi = o->tile_w;
     if (wi % 32 != 0 || wi > SYS_MAX_THREADS || wi - 2 * r < 16) return 0;
     return wi;
@@ -74,7 +74,7 @@ static bf_status plan_image(const bf_desc& d, const bf_opts* opts, Plan* pl) {
     pl->Hb = sys_batch_rows(d.r, d.H, opts);
     pl->gx = (d.W + Tw - 1) / Tw;
     pl->gy = (d.H + pl->Hb - 1) / pl->Hb;
-    pl->nch = sys_chunks(pl->p.K, false);
+    pl->nch = sys_chunks(pl->p.K, false, 0);
     if (pl->nch > SYS_BATCH_MAX_CHUNKS) return BF_ERR_UNSUPPORTED;
     pl->cost = (long long)(pl->Hb + 2 * d.r + pl->wi) * (pl->p.K + 2);
     return BF_OK;

@@ -82,8 +82,8 @@ constexpr int SYS_KP_KAHAN = 6;
 
 // mode: 0 forward, 1 forward + saved buffers, 2 adjoint.
 cudaError_t launch_sys(const SysParams& p, int mode, bool kahan, int in_dtype, int wi, int gx,
-                       int gy, cudaStream_t s);
-int sys_chunks(int K, bool kahan);
+                       int gy, cudaStream_t s, int kp_max = 0);
+int sys_chunks(int K, bool kahan, int kp_max = 0);
 cudaError_t launch_sys_w128(const SysParams& p, int mode, int dtype, int kp, int wi, int gx,
                             int gy, cudaStream_t s);
 cudaError_t launch_sys_w256(const SysParams& p, int mode, int dtype, int kp, int wi, int gx,

@@ -18,17 +18,19 @@ static int sys_kp(int K) {
     return -1;
 }
 
-int sys_chunks(int K, bool kahan) {
-    const int per = 2 * (kahan ? SYS_KP_KAHAN : SYS_KP_MAX);
+int sys_chunks(int K, bool kahan, int kp_max) {
+    int kp = kahan ? SYS_KP_KAHAN : SYS_KP_MAX;
+    if (kp_max > 0 && kp_max < kp) kp = kp_max;
+    const int per = 2 * kp;
     return (K + per - 1) / per;
 }
 
 cudaError_t launch_sys(const SysParams& base, int mode, bool kahan, int in_dtype, int wi, int gx,
-                       int gy, cudaStream_t s) {
+                       int gy, cudaStream_t s, int kp_max) {
     if (wi > SYS_MAX_THREADS || wi % 32 != 0 || base.K < 1 || base.K > KCAP)
         return cudaErrorInvalidValue;
     if (kahan && mode == 2) return cudaErrorInvalidValue;
-    const int nch = sys_chunks(base.K, kahan);
+    const int nch = sys_chunks(base.K, kahan, kp_max);
     int per = (base.K + nch - 1) / nch;
     per += per & 1;  // whole harmonic pairs per chunk
     for (int c = 0; c < nch; ++c) {
