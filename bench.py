@@ -529,6 +529,13 @@ def main():
         del h_img, h_g, h_out, h_gimg
         extra = extras(dev, flush, stream)
 
+    if rank == 0:
+        try:
+            from paper_1107_4617_gb300 import peak
+            roofline["measured_pipes"] = peak.measure()
+        except Exception as e:  # reported, never fatal: the derived peak stands
+            roofline["measured_pipes"] = {"error": str(e)[:200]}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, cores, sample = cpu_baseline()
