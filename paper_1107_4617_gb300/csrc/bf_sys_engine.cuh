@@ -117,6 +117,7 @@ struct Px<false> {
 template <>
 struct Px<true> {
     float f, g, den, out;
+    float dnum, dden;  // centre stream only: saved d num/ds, d den/ds
 };
 
 // zo / zs: element offsets of this image in the image-sized and the saved
@@ -126,7 +127,7 @@ __device__ __forceinline__ void load_px(Px<BWD>& v, const SysParams& p, const Ti
                                         size_t q, size_t zo, size_t zs) {
     if (!on) {
         v.f = 0.f;
-        if constexpr (BWD) { v.g = 0.f; v.den = 1.f; v.out = 0.f; }
+        if constexpr (BWD) { v.g = 0.f; v.den = 1.f; v.out = 0.f; v.dnum = 0.f; v.dden = 0.f; }
         return;
     }
     v.f = ld_img(img, q + zo);
@@ -134,6 +135,19 @@ __device__ __forceinline__ void load_px(Px<BWD>& v, const SysParams& p, const Ti
         v.g = __ldg(p.gout + q + zo);
         v.den = __ldg(p.bden + q + zs);
         v.out = __ldg(p.fout + q + zo);
+    }
+}
+
+// The centre stream also needs the forward's saved centre derivatives.
+template <bool BWD, typename Tin>
+__device__ __forceinline__ void load_centre(Px<BWD>& v, const SysParams& p, const Tin* img,
+                                            bool on, size_t q, size_t zo, size_t zs) {
+    load_px<BWD, Tin>(v, p, img, on, q, zo, zs);
+    if constexpr (BWD) {
+        if (on) {
+            v.dnum = __ldg(p.bdnum + q + zs);
+            v.dden = __ldg(p.bdden + q + zs);
+        }
     }
 }
 
@@ -222,7 +236,7 @@ __device__ __forceinline__ void sys_tile(const SysParams& p, int bx, int by, siz
     load_px<BWD, Tin>(v1, p, img, g.m1, g.q1, zo, zs);
     load_px<BWD, Tin>(v2, p, img, g.m2, g.q2, zo, zs);
     load_px<BWD, Tin>(v3, p, img, g.m3, g.q3, zo, zs);
-    load_px<BWD, Tin>(vc, p, img, g.out, g.qo, zo, zs);
+    load_centre<BWD, Tin>(vc, p, img, g.out, g.qo, zo, zs);
     __syncthreads();
 
     for (int t = 0; t < steps; ++t) {
@@ -245,7 +259,7 @@ __device__ __forceinline__ void sys_tile(const SysParams& p, int bx, int by, siz
             load_px<BWD, Tin>(v1, p, img, g.m1, g.q1, zo, zs);
             load_px<BWD, Tin>(v2, p, img, g.m2, g.q2, zo, zs);
             load_px<BWD, Tin>(v3, p, img, g.m3, g.q3, zo, zs);
-            load_px<BWD, Tin>(vc, p, img, g.out, g.qo, zo, zs);
+            load_centre<BWD, Tin>(vc, p, img, g.out, g.qo, zo, zs);
 
             Rot2 s0 = seed2(c0.f, p.gamma, p.gpi, p.k0, gc.m0);
             Rot2 s1 = seed2(c1.f, p.gamma, p.gpi, p.k0, gc.m1);
@@ -376,7 +390,7 @@ __device__ __forceinline__ void sys_tile(const SysParams& p, int bx, int by, siz
                 } else {
                     if (acc >= 2) { num += p.acc_gv[o]; den += p.acc_gt[o]; }
                     if (acc == 0 || acc == 3) {
-                        const float gt = den + ac * __ldg(p.bdnum + os) + bc * __ldg(p.bdden + os);
+                        const float gt = den + ac * cc.dnum + bc * cc.dden;
                         if (p.gimg) p.gimg[o] = num + p.gamma * gt;
                         gsum = fmaf(cc.f, gt, gsum);
                     } else {
