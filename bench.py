@@ -201,7 +201,7 @@ def extras(dev, flush, stream):
     img = torch.from_numpy(f_np).to(dev)
     img16 = img.to(torch.bfloat16)
     out = torch.empty_like(img)
-    sv = torch.empty((3, Hp, Hp), device=dev)
+    sv = torch.empty((Hp, Hp, 4), device=dev)
     N = bf.bf_resolve_N(0.1, 1.0)
     idx = rng.integers(0, Hp * Hp, 256)
     ref = oracle.bilateral_points(f_np.astype(np.float64), 30, oracle.gamma_fixed(1.0), N, idx)
@@ -276,7 +276,7 @@ def extras(dev, flush, stream):
     wt = torch.from_numpy(wb).to(dev)
     Nd = bf.bf_resolve_N(0.15, 1.0)
     outd = torch.empty_like(ft)
-    svd = torch.empty((B, 3, Hd, Hd), device=dev)
+    svd = torch.empty((B, Hd, Hd, 4), device=dev)
     gi = torch.empty_like(ft)
     sopt = bf._opts(save=True)
 
@@ -388,7 +388,7 @@ def main():
     img = torch.from_numpy(f_np).to(dev)
     g = torch.from_numpy(w_np).to(dev)
     out = torch.empty((H, W), dtype=torch.float32, device=dev)
-    saved = torch.empty((3, H, W), dtype=torch.float32, device=dev)
+    saved = torch.empty((H, W, 4), dtype=torch.float32, device=dev)
     gimg = torch.empty((H, W), dtype=torch.float32, device=dev)
     flush = torch.empty((L2_FLUSH_BYTES // 4,), dtype=torch.float32, device=dev)
     opts = bf._opts(save=True)

@@ -115,9 +115,12 @@ int bf_coeffs(int N, double* a, int cap);
    Returns a negative value on bad arguments. Host only. */
 double bf_gamma(float sigma_r, float T, int N, int gamma_mode);
 
-/* Bytes of the `saved` buffer bf_forward fills for bf_backward:
-   3 * H * W floats (den, d num / d s, d den / d s; Sec. 2 Eq. filter2
-   differentiated with respect to the centre value). */
+/* Bytes of the `saved` buffer bf_forward fills for bf_backward: H * W
+   quads of 4 floats, pixel-major, (f, 1 / den, out, dnum_s - out * dden_s),
+   where dnum_s, dden_s are num and den of Eq. filter2 differentiated with
+   respect to the centre value f(x) (divided by gamma). The adjoint reads one
+   16-byte quad per pixel instead of several planes. The buffer must be
+   16-byte aligned. */
 size_t bf_saved_bytes(int H, int W);
 
 /*
@@ -127,8 +130,8 @@ size_t bf_saved_bytes(int H, int W);
  *           BF_GAMMA_FROM_SIGMA mode.   T > 0.   N <= 0: derived from sigma_r.
  *   out     device, H x W FP32. Must not alias img.
  *   opts    NULL = defaults.
- *   saved   NULL, or device buffer of bf_saved_bytes(H, W), written for
- *           bf_backward. When N > 43 (or opts->kahan with N > 23) the
+ *   saved   NULL, or device buffer of bf_saved_bytes(H, W) (16-byte aligned),
+ *           written for bf_backward. When N > 43 (or opts->kahan with N > 23) the
  *           harmonics run in chunks that accumulate in this buffer; without
  *           it such calls take a slower single-pass kernel.
  * Errors: BF_ERR_INVALID_ARG (null pointer, H/W < 1, r < 0, T <= 0, bad
@@ -149,7 +152,9 @@ size_t bf_backward_workspace_bytes(int H, int W, int r, float sigma_r, float T, 
  * Adjoint of bf_forward for L with dL/dout = grad_out (derived from Eq.
  * filter2; the box window is symmetric, so the adjoint is again a moving-sum
  * pass over a stack recomputed from img, never stored).
- *   img, out      the forward's input and output (device).
+ *   img, out      the forward's input and output (device; the adjoint
+ *                 reads both through the saved quads, so they are only
+ *                 checked for NULL).
  *   grad_out      device H x W FP32.
  *   saved         the forward's saved buffer (device, bf_saved_bytes).
  *   grad_img      device H x W FP32 output, or NULL.
@@ -167,7 +172,7 @@ bf_status bf_backward(const void* img, const float* out, const float* grad_out,
 /*
  * bf_forward over B images of equal size in one launch: img, out are
  * contiguous [B, H, W] arrays (dtype as in bf_forward), saved (NULL or
- * B * bf_saved_bytes(H, W)) is [B][3][H][W]. Same parameters, errors and
+ * B * bf_saved_bytes(H, W)) is [B][H][W] quads. Same parameters, errors and
  * precondition as bf_forward, for every image.
  */
 bf_status bf_forward3d(const void* img, int B, int H, int W, int r, float sigma_r, float T, int N,

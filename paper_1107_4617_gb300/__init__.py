@@ -332,8 +332,8 @@ def _make_function():
 
     class BilateralCosN(torch.autograd.Function):
         """out = bilateral(f) with range kernel cos^N; differentiable in f and
-        sigma_r (a 0-d tensor). Forward saves den and the centre derivatives;
-        the adjoint kernel recomputes the stack from f."""
+        sigma_r (a 0-d tensor). Forward saves per pixel (f, 1/den, out, centre
+        derivative term); the adjoint kernel recomputes the stack from them."""
 
         @staticmethod
         def forward(ctx, f, sigma_r, r, T, N, kahan, gamma_mode):
@@ -346,7 +346,7 @@ def _make_function():
             B, H, W = fb.shape
             opts = _opts(kahan=kahan, gamma_mode=gamma_mode, in_dtype=_in_dtype(fb), save=True)
             out = torch.empty((B, H, W), dtype=torch.float32, device=f.device)
-            saved = torch.empty((B, 3, H, W), dtype=torch.float32, device=f.device)
+            saved = torch.empty((B, H, W, 4), dtype=torch.float32, device=f.device)
             bf_forward3d(fb, r, s, T, N, out=out, opts=opts, saved=saved)
             ctx.save_for_backward(fb, out, saved)
             ctx.cfg = (r, s, T, N, kahan, gamma_mode, squeeze)

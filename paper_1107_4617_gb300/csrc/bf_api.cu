@@ -108,6 +108,9 @@ static bool sys_tiles(int H, int W, int r, const bf_opts* o, Tiles* t) {
         wi = o->tile_w;
     }
     if (wi - 2 * r < 16) return false;
+    // the engine addresses one image with 32-bit element offsets (rows of the
+    // skew ramp above and below the image included)
+    if ((long long)(H + 2 * wi + 4 * r) * W >= 0x7fffffffLL) return false;
     t->nt = wi;
     t->Tw = wi - 2 * r;
     t->gx = (W + t->Tw - 1) / t->Tw;
@@ -164,17 +167,12 @@ bf_status fill_fwd_params(const void* img, float* out, void* saved, int H, int W
     st = choose_tiles(H, W, r, opts, &t);
     if (st != BF_OK) return st;
     if (opts && opts->save_for_backward && !saved) return BF_ERR_INVALID_ARG;
+    if (saved && ((uintptr_t)saved & 15)) return BF_ERR_INVALID_ARG;  // quads: 16-byte aligned
     FwdParams& p = *pp;
     memset(&p, 0, sizeof(p));
     p.img = img;
     p.out = out;
-    if (saved) {
-        float* s = static_cast<float*>(saved);
-        const size_t n = (size_t)H * W;
-        p.sv_den = s;
-        p.sv_dnum = s + n;
-        p.sv_dden = s + 2 * n;
-    }
+    p.sv = static_cast<float4*>(saved);
     p.H = H; p.W = W; p.r = r; p.K = rs.K; p.kstart = rs.kstart;
     p.Hb = t.Hb; p.Tw = t.Tw;
     p.gamma = (float)rs.gamma;
@@ -219,7 +217,7 @@ double bf_gamma(float sigma_r, float T, int N, int gamma_mode) {
 
 size_t bf_saved_bytes(int H, int W) {
     if (H < 1 || W < 1) return 0;
-    return (size_t)3 * (size_t)H * (size_t)W * sizeof(float);
+    return (size_t)H * (size_t)W * sizeof(float4);
 }
 
 static bf_status forward_impl(const void* img, int B, int H, int W, int r, float sigma_r,
@@ -242,7 +240,7 @@ static bf_status forward_impl(const void* img, int B, int H, int W, int r, float
         SysParams q;
         fill_sys(p, &q);
         q.out = out;
-        q.sv_den = p.sv_den; q.sv_dnum = p.sv_dnum; q.sv_dden = p.sv_dden;
+        q.sv = p.sv;
         q.Hb = t.Hb; q.Tw = t.Tw;
         q.B = B;
         e = launch_sys(q, saved ? 1 : 0, kahan, in_dtype, t.nt, t.gx, t.gy,
@@ -253,11 +251,7 @@ static bf_status forward_impl(const void* img, int B, int H, int W, int r, float
             FwdParams pb = p;
             pb.img = static_cast<const char*>(img) + b * hw * esz;
             pb.out = out + b * hw;
-            if (saved) {
-                pb.sv_den = p.sv_den + b * 3 * hw;
-                pb.sv_dnum = p.sv_dnum + b * 3 * hw;
-                pb.sv_dden = p.sv_dden + b * 3 * hw;
-            }
+            if (saved) pb.sv = p.sv + b * hw;
             e = launch_forward(pb, nt, kahan ? 1 : 0, in_dtype, (cudaStream_t)stream);
         }
     }
@@ -306,6 +300,7 @@ static bf_status backward_impl(const void* img, const float* out, const float* g
                                size_t ws_bytes, const bf_opts* opts, void* stream) {
     if (!img || !out || !grad_out || !saved || B < 1 || H < 1 || W < 1) return BF_ERR_INVALID_ARG;
     if (!grad_img && !grad_sigma) return BF_ERR_INVALID_ARG;
+    if ((uintptr_t)saved & 15) return BF_ERR_INVALID_ARG;  // quads: 16-byte aligned
     bf_status st = check_opts(opts);
     if (st != BF_OK) return st;
     const int gm = opts ? opts->gamma_mode : BF_GAMMA_FIXED;
@@ -331,10 +326,9 @@ static bf_status backward_impl(const void* img, const float* out, const float* g
 
     BwdParams p;
     memset(&p, 0, sizeof(p));
-    const float* sv = static_cast<const float*>(saved);
     const size_t n = (size_t)H * W;
-    p.img = img; p.out = out; p.gout = grad_out;
-    p.sv_den = sv; p.sv_dnum = sv + n; p.sv_dden = sv + 2 * n;
+    p.img = img; p.gout = grad_out;
+    p.sv = static_cast<const float4*>(saved);
     p.gimg = grad_img;
     p.partial = want_sigma ? static_cast<float*>(workspace) : nullptr;
     p.H = H; p.W = W; p.r = r; p.K = rs.K; p.kstart = rs.kstart; p.Hb = t.Hb; p.Tw = t.Tw;
@@ -349,8 +343,8 @@ static bf_status backward_impl(const void* img, const float* out, const float* g
         for (int i = 0; i < p.K; ++i) fp.a[i] = p.a[i];
         SysParams q;
         fill_sys(fp, &q);
-        q.fout = out; q.gout = grad_out;
-        q.bden = p.sv_den; q.bdnum = p.sv_dnum; q.bdden = p.sv_dden;
+        q.gout = grad_out;
+        q.bsv = p.sv;
         q.gimg = grad_img; q.partial = p.partial;
         if (ws.chunked) {
             float* acc = reinterpret_cast<float*>(static_cast<char*>(workspace) + ws.acc_offset);
@@ -367,11 +361,8 @@ static bf_status backward_impl(const void* img, const float* out, const float* g
         for (int b = 0; b < B && e == cudaSuccess; ++b) {
             BwdParams pb = p;
             pb.img = static_cast<const char*>(img) + b * n * esz;
-            pb.out = out + b * n;
             pb.gout = grad_out + b * n;
-            pb.sv_den = p.sv_den + b * 3 * n;
-            pb.sv_dnum = p.sv_dnum + b * 3 * n;
-            pb.sv_dden = p.sv_dden + b * 3 * n;
+            pb.sv = p.sv + b * n;
             pb.gimg = grad_img ? grad_img + b * n : nullptr;
             pb.partial = p.partial ? p.partial + (size_t)b * t.gx * t.gy : nullptr;
             e = launch_backward(pb, t.nt, opts ? opts->in_dtype : BF_F32, s);

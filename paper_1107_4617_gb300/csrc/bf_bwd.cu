@@ -15,17 +15,14 @@
 // same with Box[S_k], Box[C_k] (saved by the forward). Since theta = gamma f,
 // dL/dgamma = sum_p f(p) G_theta(p).
 //
-// The stack (alpha C_k, alpha S_k, beta C_k, beta S_k) is recomputed from f,
-// g, out and den with the same vertical-walker / horizontal-window tile
-// organisation as the forward kernel; it is never stored.
+// The stack (alpha C_k, alpha S_k, beta C_k, beta S_k) is recomputed from g
+// and the forward's saved quads (f, 1/den, out, dnum - out dden) with the same
+// vertical-walker / horizontal-window tile organisation as the forward
+// kernel; it is never stored.
 #include "bf_internal.cuh"
 
 namespace bf {
 
-__device__ __forceinline__ float bload(const float* p, size_t i) { return __ldg(p + i); }
-__device__ __forceinline__ float bload(const __nv_bfloat16* p, size_t i) {
-    return __bfloat162float(p[i]);
-}
 
 struct BSeed {
     float zc, zs, wc, ws;
@@ -49,11 +46,10 @@ __device__ __forceinline__ void brot(float& zc, float& zs, float wc, float ws) {
     zs = ns;
 }
 
-template <int KMAX, typename Tin>
+template <int KMAX>
 __global__ void __launch_bounds__(256, 1) bf_bwd_strip_kernel(BwdParams p) {
     extern __shared__ float4 vrow[];
     __shared__ float red[32];
-    const Tin* img = static_cast<const Tin*>(p.img);
     const int NT = blockDim.x;
     const int j = threadIdx.x;
     const int x0 = blockIdx.x * p.Tw;
@@ -77,15 +73,17 @@ __global__ void __launch_bounds__(256, 1) bf_bwd_strip_kernel(BwdParams p) {
         float fe = 0.f, ae = 0.f, be = 0.f, fl = 0.f, al = 0.f, bl = 0.f;
         if (me) {
             const size_t q = (size_t)e * p.W + c;
-            fe = bload(img, q);
-            ae = __ldg(p.gout + q) / __ldg(p.sv_den + q);
-            be = -ae * __ldg(p.out + q);
+            const float4 sv = __ldg(p.sv + q);
+            fe = sv.x;
+            ae = __ldg(p.gout + q) * sv.y;
+            be = -ae * sv.z;
         }
         if (ml) {
             const size_t q = (size_t)l * p.W + c;
-            fl = bload(img, q);
-            al = __ldg(p.gout + q) / __ldg(p.sv_den + q);
-            bl = -al * __ldg(p.out + q);
+            const float4 sv = __ldg(p.sv + q);
+            fl = sv.x;
+            al = __ldg(p.gout + q) * sv.y;
+            bl = -al * sv.z;
         }
         BSeed se = bseed(fe, p.gamma, p.kstart, me);
         BSeed sl = bseed(fl, p.gamma, p.kstart, ml);
@@ -108,9 +106,9 @@ __global__ void __launch_bounds__(256, 1) bf_bwd_strip_kernel(BwdParams p) {
         __syncthreads();
         if (is_out) {
             const size_t o = (size_t)rho * p.W + c;
-            const float fc = bload(img, o);
-            const float ac = __ldg(p.gout + o) / __ldg(p.sv_den + o);
-            const float bc = -ac * __ldg(p.out + o);
+            const float4 svc = __ldg(p.sv + o);
+            const float fc = svc.x;
+            const float ac = __ldg(p.gout + o) * svc.y;
             BSeed sc = bseed(fc, p.gamma, p.kstart, true);
             float gv = 0.f, gt = 0.f;
 #pragma unroll 1
@@ -127,7 +125,7 @@ __global__ void __launch_bounds__(256, 1) bf_bwd_strip_kernel(BwdParams p) {
                 gt += ak * (fc * (h.y * sc.zc - h.x * sc.zs) + (h.w * sc.zc - h.z * sc.zs));
                 brot(sc.zc, sc.zs, sc.wc, sc.ws);
             }
-            gt += ac * __ldg(p.sv_dnum + o) + bc * __ldg(p.sv_dden + o);
+            gt += ac * svc.w;
             if (p.gimg) p.gimg[o] = gv + p.gamma * gt;
             gsum += fc * gt;
         }
@@ -161,9 +159,9 @@ __global__ void bf_reduce_sigma_kernel(const float* partial, int n, float scale,
     if (threadIdx.x == 0) *dst = (float)(acc[0] * (double)scale);
 }
 
-template <int KMAX, typename Tin>
+template <int KMAX>
 static cudaError_t blaunch_t(const BwdParams& p, int nt, cudaStream_t s) {
-    auto kern = bf_bwd_strip_kernel<KMAX, Tin>;
+    auto kern = bf_bwd_strip_kernel<KMAX>;
     const size_t smem = (size_t)p.K * nt * sizeof(float4);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
@@ -173,17 +171,18 @@ static cudaError_t blaunch_t(const BwdParams& p, int nt, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-template <typename Tin>
 static cudaError_t blaunch_k(const BwdParams& p, int nt, cudaStream_t s) {
-    if (p.K <= 8) return blaunch_t<8, Tin>(p, nt, s);
-    if (p.K <= 16) return blaunch_t<16, Tin>(p, nt, s);
-    if (p.K <= 24) return blaunch_t<24, Tin>(p, nt, s);
-    return blaunch_t<KCAP, Tin>(p, nt, s);
+    if (p.K <= 8) return blaunch_t<8>(p, nt, s);
+    if (p.K <= 16) return blaunch_t<16>(p, nt, s);
+    if (p.K <= 24) return blaunch_t<24>(p, nt, s);
+    return blaunch_t<KCAP>(p, nt, s);
 }
 
+// The saved quads carry f already decoded to FP32, so the input dtype does
+// not matter here.
 cudaError_t launch_backward(const BwdParams& p, int nt, int in_dtype, cudaStream_t s) {
-    if (in_dtype == BF_BF16) return blaunch_k<__nv_bfloat16>(p, nt, s);
-    return blaunch_k<float>(p, nt, s);
+    (void)in_dtype;
+    return blaunch_k(p, nt, s);
 }
 
 cudaError_t launch_reduce_sigma(const float* partial, int n, float scale, float* dst,

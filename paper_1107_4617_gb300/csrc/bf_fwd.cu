@@ -133,12 +133,10 @@ __device__ __forceinline__ void fwd_tile(const FwdParams& p, int bx, int by, flo
                 rotate(sc.zc, sc.zs, sc.wc, sc.ws);
             }
             const size_t o = (size_t)rho * p.W + c;
-            p.out[o] = num / den;
-            if (p.sv_den) {
-                p.sv_den[o] = den;
-                p.sv_dnum[o] = dnum;
-                p.sv_dden[o] = dden;
-            }
+            const float ov = num / den;
+            p.out[o] = ov;
+            // saved for the adjoint: (f, 1/den, out, dnum - out dden)
+            if (p.sv) p.sv[o] = make_float4(fc, 1.0f / den, ov, dnum - ov * dden);
         }
         __syncthreads();
     }

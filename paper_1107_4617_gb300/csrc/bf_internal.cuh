@@ -20,9 +20,7 @@ constexpr int KCAP = BF_N_MAX / 2 + 1;
 struct FwdParams {
     const void* img;      // H x W, FP32 or BF16
     float* out;           // H x W
-    float* sv_den;        // saved den (nullable)
-    float* sv_dnum;       // saved d num / d s   (nullable)
-    float* sv_dden;       // saved d den / d s   (nullable)
+    float4* sv;           // saved quads (f, 1/den, out, dnum - out dden); nullable
     int H, W, r;
     int K;                // number of harmonics
     int kstart;           // N mod 2: frequency of harmonic 0
@@ -34,11 +32,8 @@ struct FwdParams {
 
 struct BwdParams {
     const void* img;      // forward input
-    const float* out;     // forward output
     const float* gout;    // dL/dout
-    const float* sv_den;
-    const float* sv_dnum;
-    const float* sv_dden;
+    const float4* sv;     // the forward's saved quads
     float* gimg;          // dL/dimg (nullable)
     float* partial;       // per-CTA sums of f * dL/dtheta (nullable)
     int H, W, r, K, kstart, Hb, Tw;
@@ -53,14 +48,9 @@ constexpr int SYS_MAX_THREADS = 256;
 struct SysParams {
     const void* img;
     float* out;                 // forward output
-    float* sv_den;              // forward saved buffers (SAVE)
-    float* sv_dnum;
-    float* sv_dden;
-    const float* fout;          // adjoint: forward output
+    float4* sv;                 // forward: saved quads (SAVE)
     const float* gout;          // adjoint: dL/dout
-    const float* bden;          // adjoint: saved den, d num/ds, d den/ds
-    const float* bdnum;
-    const float* bdden;
+    const float4* bsv;          // adjoint: the forward's saved quads
     float* gimg;                // adjoint: dL/dimg (nullable)
     float* partial;             // adjoint: per-CTA sum of f * dL/dtheta (nullable)
     float* acc_den;             // forward chunk accumulator for den when not saving

@@ -7,18 +7,18 @@
 
 namespace bf {
 
-template <int KPMAX, typename Tin>
+template <int KPMAX, int WMAX, typename Tin>
 __device__ __forceinline__ void run_chunk(const SysParams& p, int kp, int bx, int by,
                                           float4* smem) {
     float gsum = 0.f;
     switch (kp) {
-        case 1: sysd::sys_tile<1, false, false, false, Tin>(p, bx, by, 0, 0, smem, gsum); break;
-        case 2: sysd::sys_tile<2, false, false, false, Tin>(p, bx, by, 0, 0, smem, gsum); break;
-        case 3: sysd::sys_tile<3, false, false, false, Tin>(p, bx, by, 0, 0, smem, gsum); break;
-        case 4: sysd::sys_tile<4, false, false, false, Tin>(p, bx, by, 0, 0, smem, gsum); break;
-        case 6: sysd::sys_tile<6, false, false, false, Tin>(p, bx, by, 0, 0, smem, gsum); break;
-        case 8: sysd::sys_tile<8, false, false, false, Tin>(p, bx, by, 0, 0, smem, gsum); break;
-        default: sysd::sys_tile<KPMAX, false, false, false, Tin>(p, bx, by, 0, 0, smem, gsum); break;
+        case 1: sysd::sys_tile<1, false, false, false, WMAX, Tin>(p, bx, by, 0, smem, gsum); break;
+        case 2: sysd::sys_tile<2, false, false, false, WMAX, Tin>(p, bx, by, 0, smem, gsum); break;
+        case 3: sysd::sys_tile<3, false, false, false, WMAX, Tin>(p, bx, by, 0, smem, gsum); break;
+        case 4: sysd::sys_tile<4, false, false, false, WMAX, Tin>(p, bx, by, 0, smem, gsum); break;
+        case 6: sysd::sys_tile<6, false, false, false, WMAX, Tin>(p, bx, by, 0, smem, gsum); break;
+        case 8: sysd::sys_tile<8, false, false, false, WMAX, Tin>(p, bx, by, 0, smem, gsum); break;
+        default: sysd::sys_tile<KPMAX, false, false, false, WMAX, Tin>(p, bx, by, 0, smem, gsum); break;
     }
 }
 
@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(WMAX, 256 / WMAX) bf_sys_batch_kernel(SysBatch
             for (int i = threadIdx.x; i < (int)(sizeof(SysParams) / 4); i += blockDim.x)
                 reinterpret_cast<int*>(&sp)[i] = reinterpret_cast<const int*>(&im.ch[c])[i];
             __syncthreads();
-            run_chunk<SYS_KP_MAX, Tin>(sp, im.kp[c], bx, by, smem);
+            run_chunk<SYS_KP_MAX, WMAX, Tin>(sp, im.kp[c], bx, by, smem);
         }
         __syncthreads();
     }
@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(WMAX, 256 / WMAX) bf_sys_batch_kernel(SysBatch
 template <int WMAX, typename Tin>
 static cudaError_t batch_launch(SysBatchTable* tab, int group, int wi, int grid, cudaStream_t s) {
     auto kern = bf_sys_batch_kernel<WMAX, Tin>;
-    const size_t smem = sizeof(float4) * (size_t)sysd::sys_smem_slots(SYS_KP_MAX, wi);
+    const size_t smem = sizeof(float4) * (size_t)sysd::sys_smem_slots(SYS_KP_MAX, WMAX);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;

@@ -9,19 +9,27 @@
 //    2r+1 rows of the window -- of the DIFFERENCE D = V(cw(j)) -
 //    V(cw(j) - 2r - 1) of two columns. Per row it adds the entering pixel's
 //    planes of both columns and subtracts the leaving ones. All four pixels'
-//    planes are regenerated from f (one MUFU sincos per pixel, harmonics by
-//    complex rotation z_{k+2} = z_k z_2), so no plane is ever stored.
+//    planes are regenerated from f (one MUFU sincos per pixel, harmonic
+//    pairs by a three-term recurrence), so no plane is ever stored.
 //  * horizontal: the window sum S(j) = sum_{i=j-2r..j} V(cw(i)) obeys
 //    S(j) = S(j-1) + D(j). Thread j processes output row rho at step
 //    t = rho_index + j, one step after thread j-1 produced S(j-1) for the
-//    same row, and reads it from a one-row shared buffer (a double-buffered
-//    slot per warp carries it across warp boundaries). The strip is swept
-//    on a skew of one row per column.
+//    same row, and reads it from a shared row buffer that is double-buffered
+//    by step parity (so one CTA barrier per step orders every exchange, across
+//    warps too). The strip is swept on a skew of one row per column.
 //
 // S(j) is the full box sum centred on column cw(j) - r; thread j combines it
 // with that centre pixel's C_k, S_k and a_k (Algorithm 2 step 3). Per
 // harmonic a thread keeps 4 floats of state (D) in registers; S passes
 // through shared memory (16 B written and read per harmonic and step).
+//
+// Harmonics come in pairs (k, k+2), packed in FP32x2 registers. Pair i+1
+// follows from pairs i and i-1 by cos((n+1)x) = 2 cos(x) cos(nx) -
+// cos((n-1)x) with x = 4 theta (the shift identity of Sec. 1 applied twice).
+// Every stream stores pair i multiplied by s_i = (-1)^(i/2), which turns the
+// recurrence into d_{i+1} = (+-m) d_i + d_{i-1}, m = 2 cos 4 theta, with no
+// negation; since all planes of pair i carry the same s_i and the
+// recombination multiplies two of them, the sign cancels there.
 #pragma once
 #include "bf_internal.cuh"
 
@@ -30,18 +38,10 @@ namespace sysd {
 
 constexpr unsigned FULL = 0xffffffffu;
 
-__device__ __forceinline__ float ld_img(const float* p, size_t i) { return __ldg(p + i); }
-__device__ __forceinline__ float ld_img(const __nv_bfloat16* p, size_t i) {
+__device__ __forceinline__ float ld_img(const float* p, int i) { return __ldg(p + i); }
+__device__ __forceinline__ float ld_img(const __nv_bfloat16* p, int i) {
     return __bfloat162float(p[i]);
 }
-
-// Rotation state of one pixel stream, two harmonics at a time (packed FP32
-// pairs): zc/zs hold (cos, sin) of harmonics k and k+2; both advance by
-// w^2 = e^{4 i theta} per pair. c2, s2, ns2 = (cos 4theta, sin 4theta,
-// -sin 4theta) duplicated in both halves. A masked stream has z = 0.
-struct Rot2 {
-    float2 zc, zs, c2, s2, ns2;
-};
 
 // k0 theta reduced to [-pi, pi] (two-term Cody-Waite reduction by 2 pi;
 // 2 pi = TWO_PI_HI + TWO_PI_LO with TWO_PI_HI = 6.28125 exact in 9 bits, so
@@ -56,9 +56,17 @@ __device__ __forceinline__ void sincos_reduced(float x, float* s, float* c) {
     __sincosf(y, s, c);
 }
 
+__device__ __forceinline__ float2 dup(float v) { return make_float2(v, v); }
+
+// One pixel stream: signed harmonic pairs i (c, s) and i+1 (nc, ns), each
+// (harmonic k0 + 4i, harmonic k0 + 4i + 2); m = (2 cos 4 theta) twice, nm = -m.
+struct Strm {
+    float2 c, s, nc, ns, m, nm;
+};
+
 // k0 = frequency of the first harmonic (k0 <= 1 for an unchunked filter; a
 // later harmonic chunk starts at k0 = kstart + 2 i0 and seeds from k0 theta).
-__device__ __forceinline__ Rot2 seed2(float f, float gamma, float gpi, int k0, bool on) {
+__device__ __forceinline__ Strm seed(float f, float gamma, int k0) {
     float sn, cs;
     __sincosf(gamma * f, &sn, &cs);
     const float wc = (cs - sn) * (cs + sn);   // e^{2 i theta}
@@ -69,34 +77,30 @@ __device__ __forceinline__ Rot2 seed2(float f, float gamma, float gpi, int k0, b
     else sincos_reduced((float)k0 * (gamma * f), &z0s, &z0c);
     const float z1c = fmaf(z0c, wc, -z0s * ws);  // harmonic k0 + 2
     const float z1s = fmaf(z0s, wc, z0c * ws);
-    const float w2c = fmaf(wc, wc, -ws * ws);    // e^{4 i theta}
-    const float w2s = 2.0f * wc * ws;
-    Rot2 r;
-    r.zc = on ? make_float2(z0c, z1c) : make_float2(0.f, 0.f);
-    r.zs = on ? make_float2(z0s, z1s) : make_float2(0.f, 0.f);
-    r.c2 = make_float2(w2c, w2c);
-    r.s2 = make_float2(w2s, w2s);
-    r.ns2 = make_float2(-w2s, -w2s);
-    return r;
+    const float w4c = fmaf(wc, wc, -ws * ws);    // e^{4 i theta}
+    const float w4s = 2.0f * wc * ws;
+    Strm q;
+    q.c = make_float2(z0c, z1c);
+    q.s = make_float2(z0s, z1s);
+    // pair 1 = pair 0 * e^{4 i theta} (s_1 = +1)
+    q.nc = __ffma2_rn(q.s, dup(-w4s), __fmul2_rn(q.c, dup(w4c)));
+    q.ns = __ffma2_rn(q.c, dup(w4s), __fmul2_rn(q.s, dup(w4c)));
+    q.m = dup(2.0f * w4c);
+    q.nm = dup(-2.0f * w4c);
+    return q;
 }
 
-__device__ __forceinline__ void rot2(Rot2& s) {
-    const float2 c = __ffma2_rn(s.zs, s.ns2, __fmul2_rn(s.zc, s.c2));
-    const float2 n = __ffma2_rn(s.zc, s.s2, __fmul2_rn(s.zs, s.c2));
-    s.zc = c;
-    s.zs = n;
-}
-
-__device__ __forceinline__ float2 dup(float v) { return make_float2(v, v); }
-
-// Predicated shared store (lane 31's hand-off to the next warp): one
-// instruction, no branch inside the unrolled harmonic loop.
-__device__ __forceinline__ void st_shared_if(float4* dst, float4 v, bool pred) {
-    const unsigned a = (unsigned)__cvta_generic_to_shared(dst);
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %5, 0;\n\t"
-        "@p st.shared.v4.f32 [%0], {%1, %2, %3, %4};\n\t}"
-        :: "r"(a), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "r"((int)pred) : "memory");
+// Step from pair i to pair i+1 and form pair i+2 when it is needed:
+// d_{i+2} = (i+1 even ? m : -m) d_{i+1} + d_i.
+__device__ __forceinline__ void advance(Strm& q, int i, bool need) {
+    if (need) {
+        const float2 mm = ((i + 1) & 1) ? q.nm : q.m;
+        const float2 c2 = __ffma2_rn(mm, q.nc, q.c);
+        const float2 s2 = __ffma2_rn(mm, q.ns, q.s);
+        q.c = q.nc; q.s = q.ns; q.nc = c2; q.ns = s2;
+    } else {
+        q.c = q.nc; q.s = q.ns;
+    }
 }
 
 // Rows ahead of the current entering row that are pulled into L2.
@@ -114,110 +118,96 @@ template <>
 struct Px<false> {
     float f;
 };
+// Adjoint: the forward's saved quad of the pixel (f, 1/den, out,
+// dnum - out * dden) and dL/dout.
 template <>
 struct Px<true> {
-    float f, g, den, out;
-    float dnum, dden;  // centre stream only: saved d num/ds, d den/ds
+    float4 sv;
+    float g;
 };
 
-// zo / zs: element offsets of this image in the image-sized and the saved
-// (3 planes per image) buffers of a [B, H, W] launch.
-template <bool BWD, typename Tin>
-__device__ __forceinline__ void load_px(Px<BWD>& v, const SysParams& p, const Tin* img, bool on,
-                                        size_t q, size_t zo, size_t zs) {
-    if (!on) {
-        v.f = 0.f;
-        if constexpr (BWD) { v.g = 0.f; v.den = 1.f; v.out = 0.f; v.dnum = 0.f; v.dden = 0.f; }
-        return;
-    }
-    v.f = ld_img(img, q + zo);
-    if constexpr (BWD) {
-        v.g = __ldg(p.gout + q + zo);
-        v.den = __ldg(p.bden + q + zs);
-        v.out = __ldg(p.fout + q + zo);
-    }
-}
+// Base pointers of one image of a [B, H, W] launch.
+template <typename Tin>
+struct Bases {
+    const Tin* img;
+    const float* gout;
+    const float4* bsv;
+};
 
-// The centre stream also needs the forward's saved centre derivatives.
+// Masked loads leave neutral values (f = 0; in the adjoint g = 0, so the
+// plane weights alpha, beta are 0); the forward masks its own weights.
 template <bool BWD, typename Tin>
-__device__ __forceinline__ void load_centre(Px<BWD>& v, const SysParams& p, const Tin* img,
-                                            bool on, size_t q, size_t zo, size_t zs) {
-    load_px<BWD, Tin>(v, p, img, on, q, zo, zs);
-    if constexpr (BWD) {
+__device__ __forceinline__ void load_px(Px<BWD>& v, const Bases<Tin>& b, bool on, int q) {
+    if constexpr (!BWD) {
+        v.f = 0.f;
+        if (on) v.f = ld_img(b.img, q);
+    } else {
+        v.sv = make_float4(0.f, 0.f, 0.f, 0.f);
+        v.g = 0.f;
         if (on) {
-            v.dnum = __ldg(p.bdnum + q + zs);
-            v.dden = __ldg(p.bdden + q + zs);
+            v.sv = __ldg(b.bsv + q);
+            v.g = __ldg(b.gout + q);
         }
     }
 }
 
-// Row/column geometry of thread j at local step tau.
-struct Geo {
-    bool m0, m1, m2, m3, out;
-    size_t q0, q1, q2, q3, qo;
-};
-
-__device__ __forceinline__ Geo geometry(const SysParams& p, int tau, int span, int y0, int cw,
-                                        int c2, int co, bool own_in, bool sec_in, bool out_lane) {
-    const int r = p.r;
-    const bool act = tau >= 0 && tau < span;
-    const int e = y0 - r + tau;
-    const int l = e - 2 * r - 1;
-    const int rho = y0 - 2 * r + tau;
-    const bool in_e = act && e >= 0 && e < p.H;
-    const bool in_l = act && tau >= 2 * r + 1 && l >= 0 && l < p.H;
-    Geo g;
-    g.m0 = in_e && own_in;
-    g.m1 = in_e && sec_in;
-    g.m2 = in_l && own_in;
-    g.m3 = in_l && sec_in;
-    g.out = act && tau >= 2 * r && out_lane;
-    const size_t re = (size_t)(in_e ? e : 0) * p.W, rl = (size_t)(in_l ? l : 0) * p.W;
-    g.q0 = re + (g.m0 ? cw : 0);
-    g.q1 = re + (g.m1 ? c2 : 0);
-    g.q2 = rl + (g.m2 ? cw : 0);
-    g.q3 = rl + (g.m3 ? c2 : 0);
-    g.qo = g.out ? (size_t)rho * p.W + co : 0;
-    return g;
+template <bool BWD>
+__device__ __forceinline__ float pix_f(const Px<BWD>& v) {
+    if constexpr (BWD) return v.sv.x; else return v.f;
 }
 
+// Masks and element offsets of one step's five pixels (entering and leaving
+// row of the own and the second column, centre).
+struct Geo {
+    bool m0, m1, m2, m3, out;
+    int q0, q1, q2, q3, qo;
+};
 
-// Shared-memory float4 slots one tile needs (KP harmonic pairs, Wi threads).
-__host__ __device__ constexpr int sys_smem_slots(int KP, int Wi) {
-    return 2 * KP * Wi + 2 * (Wi / 32) * 2 * KP + 2 * KP;
+// Float4 slots of shared memory one tile needs: two step-parity buffers of
+// 2 KP planes x (WMAX + 1) columns (column 0 stays zero: the first lane's
+// carry-in).
+__host__ __device__ constexpr int sys_smem_slots(int KP, int WMAX) {
+    return 2 * 2 * KP * (WMAX + 1);
 }
 
 // One strip x band tile (bx, by) of one image, for one chunk of harmonics.
 // Called uniformly by every thread of the CTA. gsum accumulates f * dL/dtheta
 // (adjoint, last chunk only). KAHAN compensates the vertical running sums.
-template <int KP, bool BWD, bool SAVE, bool KAHAN, typename Tin>
-__device__ __forceinline__ void sys_tile(const SysParams& p, int bx, int by, size_t zo, size_t zs,
+// zo: element offset of this image in the image-sized buffers (and quad
+// offset in the saved buffer).
+template <int KP, bool BWD, bool SAVE, bool KAHAN, int WMAX, typename Tin>
+__device__ __forceinline__ void sys_tile(const SysParams& p, int bx, int by, size_t zo,
                                          float4* smem, float& gsum) {
+    constexpr int LD = WMAX + 1;          // row of one plane in shared memory
+    constexpr int BUF = 2 * KP * LD;      // one step-parity buffer
     const int Wi = blockDim.x;
-    const int NW = Wi >> 5;
-    // S of each lane at the last step: [KP][2][Wi] float4, i.e. per harmonic
-    // pair (x_k, x_k+2, y_k, y_k+2) and (z_k, z_k+2, w_k, w_k+2)
-    float4* sbuf = smem;
-    float4* xfer = smem + 2 * KP * Wi;        // [2][NW][KP][2]: lane 31 -> next warp
-    float4* zero = xfer + 2 * NW * 2 * KP;    // [KP][2]: carry-in of the first lane
-    const Tin* img = static_cast<const Tin*>(p.img);
     const int j = threadIdx.x;
-    const int lane = j & 31;
     const int w = j >> 5;
     const int r = p.r;
+    const int W = p.W;
     const int x0 = bx * p.Tw;
     const int cw = x0 - r + j;            // own column
     const int c2 = cw - 2 * r - 1;        // column leaving the horizontal window
     const int co = cw - r;                // output (centre) column
-    const bool own_in = cw >= 0 && cw < p.W;
-    const bool sec_in = (j >= 2 * r + 1) && c2 >= 0 && c2 < p.W;
-    const bool out_lane = (j >= 2 * r) && co < p.W;
+    const bool own_in = cw >= 0 && cw < W;
+    const bool sec_in = (j >= 2 * r + 1) && c2 >= 0 && c2 < W;
+    const bool out_lane = (j >= 2 * r) && co < W;
     const int y0 = by * p.Hb;
     const int rows = min(p.Hb, p.H - y0);
     const int span = rows + 2 * r;        // local steps of one thread
     const int steps = span + Wi - 1;
+    // rows that enter or leave the window: [elo, elo + ne)
+    const int elo = max(0, y0 - r);
+    const int ne = min(p.H, y0 + rows + r) - elo;
 
-    for (int i = threadIdx.x; i < sys_smem_slots(KP, Wi); i += Wi)
+    Bases<Tin> b;
+    b.img = static_cast<const Tin*>(p.img) + zo;
+    if constexpr (BWD) {
+        b.gout = p.gout + zo;
+        b.bsv = p.bsv + zo;
+    }
+
+    for (int i = threadIdx.x; i < sys_smem_slots(KP, WMAX); i += Wi)
         smem[i] = make_float4(0.f, 0.f, 0.f, 0.f);
 
     float2 Dx[KP], Dy[KP], Dz[KP], Dw[KP];
@@ -228,15 +218,39 @@ __device__ __forceinline__ void sys_tile(const SysParams& p, int bx, int by, siz
         if constexpr (KAHAN) { Ex[i] = Dx[i]; Ey[i] = Dx[i]; Ez[i] = Dx[i]; Ew[i] = Dx[i]; }
     }
 
+    // geometry of step t: entering row e = e0 + t, its element offset oe
+    const int e0 = y0 - r - j;
+    auto geometry = [&](int t) {
+        const int e = e0 + t;
+        const int tau = t - j;
+        const int oe = e * W;
+        const bool act = (unsigned)tau < (unsigned)span;
+        const bool in_e = act && (unsigned)(e - elo) < (unsigned)ne;
+        const bool in_l = act && (unsigned)(e - 2 * r - 1 - elo) < (unsigned)ne &&
+                          tau >= 2 * r + 1;
+        Geo g;
+        g.m0 = in_e && own_in;
+        g.m1 = in_e && sec_in;
+        g.m2 = in_l && own_in;
+        g.m3 = in_l && sec_in;
+        g.out = act && out_lane && (unsigned)(e - r - y0) < (unsigned)rows;
+        g.q0 = oe + cw;
+        g.q1 = oe + c2;
+        g.q2 = oe - (2 * r + 1) * W + cw;
+        g.q3 = oe - (2 * r + 1) * W + c2;
+        g.qo = oe - r * W + co;
+        return g;
+    };
+
     // pixel values of the current step, loaded during the previous one
     Px<BWD> v0, v1, v2, v3, vc;
     // a warp is first active at step 32 w; start its prefetch chain there
-    Geo g = geometry(p, w * 32 - j, span, y0, cw, c2, co, own_in, sec_in, out_lane);
-    load_px<BWD, Tin>(v0, p, img, g.m0, g.q0, zo, zs);
-    load_px<BWD, Tin>(v1, p, img, g.m1, g.q1, zo, zs);
-    load_px<BWD, Tin>(v2, p, img, g.m2, g.q2, zo, zs);
-    load_px<BWD, Tin>(v3, p, img, g.m3, g.q3, zo, zs);
-    load_centre<BWD, Tin>(vc, p, img, g.out, g.qo, zo, zs);
+    Geo g = geometry(w * 32);
+    load_px<BWD, Tin>(v0, b, g.m0, g.q0);
+    load_px<BWD, Tin>(v1, b, g.m1, g.q1);
+    load_px<BWD, Tin>(v2, b, g.m2, g.q2);
+    load_px<BWD, Tin>(v3, b, g.m3, g.q3);
+    load_px<BWD, Tin>(vc, b, g.out, g.qo);
     __syncthreads();
 
     for (int t = 0; t < steps; ++t) {
@@ -248,86 +262,80 @@ __device__ __forceinline__ void sys_tile(const SysParams& p, int bx, int by, siz
             // pull the entering row of a later step into L2 (no registers held):
             // the other four streams re-read pixels the strip touched recently
             {
-                const int ef = y0 - r + (t + PREFETCH_ROWS - j);
-                // (forward only: the adjoint's four extra streams made it slower)
-                if (!BWD && own_in && ef >= 0 && ef < p.H)
-                    prefetch_l2(static_cast<const Tin*>(p.img) + zo + (size_t)ef * p.W + cw);
+                const int ef = e0 + t + PREFETCH_ROWS;
+                // (forward only: the adjoint's extra streams made it slower)
+                if (!BWD && own_in && ef >= 0 && ef < p.H) prefetch_l2(b.img + ef * W + cw);
             }
             // prefetch the next step's pixels; their latency hides under this step
-            g = geometry(p, t + 1 - j, span, y0, cw, c2, co, own_in, sec_in, out_lane);
-            load_px<BWD, Tin>(v0, p, img, g.m0, g.q0, zo, zs);
-            load_px<BWD, Tin>(v1, p, img, g.m1, g.q1, zo, zs);
-            load_px<BWD, Tin>(v2, p, img, g.m2, g.q2, zo, zs);
-            load_px<BWD, Tin>(v3, p, img, g.m3, g.q3, zo, zs);
-            load_centre<BWD, Tin>(vc, p, img, g.out, g.qo, zo, zs);
+            g = geometry(t + 1);
+            load_px<BWD, Tin>(v0, b, g.m0, g.q0);
+            load_px<BWD, Tin>(v1, b, g.m1, g.q1);
+            load_px<BWD, Tin>(v2, b, g.m2, g.q2);
+            load_px<BWD, Tin>(v3, b, g.m3, g.q3);
+            load_px<BWD, Tin>(vc, b, g.out, g.qo);
 
-            Rot2 s0 = seed2(c0.f, p.gamma, p.gpi, p.k0, gc.m0);
-            Rot2 s1 = seed2(c1.f, p.gamma, p.gpi, p.k0, gc.m1);
-            Rot2 s2 = seed2(c2v.f, p.gamma, p.gpi, p.k0, gc.m2);
-            Rot2 s3 = seed2(c3.f, p.gamma, p.gpi, p.k0, gc.m3);
-            Rot2 sc = seed2(cc.f, p.gamma, p.gpi, p.k0, gc.out);
+            Strm s0 = seed(pix_f(c0), p.gamma, p.k0);
+            Strm s1 = seed(pix_f(c1), p.gamma, p.k0);
+            Strm s2 = seed(pix_f(c2v), p.gamma, p.k0);
+            Strm s3 = seed(pix_f(c3), p.gamma, p.k0);
+            Strm sc = seed(pix_f(cc), p.gamma, p.k0);
             // plane weights (u: first two planes, v: last two) with the stream's
-            // sign: + own enter, - second enter, - own leave, + second leave
+            // sign: + own enter, - second enter, - own leave, + second leave;
+            // 0 for a masked stream
             float2 U0, U1, U2, U3, V0, V1, V2, V3;
-            float ac = 0.f, bc = 0.f;
+            float xc = 0.f;  // adjoint: alpha dnum + beta dden of the centre
             if constexpr (!BWD) {
                 U0 = dup(c0.f); U1 = dup(-c1.f); U2 = dup(-c2v.f); U3 = dup(c3.f);
-                V0 = dup(1.f); V1 = dup(-1.f); V2 = dup(-1.f); V3 = dup(1.f);
+                V0 = dup(gc.m0 ? 1.f : 0.f); V1 = dup(gc.m1 ? -1.f : 0.f);
+                V2 = dup(gc.m2 ? -1.f : 0.f); V3 = dup(gc.m3 ? 1.f : 0.f);
             } else {
-                const float a0 = __fdividef(c0.g, c0.den), a1 = __fdividef(c1.g, c1.den);
-                const float a2 = __fdividef(c2v.g, c2v.den), a3 = __fdividef(c3.g, c3.den);
+                // alpha = g / den, beta = -alpha out
+                const float a0 = c0.g * c0.sv.y, a1 = c1.g * c1.sv.y;
+                const float a2 = c2v.g * c2v.sv.y, a3 = c3.g * c3.sv.y;
                 U0 = dup(a0); U1 = dup(-a1); U2 = dup(-a2); U3 = dup(a3);
-                V0 = dup(-a0 * c0.out); V1 = dup(a1 * c1.out);
-                V2 = dup(a2 * c2v.out); V3 = dup(-a3 * c3.out);
-                ac = __fdividef(cc.g, cc.den);
-                bc = -ac * cc.out;
+                V0 = dup(-a0 * c0.sv.z); V1 = dup(a1 * c1.sv.z);
+                V2 = dup(a2 * c2v.sv.z); V3 = dup(-a3 * c3.sv.z);
+                xc = cc.g * cc.sv.y * cc.sv.w;
             }
-            const float2 FC = dup(cc.f);
+            const float2 FC = dup(pix_f(cc));
 
-            // where this lane reads its left neighbour's S of the previous step
-            const float4* rd;
-            int rstride;
-            if (lane != 0) { rd = sbuf + (j - 1); rstride = Wi; }
-            else if (w != 0) { rd = xfer + (((t + 1) & 1) * NW + (w - 1)) * 2 * KP; rstride = 1; }
-            else { rd = zero; rstride = 1; }
-            float4* wr = sbuf + j;
-            float4* wx = xfer + ((t & 1) * NW + w) * 2 * KP;
-            const bool carry = (lane == 31) && (w + 1 < NW);
+            // left neighbour's S of the previous step (column j of the other
+            // buffer; column 0 is the zero carry-in of the first lane), and
+            // this lane's slot (column j + 1)
+            const float4* rd = smem + ((t + 1) & 1) * BUF + j;
+            float4* wr = smem + (t & 1) * BUF + j + 1;
 
             float2 NUM = make_float2(0.f, 0.f), DEN = NUM, DNUM = NUM, DDEN = NUM;
-            // carry-ins read one pair ahead: a slot of pair i is only rewritten
-            // after the __syncwarp of iteration i, so earlier reads are safe
-            float4 ina = rd[0], inb = rd[rstride];
 #pragma unroll
             for (int i = 0; i < KP; ++i) {
-                const float4 A = ina, B = inb;
-                if (i + 1 < KP) { ina = rd[(2 * i + 2) * rstride]; inb = rd[(2 * i + 3) * rstride]; }
+                const float4 A = rd[(2 * i) * LD];
+                const float4 B = rd[(2 * i + 1) * LD];
                 float2 dx, dy, dz, dw;
                 if constexpr (!KAHAN) {
                     dx = Dx[i]; dy = Dy[i]; dz = Dz[i]; dw = Dw[i];
-                    dx = __ffma2_rn(s0.zc, U0, dx); dx = __ffma2_rn(s1.zc, U1, dx);
-                    dx = __ffma2_rn(s2.zc, U2, dx); dx = __ffma2_rn(s3.zc, U3, dx);
-                    dy = __ffma2_rn(s0.zs, U0, dy); dy = __ffma2_rn(s1.zs, U1, dy);
-                    dy = __ffma2_rn(s2.zs, U2, dy); dy = __ffma2_rn(s3.zs, U3, dy);
-                    dz = __ffma2_rn(s0.zc, V0, dz); dz = __ffma2_rn(s1.zc, V1, dz);
-                    dz = __ffma2_rn(s2.zc, V2, dz); dz = __ffma2_rn(s3.zc, V3, dz);
-                    dw = __ffma2_rn(s0.zs, V0, dw); dw = __ffma2_rn(s1.zs, V1, dw);
-                    dw = __ffma2_rn(s2.zs, V2, dw); dw = __ffma2_rn(s3.zs, V3, dw);
+                    dx = __ffma2_rn(s0.c, U0, dx); dx = __ffma2_rn(s1.c, U1, dx);
+                    dx = __ffma2_rn(s2.c, U2, dx); dx = __ffma2_rn(s3.c, U3, dx);
+                    dy = __ffma2_rn(s0.s, U0, dy); dy = __ffma2_rn(s1.s, U1, dy);
+                    dy = __ffma2_rn(s2.s, U2, dy); dy = __ffma2_rn(s3.s, U3, dy);
+                    dz = __ffma2_rn(s0.c, V0, dz); dz = __ffma2_rn(s1.c, V1, dz);
+                    dz = __ffma2_rn(s2.c, V2, dz); dz = __ffma2_rn(s3.c, V3, dz);
+                    dw = __ffma2_rn(s0.s, V0, dw); dw = __ffma2_rn(s1.s, V1, dw);
+                    dw = __ffma2_rn(s2.s, V2, dw); dw = __ffma2_rn(s3.s, V3, dw);
                 } else {
                     // this row's increment of each running sum, then a
                     // Kahan-compensated add (Kahan 1965): y = inc - e,
                     // t = D + y, e = (t - D) - y, D = t
                     const float2 m1 = dup(-1.f);
-                    float2 ix = __fmul2_rn(s0.zc, U0), iy = __fmul2_rn(s0.zs, U0);
-                    float2 iz = __fmul2_rn(s0.zc, V0), iw = __fmul2_rn(s0.zs, V0);
-                    ix = __ffma2_rn(s1.zc, U1, ix); ix = __ffma2_rn(s2.zc, U2, ix);
-                    ix = __ffma2_rn(s3.zc, U3, ix);
-                    iy = __ffma2_rn(s1.zs, U1, iy); iy = __ffma2_rn(s2.zs, U2, iy);
-                    iy = __ffma2_rn(s3.zs, U3, iy);
-                    iz = __ffma2_rn(s1.zc, V1, iz); iz = __ffma2_rn(s2.zc, V2, iz);
-                    iz = __ffma2_rn(s3.zc, V3, iz);
-                    iw = __ffma2_rn(s1.zs, V1, iw); iw = __ffma2_rn(s2.zs, V2, iw);
-                    iw = __ffma2_rn(s3.zs, V3, iw);
+                    float2 ix = __fmul2_rn(s0.c, U0), iy = __fmul2_rn(s0.s, U0);
+                    float2 iz = __fmul2_rn(s0.c, V0), iw = __fmul2_rn(s0.s, V0);
+                    ix = __ffma2_rn(s1.c, U1, ix); ix = __ffma2_rn(s2.c, U2, ix);
+                    ix = __ffma2_rn(s3.c, U3, ix);
+                    iy = __ffma2_rn(s1.s, U1, iy); iy = __ffma2_rn(s2.s, U2, iy);
+                    iy = __ffma2_rn(s3.s, U3, iy);
+                    iz = __ffma2_rn(s1.c, V1, iz); iz = __ffma2_rn(s2.c, V2, iz);
+                    iz = __ffma2_rn(s3.c, V3, iz);
+                    iw = __ffma2_rn(s1.s, V1, iw); iw = __ffma2_rn(s2.s, V2, iw);
+                    iw = __ffma2_rn(s3.s, V3, iw);
                     auto kadd = [&](float2& D, float2& E, float2 inc) {
                         const float2 y = __ffma2_rn(E, m1, inc);
                         const float2 t2 = __fadd2_rn(D, y);
@@ -343,56 +351,67 @@ __device__ __forceinline__ void sys_tile(const SysParams& p, int bx, int by, siz
                 const float2 hy = __fadd2_rn(make_float2(A.z, A.w), dy);
                 const float2 hz = __fadd2_rn(make_float2(B.x, B.y), dz);
                 const float2 hw = __fadd2_rn(make_float2(B.z, B.w), dw);
-                __syncwarp();  // every lane has read its neighbour's slots before they change
-                const float4 oa = make_float4(hx.x, hx.y, hy.x, hy.y);
-                const float4 ob = make_float4(hz.x, hz.y, hw.x, hw.y);
-                wr[(2 * i) * Wi] = oa;
-                wr[(2 * i + 1) * Wi] = ob;
-                st_shared_if(wx + 2 * i, oa, carry);
-                st_shared_if(wx + 2 * i + 1, ob, carry);
+                wr[(2 * i) * LD] = make_float4(hx.x, hx.y, hy.x, hy.y);
+                wr[(2 * i + 1) * LD] = make_float4(hz.x, hz.y, hw.x, hw.y);
                 const float2 A2 = make_float2(p.a[2 * i], p.a[2 * i + 1]);
                 const float2 AK2 = make_float2(p.ak[2 * i], p.ak[2 * i + 1]);
-                const float2 nzs = __fmul2_rn(sc.zs, dup(-1.f));
+                const float2 nzs = __fmul2_rn(sc.s, dup(-1.f));
                 if constexpr (!BWD) {
-                    NUM = __ffma2_rn(A2, __ffma2_rn(sc.zc, hx, __fmul2_rn(sc.zs, hy)), NUM);
-                    DEN = __ffma2_rn(A2, __ffma2_rn(sc.zc, hz, __fmul2_rn(sc.zs, hw)), DEN);
+                    NUM = __ffma2_rn(A2, __ffma2_rn(sc.c, hx, __fmul2_rn(sc.s, hy)), NUM);
+                    DEN = __ffma2_rn(A2, __ffma2_rn(sc.c, hz, __fmul2_rn(sc.s, hw)), DEN);
                     if constexpr (SAVE) {
-                        DNUM = __ffma2_rn(AK2, __ffma2_rn(sc.zc, hy, __fmul2_rn(nzs, hx)), DNUM);
-                        DDEN = __ffma2_rn(AK2, __ffma2_rn(sc.zc, hw, __fmul2_rn(nzs, hz)), DDEN);
+                        DNUM = __ffma2_rn(AK2, __ffma2_rn(sc.c, hy, __fmul2_rn(nzs, hx)), DNUM);
+                        DDEN = __ffma2_rn(AK2, __ffma2_rn(sc.c, hw, __fmul2_rn(nzs, hz)), DDEN);
                     }
                 } else {
                     // h = (Box[alpha C], Box[alpha S], Box[beta C], Box[beta S])
-                    NUM = __ffma2_rn(A2, __ffma2_rn(hx, sc.zc, __fmul2_rn(hy, sc.zs)), NUM);
-                    const float2 pp = __ffma2_rn(hy, sc.zc, __fmul2_rn(hx, nzs));
-                    const float2 qq = __ffma2_rn(hw, sc.zc, __fmul2_rn(hz, nzs));
+                    NUM = __ffma2_rn(A2, __ffma2_rn(hx, sc.c, __fmul2_rn(hy, sc.s)), NUM);
+                    const float2 pp = __ffma2_rn(hy, sc.c, __fmul2_rn(hx, nzs));
+                    const float2 qq = __ffma2_rn(hw, sc.c, __fmul2_rn(hz, nzs));
                     DEN = __ffma2_rn(AK2, __ffma2_rn(FC, pp, qq), DEN);
                 }
-                rot2(s0); rot2(s1); rot2(s2); rot2(s3); rot2(sc);
+                if (i + 1 < KP) {
+                    const bool need = i + 2 < KP;
+                    advance(s0, i, need); advance(s1, i, need); advance(s2, i, need);
+                    advance(s3, i, need); advance(sc, i, need);
+                }
             }
             if (gc.out) {
-                const size_t o = gc.qo + zo;   // image-sized buffers
-                const size_t os = gc.qo + zs;  // saved buffers
+                const size_t o = (size_t)gc.qo + zo;   // image-sized buffers
                 float num = NUM.x + NUM.y, den = DEN.x + DEN.y;
                 // chunked harmonics: partial sums live in the output buffers
                 // between chunks (acc: 0 single, 1 first, 2 middle, 3 last)
                 const int acc = p.acc;
+                const bool last = acc == 0 || acc == 3;
                 if constexpr (!BWD) {
                     float dn = DNUM.x + DNUM.y, dd = DDEN.x + DDEN.y;
-                    float* dbuf = SAVE ? p.sv_den + zs : p.acc_den + zo;
-                    if (acc >= 2) {
-                        num += p.out[o];
-                        den += dbuf[gc.qo];
-                        if constexpr (SAVE) { dn += p.sv_dnum[os]; dd += p.sv_dden[os]; }
+                    if constexpr (SAVE) {
+                        // between chunks the quad holds the partial (., den,
+                        // dnum, dden); the last chunk leaves (f, 1/den, out,
+                        // dnum - out dden) for the adjoint
+                        if (acc >= 2) {
+                            const float4 q = p.sv[o];
+                            num += p.out[o]; den += q.y; dn += q.z; dd += q.w;
+                        }
+                        if (last) {
+                            const float ov = num / den;
+                            p.out[o] = ov;
+                            p.sv[o] = make_float4(cc.f, 1.0f / den, ov, fmaf(-ov, dd, dn));
+                        } else {
+                            p.out[o] = num;
+                            p.sv[o] = make_float4(cc.f, den, dn, dd);
+                        }
+                    } else {
+                        if (acc >= 2) { num += p.out[o]; den += p.acc_den[o]; }
+                        p.out[o] = last ? num / den : num;
+                        if (acc != 0) p.acc_den[o] = den;
                     }
-                    p.out[o] = (acc == 0 || acc == 3) ? num / den : num;
-                    if (SAVE || acc != 0) dbuf[gc.qo] = den;
-                    if constexpr (SAVE) { p.sv_dnum[os] = dn; p.sv_dden[os] = dd; }
                 } else {
                     if (acc >= 2) { num += p.acc_gv[o]; den += p.acc_gt[o]; }
-                    if (acc == 0 || acc == 3) {
-                        const float gt = den + ac * cc.dnum + bc * cc.dden;
+                    if (last) {
+                        const float gt = den + xc;
                         if (p.gimg) p.gimg[o] = num + p.gamma * gt;
-                        gsum = fmaf(cc.f, gt, gsum);
+                        gsum = fmaf(cc.sv.x, gt, gsum);
                     } else {
                         p.acc_gv[o] = num;
                         p.acc_gt[o] = den;
@@ -429,8 +448,8 @@ __global__ void __launch_bounds__(WMAX, 256 / WMAX) bf_sys_kernel(SysParams p) {
     float gsum = 0.f;
     const size_t z = blockIdx.z;  // image of a [B, H, W] launch
     const size_t hw = (size_t)p.H * p.W;
-    sysd::sys_tile<KP, BWD, SAVE, KAHAN, Tin>(p, blockIdx.x, blockIdx.y, z * hw, z * 3 * hw, smem,
-                                              gsum);
+    sysd::sys_tile<KP, BWD, SAVE, KAHAN, WMAX, Tin>(p, blockIdx.x, blockIdx.y, z * hw, smem,
+                                                    gsum);
     if (BWD && p.partial)
         sysd::cta_sum_to(gsum, p.partial, (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x);
 }
@@ -439,7 +458,7 @@ template <int KP, bool BWD, bool SAVE, bool KAHAN, int WMAX, typename Tin>
 cudaError_t sys_launch_one(const SysParams& p, int wi, int gx, int gy, cudaStream_t s) {
     const int gz = p.B > 0 ? p.B : 1;
     auto kern = bf_sys_kernel<KP, BWD, SAVE, KAHAN, WMAX, Tin>;
-    const size_t smem = sizeof(float4) * (size_t)sysd::sys_smem_slots(KP, wi);
+    const size_t smem = sizeof(float4) * (size_t)sysd::sys_smem_slots(KP, WMAX);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
@@ -448,4 +467,3 @@ cudaError_t sys_launch_one(const SysParams& p, int wi, int gx, int gy, cudaStrea
 }
 
 }  // namespace bf
-

@@ -113,7 +113,7 @@ def test_backward_raw_abi_grad_sigma_fixed_is_zero(cuda_lib):
     H, W = 40, 50
     f = torch.from_numpy(synth.rectangles(H, W, seed=2)).cuda()
     opts = bf._opts(save=True)
-    sv = torch.empty((3, H, W), device="cuda")
+    sv = torch.empty((H, W, 4), device="cuda")
     out = bf.bf_forward(f, 3, 0.2, 1.0, 0, opts=opts, saved=sv)
     g = torch.ones_like(out)
     gs = torch.full((1,), 7.0, device="cuda")
@@ -148,7 +148,7 @@ def test_3d_launch_matches_per_image(cuda_lib, kahan_fallback):
     g = torch.from_numpy(synth.weights((B, H, W), seed=2)).cuda()
     N = oracle.resolve_N(sigma, 1.0)
     opts = bf._opts(save=not kahan_fallback, kahan=kahan_fallback, gamma_mode=bf.GAMMA_FROM_SIGMA)
-    sv = torch.empty((B, 3, H, W), device="cuda")
+    sv = torch.empty((B, H, W, 4), device="cuda")
     out3 = bf.bf_forward3d(f, r, sigma, 1.0, N, opts=opts, saved=None if kahan_fallback else sv)
     for b in range(B):
         o1 = bf.bf_forward(f[b], r, sigma, 1.0, N, opts=opts, saved=None if kahan_fallback else sv[b])

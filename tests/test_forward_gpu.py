@@ -34,14 +34,15 @@ def run_fwd(bf, img_np, r, sigma_r=0.2, T=1.0, N=0, kahan=False, dtype=torch.flo
                     tile_h=tile_h, tile_w=tile_w, save=saved)
     buf = torch.full((H * W + 2 * guard,), 12345.0, dtype=torch.float32, device=dev)
     out = buf[guard:guard + H * W].view(H, W)
-    sv = torch.empty((3, H, W), dtype=torch.float32, device=dev) if saved else None
+    sv = torch.empty((H, W, 4), dtype=torch.float32, device=dev) if saved else None
     bf.bf_forward(img, r, sigma_r, T, N, out=out, opts=opts, saved=sv)
     torch.cuda.synchronize()
     if guard:
         b = buf.cpu().numpy()
         assert np.all(b[:guard] == 12345.0) and np.all(b[guard + H * W:] == 12345.0), "guard band written"
     res = out.cpu().numpy()
-    return (res, sv.cpu().numpy()) if saved else res
+    # saved quads as planes: (f, 1/den, out, dnum_s - out dden_s)
+    return (res, np.moveaxis(sv.cpu().numpy(), 2, 0)) if saved else res
 
 
 def oracle_ref(img_np, r, sigma_r, T, N, gamma=None):
@@ -133,13 +134,16 @@ def test_bf16_input(cuda_lib):
 
 
 def test_saved_buffers(cuda_lib):
-    """den saved by the forward equals the oracle's normaliser; den >= 1."""
+    """The saved quads: f and out exactly as read and written, 1/den equal to
+    the oracle's normaliser's reciprocal; den >= 1."""
     f = synth.rectangles(90, 110, seed=13)
     got, sv = run_fwd(cuda_lib, f, 5, 0.2, 1.0, 0, saved=True)
     ref, den = oracle_ref(f, 5, 0.2, 1.0, 0)
     assert rel_err(got, ref).max() <= TOL
-    np.testing.assert_allclose(sv[0], den, rtol=2e-5, atol=0)
-    assert sv[0].min() >= 1.0 - 1e-5
+    np.testing.assert_array_equal(sv[0], f)
+    np.testing.assert_array_equal(sv[2], got)
+    np.testing.assert_allclose(1.0 / sv[1], den, rtol=2e-5, atol=0)
+    assert (1.0 / sv[1]).min() >= 1.0 - 1e-5
 
 
 def test_full_size_sampled_headline(cuda_lib):
@@ -155,7 +159,7 @@ def test_full_size_sampled_headline(cuda_lib):
                            (H - 1) * W + W // 2]])
     ref = oracle.bilateral_points(f.astype(np.float64), 10, math.pi / 2, 41, idx)
     assert rel_err(got.ravel()[idx], ref).max() <= TOL
-    assert sv[0].min() >= 1.0 - 1e-4
+    assert (1.0 / sv[1]).min() >= 1.0 - 1e-4
     assert np.isfinite(got).all()
 
 
@@ -168,7 +172,9 @@ def test_chunked_harmonics_with_saved(cuda_lib, N):
     got, sv = run_fwd(cuda_lib, f, 6, 0.2, 1.0, N, saved=True)
     ref, den = oracle_ref(f, 6, 0.2, 1.0, N)
     assert rel_err(got, ref).max() <= TOL
-    np.testing.assert_allclose(sv[0], den, rtol=2e-5, atol=0)
+    np.testing.assert_array_equal(sv[0], f)
+    np.testing.assert_array_equal(sv[2], got)
+    np.testing.assert_allclose(1.0 / sv[1], den, rtol=2e-5, atol=0)
 
 
 @pytest.mark.parametrize("r", [21, 30, 45, 56])
@@ -200,8 +206,8 @@ def test_kp_max_chunks(cuda_lib, kp_max):
     f = synth.rectangles(120, 200, seed=kp_max)
     dev = torch.device("cuda:0")
     img = torch.from_numpy(f).to(dev)
-    sv1 = torch.empty((3, 120, 200), device=dev)
-    sv2 = torch.empty((3, 120, 200), device=dev)
+    sv1 = torch.empty((120, 200, 4), device=dev)
+    sv2 = torch.empty((120, 200, 4), device=dev)
     a = bf.bf_forward(img, 8, 0.1, 1.0, 0, opts=bf._opts(save=True, kp_max=kp_max), saved=sv1)
     b = bf.bf_forward(img, 8, 0.1, 1.0, 0, opts=bf._opts(save=True), saved=sv2)
     torch.cuda.synchronize()
@@ -210,6 +216,6 @@ def test_kp_max_chunks(cuda_lib, kp_max):
     assert torch.max(torch.abs(a - b)).item() <= 1e-5
     # den and the centre derivatives: same sums in another order (the
     # derivative planes cancel heavily, so compare against each plane's scale)
-    s1, s2 = sv1.cpu().numpy(), sv2.cpu().numpy()
+    s1, s2 = np.moveaxis(sv1.cpu().numpy(), 2, 0), np.moveaxis(sv2.cpu().numpy(), 2, 0)
     scale = np.abs(s2).max(axis=(1, 2), keepdims=True)
     assert np.all(np.abs(s1 - s2) <= 1e-4 * scale)

@@ -92,7 +92,7 @@ def test_order_rule_and_gamma():
 
 
 def test_sizes():
-    assert bf.bf_saved_bytes(4, 5) == 3 * 4 * 5 * 4
+    assert bf.bf_saved_bytes(4, 5) == 4 * 4 * 5 * 4
     assert bf.bf_saved_bytes(0, 5) == 0
 
 

@@ -41,7 +41,7 @@ def test_tuned_opts_same_filter(cuda_lib, tmp_path, monkeypatch):
     H, W, r, sigma = 600, 700, 10, 0.1
     o = tune.tuned_opts(H, W, r, sigma)
     f = torch.from_numpy(synth.rectangles(H, W, seed=4)).cuda()
-    sv = torch.empty((3, H, W), device="cuda")
+    sv = torch.empty((H, W, 4), device="cuda")
     a = bf.bf_forward(f, r, sigma, 1.0, 0, opts=o, saved=sv)
     b = bf.bf_forward(f, r, sigma, 1.0, 0)
     torch.cuda.synchronize()

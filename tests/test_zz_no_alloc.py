@@ -28,7 +28,7 @@ def _case(bf, H, W, r, sigma, seed):
     g = torch.from_numpy(synth.weights((H, W), seed=seed + 1)).to(dev)
     N = bf.bf_resolve_N(sigma, 1.0)
     opts = bf._opts(save=True, gamma_mode=bf.GAMMA_FROM_SIGMA)
-    sv = torch.empty((3, H, W), device=dev)
+    sv = torch.empty((H, W, 4), device=dev)
     out = bf.bf_forward(f, r, sigma, 1.0, N, opts=opts, saved=sv)
     return f, g, out, sv, N, opts
 
