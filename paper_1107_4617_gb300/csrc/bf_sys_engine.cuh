@@ -274,11 +274,6 @@ __device__ __forceinline__ void sys_tile(const SysParams& p, int bx, int by, siz
             load_px<BWD, Tin>(v3, b, g.m3, g.q3);
             load_px<BWD, Tin>(vc, b, g.out, g.qo);
 
-            Strm s0 = seed(pix_f(c0), p.gamma, p.k0);
-            Strm s1 = seed(pix_f(c1), p.gamma, p.k0);
-            Strm s2 = seed(pix_f(c2v), p.gamma, p.k0);
-            Strm s3 = seed(pix_f(c3), p.gamma, p.k0);
-            Strm sc = seed(pix_f(cc), p.gamma, p.k0);
             // plane weights (u: first two planes, v: last two) with the stream's
             // sign: + own enter, - second enter, - own leave, + second leave;
             // 0 for a masked stream
@@ -304,55 +299,10 @@ __device__ __forceinline__ void sys_tile(const SysParams& p, int bx, int by, siz
             // this lane's slot (column j + 1)
             const float4* rd = smem + ((t + 1) & 1) * BUF + j;
             float4* wr = smem + (t & 1) * BUF + j + 1;
-
             float2 NUM = make_float2(0.f, 0.f), DEN = NUM, DNUM = NUM, DDEN = NUM;
-#pragma unroll
-            for (int i = 0; i < KP; ++i) {
-                const float4 A = rd[(2 * i) * LD];
-                const float4 B = rd[(2 * i + 1) * LD];
-                float2 dx, dy, dz, dw;
-                if constexpr (!KAHAN) {
-                    dx = Dx[i]; dy = Dy[i]; dz = Dz[i]; dw = Dw[i];
-                    dx = __ffma2_rn(s0.c, U0, dx); dx = __ffma2_rn(s1.c, U1, dx);
-                    dx = __ffma2_rn(s2.c, U2, dx); dx = __ffma2_rn(s3.c, U3, dx);
-                    dy = __ffma2_rn(s0.s, U0, dy); dy = __ffma2_rn(s1.s, U1, dy);
-                    dy = __ffma2_rn(s2.s, U2, dy); dy = __ffma2_rn(s3.s, U3, dy);
-                    dz = __ffma2_rn(s0.c, V0, dz); dz = __ffma2_rn(s1.c, V1, dz);
-                    dz = __ffma2_rn(s2.c, V2, dz); dz = __ffma2_rn(s3.c, V3, dz);
-                    dw = __ffma2_rn(s0.s, V0, dw); dw = __ffma2_rn(s1.s, V1, dw);
-                    dw = __ffma2_rn(s2.s, V2, dw); dw = __ffma2_rn(s3.s, V3, dw);
-                } else {
-                    // this row's increment of each running sum, then a
-                    // Kahan-compensated add (Kahan 1965): y = inc - e,
-                    // t = D + y, e = (t - D) - y, D = t
-                    const float2 m1 = dup(-1.f);
-                    float2 ix = __fmul2_rn(s0.c, U0), iy = __fmul2_rn(s0.s, U0);
-                    float2 iz = __fmul2_rn(s0.c, V0), iw = __fmul2_rn(s0.s, V0);
-                    ix = __ffma2_rn(s1.c, U1, ix); ix = __ffma2_rn(s2.c, U2, ix);
-                    ix = __ffma2_rn(s3.c, U3, ix);
-                    iy = __ffma2_rn(s1.s, U1, iy); iy = __ffma2_rn(s2.s, U2, iy);
-                    iy = __ffma2_rn(s3.s, U3, iy);
-                    iz = __ffma2_rn(s1.c, V1, iz); iz = __ffma2_rn(s2.c, V2, iz);
-                    iz = __ffma2_rn(s3.c, V3, iz);
-                    iw = __ffma2_rn(s1.s, V1, iw); iw = __ffma2_rn(s2.s, V2, iw);
-                    iw = __ffma2_rn(s3.s, V3, iw);
-                    auto kadd = [&](float2& D, float2& E, float2 inc) {
-                        const float2 y = __ffma2_rn(E, m1, inc);
-                        const float2 t2 = __fadd2_rn(D, y);
-                        E = __ffma2_rn(y, m1, __ffma2_rn(D, m1, t2));
-                        D = t2;
-                    };
-                    kadd(Dx[i], Ex[i], ix); kadd(Dy[i], Ey[i], iy);
-                    kadd(Dz[i], Ez[i], iz); kadd(Dw[i], Ew[i], iw);
-                    dx = Dx[i]; dy = Dy[i]; dz = Dz[i]; dw = Dw[i];
-                }
-                Dx[i] = dx; Dy[i] = dy; Dz[i] = dz; Dw[i] = dw;
-                const float2 hx = __fadd2_rn(make_float2(A.x, A.y), dx);
-                const float2 hy = __fadd2_rn(make_float2(A.z, A.w), dy);
-                const float2 hz = __fadd2_rn(make_float2(B.x, B.y), dz);
-                const float2 hw = __fadd2_rn(make_float2(B.z, B.w), dw);
-                wr[(2 * i) * LD] = make_float4(hx.x, hx.y, hy.x, hy.y);
-                wr[(2 * i + 1) * LD] = make_float4(hz.x, hz.y, hw.x, hw.y);
+            // the centre pixel's recombination of pair i with its box sums h
+            auto combine = [&](const Strm& sc, int i, float2 hx, float2 hy, float2 hz,
+                               float2 hw) {
                 const float2 A2 = make_float2(p.a[2 * i], p.a[2 * i + 1]);
                 const float2 AK2 = make_float2(p.ak[2 * i], p.ak[2 * i + 1]);
                 const float2 nzs = __fmul2_rn(sc.s, dup(-1.f));
@@ -370,10 +320,102 @@ __device__ __forceinline__ void sys_tile(const SysParams& p, int bx, int by, siz
                     const float2 qq = __ffma2_rn(hw, sc.c, __fmul2_rn(hz, nzs));
                     DEN = __ffma2_rn(AK2, __ffma2_rn(FC, pp, qq), DEN);
                 }
-                if (i + 1 < KP) {
-                    const bool need = i + 2 < KP;
-                    advance(s0, i, need); advance(s1, i, need); advance(s2, i, need);
-                    advance(s3, i, need); advance(sc, i, need);
+            };
+            if constexpr (!BWD && !KAHAN) {
+                // forward: the vertical running sums one stream at a time (only
+                // that stream's recurrence is live, and its harmonic pairs update
+                // independent sums), then the horizontal step and the centre
+                auto accumulate = [&](float f, float2 U, float2 V) {
+                    Strm q = seed(f, p.gamma, p.k0);
+#pragma unroll
+                    for (int i = 0; i < KP; ++i) {
+                        Dx[i] = __ffma2_rn(q.c, U, Dx[i]);
+                        Dy[i] = __ffma2_rn(q.s, U, Dy[i]);
+                        Dz[i] = __ffma2_rn(q.c, V, Dz[i]);
+                        Dw[i] = __ffma2_rn(q.s, V, Dw[i]);
+                        if (i + 1 < KP) advance(q, i, i + 2 < KP);
+                    }
+                };
+                accumulate(c0.f, U0, V0);
+                accumulate(c1.f, U1, V1);
+                accumulate(c2v.f, U2, V2);
+                accumulate(c3.f, U3, V3);
+                Strm sc = seed(cc.f, p.gamma, p.k0);
+#pragma unroll
+                for (int i = 0; i < KP; ++i) {
+                    const float4 A = rd[(2 * i) * LD];
+                    const float4 B = rd[(2 * i + 1) * LD];
+                    const float2 hx = __fadd2_rn(make_float2(A.x, A.y), Dx[i]);
+                    const float2 hy = __fadd2_rn(make_float2(A.z, A.w), Dy[i]);
+                    const float2 hz = __fadd2_rn(make_float2(B.x, B.y), Dz[i]);
+                    const float2 hw = __fadd2_rn(make_float2(B.z, B.w), Dw[i]);
+                    wr[(2 * i) * LD] = make_float4(hx.x, hx.y, hy.x, hy.y);
+                    wr[(2 * i + 1) * LD] = make_float4(hz.x, hz.y, hw.x, hw.y);
+                    combine(sc, i, hx, hy, hz, hw);
+                    if (i + 1 < KP) advance(sc, i, i + 2 < KP);
+                }
+            } else {
+                // adjoint and Kahan: all five streams advance together, pair by
+                // pair (Kahan compensates one add per row and sum, so the four
+                // streams' increments are formed together)
+                Strm s0 = seed(pix_f(c0), p.gamma, p.k0);
+                Strm s1 = seed(pix_f(c1), p.gamma, p.k0);
+                Strm s2 = seed(pix_f(c2v), p.gamma, p.k0);
+                Strm s3 = seed(pix_f(c3), p.gamma, p.k0);
+                Strm sc = seed(pix_f(cc), p.gamma, p.k0);
+#pragma unroll
+                for (int i = 0; i < KP; ++i) {
+                    const float4 A = rd[(2 * i) * LD];
+                    const float4 B = rd[(2 * i + 1) * LD];
+                    float2 dx, dy, dz, dw;
+                    if constexpr (!KAHAN) {
+                        dx = Dx[i]; dy = Dy[i]; dz = Dz[i]; dw = Dw[i];
+                        dx = __ffma2_rn(s0.c, U0, dx); dx = __ffma2_rn(s1.c, U1, dx);
+                        dx = __ffma2_rn(s2.c, U2, dx); dx = __ffma2_rn(s3.c, U3, dx);
+                        dy = __ffma2_rn(s0.s, U0, dy); dy = __ffma2_rn(s1.s, U1, dy);
+                        dy = __ffma2_rn(s2.s, U2, dy); dy = __ffma2_rn(s3.s, U3, dy);
+                        dz = __ffma2_rn(s0.c, V0, dz); dz = __ffma2_rn(s1.c, V1, dz);
+                        dz = __ffma2_rn(s2.c, V2, dz); dz = __ffma2_rn(s3.c, V3, dz);
+                        dw = __ffma2_rn(s0.s, V0, dw); dw = __ffma2_rn(s1.s, V1, dw);
+                        dw = __ffma2_rn(s2.s, V2, dw); dw = __ffma2_rn(s3.s, V3, dw);
+                    } else {
+                        // this row's increment of each running sum, then a
+                        // Kahan-compensated add (Kahan 1965): y = inc - e,
+                        // t = D + y, e = (t - D) - y, D = t
+                        const float2 m1 = dup(-1.f);
+                        float2 ix = __fmul2_rn(s0.c, U0), iy = __fmul2_rn(s0.s, U0);
+                        float2 iz = __fmul2_rn(s0.c, V0), iw = __fmul2_rn(s0.s, V0);
+                        ix = __ffma2_rn(s1.c, U1, ix); ix = __ffma2_rn(s2.c, U2, ix);
+                        ix = __ffma2_rn(s3.c, U3, ix);
+                        iy = __ffma2_rn(s1.s, U1, iy); iy = __ffma2_rn(s2.s, U2, iy);
+                        iy = __ffma2_rn(s3.s, U3, iy);
+                        iz = __ffma2_rn(s1.c, V1, iz); iz = __ffma2_rn(s2.c, V2, iz);
+                        iz = __ffma2_rn(s3.c, V3, iz);
+                        iw = __ffma2_rn(s1.s, V1, iw); iw = __ffma2_rn(s2.s, V2, iw);
+                        iw = __ffma2_rn(s3.s, V3, iw);
+                        auto kadd = [&](float2& D, float2& E, float2 inc) {
+                            const float2 y = __ffma2_rn(E, m1, inc);
+                            const float2 t2 = __fadd2_rn(D, y);
+                            E = __ffma2_rn(y, m1, __ffma2_rn(D, m1, t2));
+                            D = t2;
+                        };
+                        kadd(Dx[i], Ex[i], ix); kadd(Dy[i], Ey[i], iy);
+                        kadd(Dz[i], Ez[i], iz); kadd(Dw[i], Ew[i], iw);
+                        dx = Dx[i]; dy = Dy[i]; dz = Dz[i]; dw = Dw[i];
+                    }
+                    Dx[i] = dx; Dy[i] = dy; Dz[i] = dz; Dw[i] = dw;
+                    const float2 hx = __fadd2_rn(make_float2(A.x, A.y), dx);
+                    const float2 hy = __fadd2_rn(make_float2(A.z, A.w), dy);
+                    const float2 hz = __fadd2_rn(make_float2(B.x, B.y), dz);
+                    const float2 hw = __fadd2_rn(make_float2(B.z, B.w), dw);
+                    wr[(2 * i) * LD] = make_float4(hx.x, hx.y, hy.x, hy.y);
+                    wr[(2 * i + 1) * LD] = make_float4(hz.x, hz.y, hw.x, hw.y);
+                    combine(sc, i, hx, hy, hz, hw);
+                    if (i + 1 < KP) {
+                        const bool need = i + 2 < KP;
+                        advance(s0, i, need); advance(s1, i, need); advance(s2, i, need);
+                        advance(s3, i, need); advance(sc, i, need);
+                    }
                 }
             }
             if (gc.out) {
