@@ -83,6 +83,15 @@ typedef struct {
                              mean fewer registers per thread; the harmonics then run
                              in chunks, which accumulate in `saved` (forward) or the
                              workspace (adjoint) */
+    float trunc_tol;      /* 0: the exact q_N. > 0 (and < 1): keep only the lowest
+                             harmonics of q_N's expansion, dropping the highest ones
+                             while their a_k sum to at most min(trunc_tol,
+                             1/(2 (2r+1)^2)) (end of Sec. 3: discard the less
+                             significant basis functions). The range kernel then
+                             differs from cos^N(gamma t) by at most that sum
+                             anywhere on [-T, T], may dip below 0 by as much, and
+                             den >= 1/2 still holds. Forward and backward calls
+                             must pass the same value. See bf_trunc_harmonics. */
 } bf_opts;
 
 /* One image of a batch (bf_batch). img/out/den are device pointers. */
@@ -110,6 +119,11 @@ int bf_resolve_N(float sigma_r, float T);
    a[0 .. K-1] (K = N/2 + 1, in that order) in FP64 and returns K; returns -1
    if N < 0, N > BF_N_MAX or cap < K. Host only, no GPU needed. */
 int bf_coeffs(int N, double* a, int cap);
+
+/* Number of harmonics kept for order N, half-width r and opts->trunc_tol
+   (the rule described at bf_opts.trunc_tol; N/2 + 1 when trunc_tol = 0).
+   Returns -1 on bad arguments. Host only. */
+int bf_trunc_harmonics(int N, int r, float trunc_tol);
 
 /* gamma used for (sigma_r, T, N, gamma_mode); N must already be resolved.
    Returns a negative value on bad arguments. Host only. */

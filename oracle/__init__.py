@@ -68,6 +68,17 @@ def _load():
             lib.oracle_bf_grad.restype = ctypes.c_int
             lib.oracle_bf_grad.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                            ctypes.c_double, ctypes.c_int, _dp, _dp]
+            lib.oracle_bf_general_rows.restype = ctypes.c_int
+            lib.oracle_bf_general_rows.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                   ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                   ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                                   ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                                   _dp, _dp]
+            lib.oracle_trunc_weight.restype = ctypes.c_double
+            lib.oracle_trunc_weight.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                                ctypes.c_int]
+            lib.oracle_spatial_weight.restype = ctypes.c_double
+            lib.oracle_spatial_weight.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
             lib.oracle_num_threads.restype = ctypes.c_int
             lib.oracle_num_threads.argtypes = []
             _lib = lib
@@ -173,3 +184,42 @@ def bilateral_grad(f, g, r: int, gamma: float, N: int):
     if rc != 0:
         raise ValueError(f"oracle_bf_grad failed ({rc})")
     return gf, float(gg.value)
+
+
+# ---- generalised filters (Algorithm 1, Algorithm 2 with a shiftable spatial
+# kernel, truncated expansion, polynomial range kernel) ---------------------
+
+SPATIAL_BOX, SPATIAL_QM = 0, 1
+RANGE_NONE, RANGE_COSN, RANGE_TRUNC, RANGE_POLY = 0, 1, 2, 3
+
+
+def trunc_weight(t: float, gamma: float, N: int, K_keep: int) -> float:
+    """q_N's shift expansion cut to its K_keep lowest harmonics, evaluated
+    term by term (end of Sec. 3: discarding the less significant basis
+    functions)."""
+    return float(_load().oracle_trunc_weight(float(t), float(gamma), int(N), int(K_keep)))
+
+
+def spatial_weight(d: int, r: int, M: int) -> float:
+    """1-D factor of the separable spatial kernel q_M(d) = cos^M(pi d / (2 Ts)),
+    Ts = r + 1/2 (Sec. 3, separable kernels)."""
+    return float(_load().oracle_spatial_weight(int(d), int(r), int(M)))
+
+
+def bilateral_general(f, r: int, spatial: int = SPATIAL_BOX, M: int = 0,
+                      range_kind: int = RANGE_COSN, gamma: float = math.pi / 2, N: int = 0,
+                      K_keep: int = 0, Tr: float = 1.0, rows=None, return_den=False):
+    """Direct O(r^2) neighbourhood filter with spatial kernel box or
+    q_M(d1) q_M(d2) and range kernel none (Algorithm 1), q_N, truncated q_N or
+    p_N (Algorithm 2); truncated window at the border."""
+    f = _as_f64(f)
+    H, W = f.shape
+    r0, r1 = (0, H) if rows is None else (max(0, rows[0]), min(H, rows[1]))
+    out = np.empty((r1 - r0, W), np.float64)
+    den = np.empty((r1 - r0, W), np.float64)
+    rc = _load().oracle_bf_general_rows(_ptr(f), H, W, int(r), int(spatial), int(M),
+                                        int(range_kind), float(gamma), int(N), int(K_keep),
+                                        float(Tr), r0, r1, _ptr(out), _ptr(den))
+    if rc != 0:
+        raise ValueError(f"oracle_bf_general_rows failed ({rc})")
+    return (out, den) if return_den else out

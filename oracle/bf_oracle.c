@@ -214,3 +214,93 @@ int oracle_bf_grad(const double* f, const double* g, int H, int W, int r,
     free(out); free(den); free(self);
     return 0;
 }
+
+/*
+ * Generalised neighbourhood filter by its definition, for the variants of
+ * Algorithms 1-2 beyond the box / q_N pair (Sec. 2, Sec. 3):
+ *
+ *   out(x) = sum_{y in W(x)} phi(y - x) w(f(y) - f(x)) f(y)
+ *            / sum_{y in W(x)} phi(y - x) w(f(y) - f(x))
+ *
+ * over the same truncated (2r+1)^2 window.
+ *
+ * Spatial kernel phi (spatial = 0: box, phi = 1; spatial = 1: the separable
+ * kernel q_M(d1) q_M(d2) of Sec. 3 with q_M(d) = cos^M(pi d / (2 Ts)) on
+ * [-Ts, Ts], Ts = r + 1/2, so that the window |d| <= r lies inside the
+ * kernel's support).
+ *
+ * Range kernel w (range = 0: none, w = 1, i.e. Algorithm 1's linear
+ * filter; 1: q_N, cos^N(gamma t); 2: q_N with its shift expansion cut to the
+ * K_keep lowest harmonics, sum_{i < K_keep} a_i cos(k_i gamma t), k_i =
+ * N mod 2 + 2i, a_i = 2^(1-N) C(N, (N-k_i)/2) (halved for k = 0) -- the
+ * "discard the less significant basis functions" of the end of Sec. 3;
+ * 3: p_N(t) = (1 - t^2/T^2)^N with T = Tr).
+ * Rows [row0, row1) are written; den may be NULL.
+ */
+static double binom(int n, int k) {
+    double c = 1.0;
+    if (k < 0 || k > n) return 0.0;
+    if (k > n - k) k = n - k;
+    for (int i = 1; i <= k; ++i) c = c * (double)(n - k + i) / (double)i;
+    return c;
+}
+
+double oracle_trunc_weight(double t, double gamma, int N, int K_keep) {
+    double w = 0.0;
+    for (int i = 0; i < K_keep && 2 * i + (N & 1) <= N; ++i) {
+        const int k = (N & 1) + 2 * i;
+        double a = ldexp(binom(N, (N - k) / 2), 1 - N);
+        if (k == 0) a *= 0.5;
+        w += a * cos((double)k * gamma * t);
+    }
+    return w;
+}
+
+static double range_weight(int range, double t, double gamma, int N, int K_keep, double Tr) {
+    switch (range) {
+        case 0: return 1.0;
+        case 1: return oracle_weight(t, gamma, N);
+        case 2: return oracle_trunc_weight(t, gamma, N, K_keep);
+        default: {
+            const double u = 1.0 - (t * t) / (Tr * Tr);
+            return pow_int(u, N);
+        }
+    }
+}
+
+double oracle_spatial_weight(int d, int r, int M) {
+    return pow_int(cos(acos(-1.0) * (double)d / (2.0 * ((double)r + 0.5))), M);
+}
+
+int oracle_bf_general_rows(const double* f, int H, int W, int r, int spatial, int M, int range,
+                           double gamma, int N, int K_keep, double Tr, int row0, int row1,
+                           double* out, double* den) {
+    if (!f || !out || H <= 0 || W <= 0 || r < 0 || N < 0 || M < 0) return -1;
+    if (range < 0 || range > 3 || spatial < 0 || spatial > 1) return -1;
+    if (range == 3 && !(Tr > 0)) return -1;
+    if (row0 < 0) row0 = 0;
+    if (row1 > H) row1 = H;
+    double* sw = (double*)malloc((size_t)(2 * r + 1) * sizeof(double));
+    if (!sw) return -2;
+    for (int d = -r; d <= r; ++d) sw[d + r] = spatial ? oracle_spatial_weight(d, r, M) : 1.0;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int y = row0; y < row1; ++y) {
+        for (int x = 0; x < W; ++x) {
+            const double fx = f[(size_t)y * W + x];
+            double num = 0.0, eta = 0.0;
+            for (int yy = imax(0, y - r); yy <= imin(H - 1, y + r); ++yy) {
+                for (int xx = imax(0, x - r); xx <= imin(W - 1, x + r); ++xx) {
+                    const double fy = f[(size_t)yy * W + xx];
+                    const double w = sw[yy - y + r] * sw[xx - x + r] *
+                                     range_weight(range, fy - fx, gamma, N, K_keep, Tr);
+                    num += w * fy;
+                    eta += w;
+                }
+            }
+            out[(size_t)(y - row0) * W + x] = num / eta;
+            if (den) den[(size_t)(y - row0) * W + x] = eta;
+        }
+    }
+    free(sw);
+    return 0;
+}

@@ -21,7 +21,7 @@ __all__ = [
     "BfError", "BfOpts", "BfDesc", "load", "lib_path",
     "bf_forward", "bf_backward", "bf_forward3d", "bf_backward3d", "bf_batch", "bf_batch_prepare",
     "bf_batch_launch", "bf_backward3d_workspace_bytes",
-    "bf_resolve_N", "bf_coeffs", "bf_gamma", "bf_saved_bytes", "bf_backward_workspace_bytes",
+    "bf_resolve_N", "bf_coeffs", "bf_trunc_harmonics", "bf_gamma", "bf_saved_bytes", "bf_backward_workspace_bytes",
     "bf_batch_workspace_bytes", "bf_status_string", "bf_last_cuda_error", "bilateral",
     "GAMMA_FIXED", "GAMMA_FROM_SIGMA", "F32", "BF16", "N_MAX", "R_MAX",
 ]
@@ -49,7 +49,8 @@ class BfError(RuntimeError):
 class BfOpts(ctypes.Structure):
     _fields_ = [("kahan", ctypes.c_int), ("gamma_mode", ctypes.c_int),
                 ("in_dtype", ctypes.c_int), ("save_for_backward", ctypes.c_int),
-                ("tile_h", ctypes.c_int), ("tile_w", ctypes.c_int), ("kp_max", ctypes.c_int)]
+                ("tile_h", ctypes.c_int), ("tile_w", ctypes.c_int), ("kp_max", ctypes.c_int),
+                ("trunc_tol", ctypes.c_float)]
 
 
 class BfDesc(ctypes.Structure):
@@ -84,6 +85,7 @@ def load():
             "bf_default_opts": (None, [P_opts]),
             "bf_resolve_N": (c_int, [c_float, c_float]),
             "bf_coeffs": (c_int, [c_int, ctypes.POINTER(ctypes.c_double), c_int]),
+            "bf_trunc_harmonics": (c_int, [c_int, c_int, c_float]),
             "bf_gamma": (ctypes.c_double, [c_float, c_float, c_int, c_int]),
             "bf_saved_bytes": (c_size, [c_int, c_int]),
             "bf_forward": (c_int, [vp, c_int, c_int, c_int, c_float, c_float, c_int, vp, P_opts,
@@ -136,11 +138,12 @@ def _check(fn: str, status: int):
 
 
 def _opts(kahan=False, gamma_mode=GAMMA_FIXED, in_dtype=F32, save=False, tile_h=0, tile_w=0,
-          kp_max=0):
+          kp_max=0, trunc_tol=0.0):
     o = BfOpts()
     o.kahan, o.gamma_mode, o.in_dtype = int(bool(kahan)), int(gamma_mode), int(in_dtype)
     o.save_for_backward, o.tile_h, o.tile_w = int(bool(save)), int(tile_h), int(tile_w)
     o.kp_max = int(kp_max)
+    o.trunc_tol = float(trunc_tol)
     return o
 
 
@@ -182,6 +185,11 @@ def bf_coeffs(N: int):
     if K < 0:
         raise ValueError(f"bf_coeffs: invalid N={N}")
     return [buf[i] for i in range(K)]
+
+
+def bf_trunc_harmonics(N: int, r: int, trunc_tol: float) -> int:
+    """Harmonics of q_N's expansion kept under trunc_tol (see bf_opts)."""
+    return int(load().bf_trunc_harmonics(int(N), int(r), float(trunc_tol)))
 
 
 def bf_gamma(sigma_r: float, T: float, N: int, gamma_mode: int = GAMMA_FIXED) -> float:
@@ -336,7 +344,7 @@ def _make_function():
         derivative term); the adjoint kernel recomputes the stack from them."""
 
         @staticmethod
-        def forward(ctx, f, sigma_r, r, T, N, kahan, gamma_mode):
+        def forward(ctx, f, sigma_r, r, T, N, kahan, gamma_mode, trunc_tol):
             s = float(sigma_r)
             if N <= 0:
                 N = bf_resolve_N(s, T)
@@ -344,22 +352,24 @@ def _make_function():
             fb = f.unsqueeze(0) if squeeze else f
             fb = fb.contiguous()
             B, H, W = fb.shape
-            opts = _opts(kahan=kahan, gamma_mode=gamma_mode, in_dtype=_in_dtype(fb), save=True)
+            opts = _opts(kahan=kahan, gamma_mode=gamma_mode, in_dtype=_in_dtype(fb), save=True,
+                         trunc_tol=trunc_tol)
             out = torch.empty((B, H, W), dtype=torch.float32, device=f.device)
             saved = torch.empty((B, H, W, 4), dtype=torch.float32, device=f.device)
             bf_forward3d(fb, r, s, T, N, out=out, opts=opts, saved=saved)
             ctx.save_for_backward(fb, out, saved)
-            ctx.cfg = (r, s, T, N, kahan, gamma_mode, squeeze)
+            ctx.cfg = (r, s, T, N, kahan, gamma_mode, trunc_tol, squeeze)
             return out[0] if squeeze else out
 
         @staticmethod
         def backward(ctx, g):
             fb, out, saved = ctx.saved_tensors
-            r, s, T, N, kahan, gamma_mode, squeeze = ctx.cfg
+            r, s, T, N, kahan, gamma_mode, trunc_tol, squeeze = ctx.cfg
             g = g.unsqueeze(0) if squeeze else g
             g = g.contiguous().float()
             B, H, W = fb.shape
-            opts = _opts(kahan=kahan, gamma_mode=gamma_mode, in_dtype=_in_dtype(fb))
+            opts = _opts(kahan=kahan, gamma_mode=gamma_mode, in_dtype=_in_dtype(fb),
+                         trunc_tol=trunc_tol)
             need_f = ctx.needs_input_grad[0]
             need_s = ctx.needs_input_grad[1]
             gf = torch.empty((B, H, W), dtype=torch.float32, device=fb.device) if need_f else None
@@ -374,7 +384,7 @@ def _make_function():
                 gf = gf[0] if squeeze else gf
                 gf = gf.to(fb.dtype)
             gsig = gs[0] if gs is not None else None
-            return gf, gsig, None, None, None, None, None
+            return gf, gsig, None, None, None, None, None, None
 
     return BilateralCosN
 
@@ -383,17 +393,19 @@ _fn = None
 
 
 def bilateral(f, r: int, sigma_r, T: float = 1.0, N: int = 0, kahan: bool = False,
-              gamma_mode: int = GAMMA_FIXED):
+              gamma_mode: int = GAMMA_FIXED, trunc_tol: float = 0.0):
     """Raised-cosine bilateral filter of f ([H, W] or [B, H, W], CUDA, float32
     or bfloat16) with a (2r+1)^2 box window. sigma_r may be a float or a 0-d
-    tensor (to get dL/dsigma_r); N <= 0 derives N from sigma_r."""
+    tensor (to get dL/dsigma_r); N <= 0 derives N from sigma_r. trunc_tol > 0
+    keeps only the lowest harmonics of q_N's expansion (see bf_opts)."""
     import torch
     global _fn
     if _fn is None:
         _fn = _make_function()
     if not isinstance(sigma_r, torch.Tensor):
         sigma_r = torch.tensor(float(sigma_r), dtype=torch.float32)
-    return _fn.apply(f, sigma_r, int(r), float(T), int(N), bool(kahan), int(gamma_mode))
+    return _fn.apply(f, sigma_r, int(r), float(T), int(N), bool(kahan), int(gamma_mode),
+                     float(trunc_tol))
 
 
 def bf_backward_noalloc(img, out, grad_out, saved, r: int, sigma_r: float, T: float = 1.0,

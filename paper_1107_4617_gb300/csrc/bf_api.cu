@@ -38,7 +38,24 @@ static int coeffs(int N, double* a, int cap) {
     return K;
 }
 
-bf_status resolve(int r, float sigma_r, float T, int N, int gamma_mode, Resolved* out) {
+// Number of harmonics of q_N's expansion kept under a kernel tolerance
+// (the end of Sec. 3: discard the less significant basis functions). The
+// highest harmonics have the smallest a_k; dropping a set of them changes the
+// kernel by at most the sum of their a_k (|cos| <= 1), attained at t = 0. The
+// dropped sum is kept <= min(tol, 1 / (2 (2r+1)^2)), so the truncated kernel
+// is above -1/(2 (2r+1)^2) everywhere and den >= 1 - 1/2 stays positive.
+static int trunc_keep(const double* a, int K, int r, double tol) {
+    if (!(tol > 0.0)) return K;
+    const double n = (double)(2 * r + 1) * (double)(2 * r + 1);
+    const double cap = tol < 0.5 / n ? tol : 0.5 / n;
+    double tail = 0.0;
+    int keep = K;
+    while (keep > 1 && tail + a[keep - 1] <= cap) tail += a[--keep];
+    return keep;
+}
+
+bf_status resolve(int r, float sigma_r, float T, int N, int gamma_mode, float trunc_tol,
+                  Resolved* out) {
     if (!(T > 0.f) || !isfinite(T)) return BF_ERR_INVALID_ARG;
     if (r < 0) return BF_ERR_INVALID_ARG;
     if (r > BF_R_MAX) return BF_ERR_UNSUPPORTED;
@@ -57,6 +74,7 @@ bf_status resolve(int r, float sigma_r, float T, int N, int gamma_mode, Resolved
     out->kstart = N & 1;
     out->K = coeffs(N, out->a, KCAP);
     if (out->K < 0) return BF_ERR_INTERNAL;
+    out->K = trunc_keep(out->a, out->K, r, (double)trunc_tol);
     const double g = bf_gamma(sigma_r, T, N, gamma_mode);
     if (!(g > 0.0)) return BF_ERR_INVALID_ARG;
     out->gamma = g;
@@ -149,6 +167,7 @@ bf_status check_opts(const bf_opts* o) {
         return BF_ERR_INVALID_ARG;
     if (o->tile_h < 0 || o->tile_w < 0) return BF_ERR_INVALID_ARG;
     if (o->kp_max < 0 || o->kp_max > SYS_KP_MAX) return BF_ERR_INVALID_ARG;
+    if (!(o->trunc_tol >= 0.f && o->trunc_tol < 1.f)) return BF_ERR_INVALID_ARG;
     return BF_OK;
 }
 
@@ -161,7 +180,7 @@ bf_status fill_fwd_params(const void* img, float* out, void* saved, int H, int W
     if (st != BF_OK) return st;
     const int gm = opts ? opts->gamma_mode : BF_GAMMA_FIXED;
     Resolved rs;
-    st = resolve(r, sigma_r, T, N, gm, &rs);
+    st = resolve(r, sigma_r, T, N, gm, opts ? opts->trunc_tol : 0.f, &rs);
     if (st != BF_OK) return st;
     Tiles t;
     st = choose_tiles(H, W, r, opts, &t);
@@ -204,6 +223,15 @@ int bf_resolve_N(float sigma_r, float T) {
 }
 
 int bf_coeffs(int N, double* a, int cap) { return coeffs(N, a, cap); }
+
+int bf_trunc_harmonics(int N, int r, float trunc_tol) {
+    if (N < 0 || N > BF_N_MAX || r < 0 || r > BF_R_MAX) return -1;
+    if (!(trunc_tol >= 0.f && trunc_tol < 1.f)) return -1;
+    double a[KCAP];
+    const int K = coeffs(N, a, KCAP);
+    if (K < 0) return -1;
+    return trunc_keep(a, K, r, (double)trunc_tol);
+}
 
 double bf_gamma(float sigma_r, float T, int N, int gamma_mode) {
     if (!(T > 0.f)) return -1.0;
@@ -286,7 +314,7 @@ static size_t backward_ws_impl(int B, int H, int W, int r, float sigma_r, float 
     if (B < 1 || H < 1 || W < 1 || check_opts(opts) != BF_OK) return 0;
     const int gm = opts ? opts->gamma_mode : BF_GAMMA_FIXED;
     Resolved rs;
-    if (resolve(r, sigma_r, T, N, gm, &rs) != BF_OK) return 0;
+    if (resolve(r, sigma_r, T, N, gm, opts ? opts->trunc_tol : 0.f, &rs) != BF_OK) return 0;
     BwdWs ws;
     Tiles t;
     bool use_sys = false;
@@ -305,7 +333,7 @@ static bf_status backward_impl(const void* img, const float* out, const float* g
     if (st != BF_OK) return st;
     const int gm = opts ? opts->gamma_mode : BF_GAMMA_FIXED;
     Resolved rs;
-    st = resolve(r, sigma_r, T, N, gm, &rs);
+    st = resolve(r, sigma_r, T, N, gm, opts ? opts->trunc_tol : 0.f, &rs);
     if (st != BF_OK) return st;
     Tiles t;
     BwdWs ws;

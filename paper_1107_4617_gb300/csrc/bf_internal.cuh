@@ -144,7 +144,8 @@ struct Resolved {
     double a[KCAP];
 };
 
-bf_status resolve(int r, float sigma_r, float T, int N, int gamma_mode, Resolved* out);
+bf_status resolve(int r, float sigma_r, float T, int N, int gamma_mode, float trunc_tol,
+                  Resolved* out);
 bf_status set_cuda_error(cudaError_t e);
 
 // Launchers (defined in the kernel translation units).

@@ -127,8 +127,58 @@ def test_argument_checks_return_before_any_launch():
                            ctypes.byref(o), None) == 6
     # batch: empty list
     assert lib.bf_batch(None, 0, None, p, 64, None) == 1
+    # truncation tolerance outside [0, 1)
+    for bad in (-1e-3, 1.0, float("nan")):
+        lib.bf_default_opts(ctypes.byref(o))
+        o.trunc_tol = bad
+        assert lib.bf_forward(p, 4, 4, 1, 0.2, 1.0, 0, q, ctypes.byref(o), None, None) == 1
 
 
 def test_status_strings():
     for s in range(7):
         assert isinstance(bf.bf_status_string(s), str) and bf.bf_status_string(s)
+
+
+def truncation_rule(N, r, tol):
+    """Independent restatement of the truncated-basis rule: drop the highest
+    harmonics of cos^N's expansion (smallest a_k, end of Sec. 3) while their
+    coefficients sum to at most min(tol, 1/(2 (2r+1)^2))."""
+    ks = list(range(N % 2, N + 1, 2))
+    a = [math.comb(N, (N - k) // 2) / 2.0 ** (N - 1) for k in ks]
+    if N % 2 == 0:
+        a[0] /= 2
+    if tol <= 0:
+        return len(a)
+    cap = min(tol, 0.5 / (2 * r + 1) ** 2)
+    keep, tail = len(a), 0.0
+    while keep > 1 and tail + a[keep - 1] <= cap:
+        keep -= 1
+        tail += a[keep]
+    return keep
+
+
+@pytest.mark.parametrize("N", [1, 2, 5, 11, 19, 40, 41, 64])
+@pytest.mark.parametrize("r", [1, 10, 30])
+@pytest.mark.parametrize("tol", [0.0, 1e-6, 1e-4, 1e-3, 1e-2, 0.5])
+def test_truncated_basis_rule(N, r, tol):
+    K = bf.bf_trunc_harmonics(N, r, tol)
+    assert K == truncation_rule(N, r, tol)
+    assert 1 <= K <= N // 2 + 1
+    # the kept expansion differs from cos^N by at most the dropped coefficients,
+    # and by exactly that at t = 0
+    a = bf.bf_coeffs(N)
+    dropped = sum(a[K:])
+    assert dropped <= min(tol, 0.5 / (2 * r + 1) ** 2) + 1e-15 if tol > 0 else dropped == 0
+    th = np.linspace(0, math.pi / 2, 2001)
+    ks = (N % 2) + 2 * np.arange(K)
+    w = sum(ai * np.cos(k * th) for ai, k in zip(a[:K], ks))
+    assert np.max(np.abs(w - np.cos(th) ** N)) <= dropped + 1e-14
+    assert abs((1.0 - w[0]) - dropped) <= 1e-14
+
+
+def test_truncated_basis_rule_rejects_bad_arguments():
+    assert bf.bf_trunc_harmonics(-1, 3, 0.0) == -1
+    assert bf.bf_trunc_harmonics(65, 3, 0.0) == -1
+    assert bf.bf_trunc_harmonics(11, -1, 0.0) == -1
+    assert bf.bf_trunc_harmonics(11, 3, 1.0) == -1
+    assert bf.bf_trunc_harmonics(11, 3, -0.5) == -1

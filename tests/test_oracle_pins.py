@@ -201,3 +201,72 @@ def test_points_match_full():
     np.testing.assert_array_equal(oracle.bilateral_points(f, 4, GAMMA1, 11, idx), full.ravel()[idx])
     part = oracle.bilateral(f, 4, GAMMA1, 11, rows=(10, 17))
     np.testing.assert_array_equal(part, full[10:17])
+
+
+# ---- truncated expansion (end of Sec. 3) ------------------------------------
+
+def binom_coeffs(N):
+    ks = list(range(N % 2, N + 1, 2))
+    a = [math.comb(N, (N - k) // 2) / 2.0 ** (N - 1) for k in ks]
+    if N % 2 == 0:
+        a[0] /= 2
+    return ks, a
+
+
+@pytest.mark.parametrize("N", [0, 1, 4, 11, 41])
+def test_truncated_kernel_full_expansion_is_cos_power(N):
+    """All N/2 + 1 harmonics: the expansion is cos^N exactly (binomial
+    theorem), so the truncated-kernel filter reproduces the q_N filter."""
+    K = N // 2 + 1
+    for t in np.linspace(-1, 1, 41):
+        assert abs(oracle.trunc_weight(t, GAMMA1, N, K) - math.cos(GAMMA1 * t) ** N) <= 1e-14
+    f = synth.rectangles(14, 17, seed=N).astype(np.float64)
+    np.testing.assert_allclose(
+        oracle.bilateral_general(f, 3, range_kind=oracle.RANGE_TRUNC, gamma=GAMMA1, N=N,
+                                 K_keep=K),
+        oracle.bilateral(f, 3, GAMMA1, N), rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("N,K", [(11, 3), (41, 11), (41, 15), (20, 4)])
+def test_truncated_kernel_error_closed_form(N, K):
+    """Dropping the harmonics from index K on changes the kernel by at most
+    the dropped coefficients' sum, reached at t = 0 (all cosines 1); the
+    kept kernel equals an independent sum of math.cos terms."""
+    ks, a = binom_coeffs(N)
+    tail = sum(a[K:])
+    ts = np.linspace(-1, 1, 801)
+    dev = [abs(oracle.trunc_weight(t, GAMMA1, N, K) - math.cos(GAMMA1 * t) ** N) for t in ts]
+    assert max(dev) <= tail + 1e-14
+    assert abs(oracle.trunc_weight(0.0, GAMMA1, N, K) - (1.0 - tail)) <= 1e-14
+    for t in (-0.7, 0.13, 0.9):
+        ref = sum(ai * math.cos(k * GAMMA1 * t) for ai, k in zip(a[:K], ks[:K]))
+        assert abs(oracle.trunc_weight(t, GAMMA1, N, K) - ref) <= 1e-14
+
+
+def test_truncated_filter_brute_force_and_bound():
+    """Truncated-kernel filter against a Python quadruple loop, and its
+    distance to the exact q_N filter within the bound
+    |out_t - out| <= n * tail * max|f - out_t| / den (den of the exact q_N)."""
+    N, K, r = 41, 11, 2
+    ks, a = binom_coeffs(N)
+    f = np.random.default_rng(3).uniform(0, 1, (7, 9))
+    H, W = f.shape
+    ref = np.zeros((H, W))
+    for y in range(H):
+        for x in range(W):
+            num = eta = 0.0
+            for yy in range(max(0, y - r), min(H, y + r + 1)):
+                for xx in range(max(0, x - r), min(W, x + r + 1)):
+                    t = f[yy, xx] - f[y, x]
+                    w = sum(ai * math.cos(k * GAMMA1 * t) for ai, k in zip(a[:K], ks[:K]))
+                    num += w * f[yy, xx]
+                    eta += w
+            ref[y, x] = num / eta
+    got = oracle.bilateral_general(f, r, range_kind=oracle.RANGE_TRUNC, gamma=GAMMA1, N=N,
+                                   K_keep=K)
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-13)
+    # out - out_t = sum (w - w_t)(f - out_t) / sum w, |w - w_t| <= tail, |f - out_t| <= 1
+    exact, den = oracle.bilateral(f, r, GAMMA1, N, return_den=True)
+    tail = sum(a[K:])
+    n = (2 * r + 1) ** 2
+    assert np.all(np.abs(got - exact) <= n * tail / den + 1e-12)
