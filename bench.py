@@ -307,6 +307,54 @@ def extras(dev, flush, stream):
     res["differentiation_16x512sq_r7_N19"] = {
         "fwd_bwd_ms": ms_d, "fwd_bwd_mpx_s": B * Hd * Hd / ms_d / 1e3,
         "grad_max_rel_err_vs_fp64_fd": gerr}
+    del ft, wt, outd, svd, gi
+
+    # truncated basis (end of Sec. 3): the headline workload with the highest
+    # harmonics of q_N's expansion dropped under a kernel tolerance
+    f_np = synth.rectangles(H, W, seed=0)
+    img = torch.from_numpy(f_np).to(dev)
+    g_t = torch.from_numpy(synth.weights((H, W), seed=1)).to(dev)
+    out = torch.empty_like(img)
+    sv = torch.empty((H, W, 4), device=dev)
+    gimg = torch.empty_like(img)
+    Nt = bf.bf_resolve_N(SIGMA, T_RANGE)
+    rows = [int(y) for y in rng.integers(0, H, 3)]
+    f64 = f_np.astype(np.float64)
+    exact = {y: oracle.bilateral(f64, R, oracle.gamma_fixed(T_RANGE), Nt, rows=(y, y + 1))[0]
+             for y in rows}
+    trunc = {}
+    for tol in (1e-6, 1e-3):
+        K = bf.bf_trunc_harmonics(Nt, R, tol)
+        o = bf._opts(save=True, trunc_tol=tol)
+        ws_n = bf.bf_backward_workspace_bytes(H, W, R, SIGMA, T_RANGE, Nt, o)
+        ws = torch.empty((max(ws_n, 4) + 3) // 4, device=dev)
+
+        def fb(o=o, ws=ws):
+            bf.bf_forward(img, R, SIGMA, T_RANGE, Nt, out=out, opts=o, saved=sv, stream=stream)
+            bf.bf_backward(img, out, g_t, sv, R, SIGMA, T_RANGE, Nt, grad_img=gimg, workspace=ws,
+                           opts=o, stream=stream)
+
+        def fo(o=o):
+            bf.bf_forward(img, R, SIGMA, T_RANGE, Nt, out=out, opts=o, saved=sv, stream=stream)
+        fb()
+        ms_fb = _time_ms(fb, flush, stream)
+        ms_f = _time_ms(fo, flush, stream)
+        fo()
+        o_np = out.cpu().numpy()
+        got = np.concatenate([o_np[y] for y in rows])
+        ref_t = np.concatenate([oracle.bilateral_general(f64, R, range_kind=oracle.RANGE_TRUNC,
+                                                         gamma=oracle.gamma_fixed(T_RANGE), N=Nt,
+                                                         K_keep=K, rows=(y, y + 1))[0]
+                                for y in rows])
+        ref_e = np.concatenate([exact[y] for y in rows])
+        trunc[f"tol_{tol:g}"] = {
+            "harmonics_kept": K, "harmonics_exact": Nt // 2 + 1,
+            "fwd_ms": ms_f, "fwd_mpx_s": H * W / ms_f / 1e3,
+            "fwd_bwd_ms": ms_fb, "fwd_bwd_mpx_s": H * W / ms_fb / 1e3,
+            "err_vs_fp64_truncated_kernel": _err_stats(got, ref_t),
+            "err_vs_fp64_exact_qN": _err_stats(got, ref_e),
+            "rows_checked": rows}
+    res["truncated_basis_4096sq_r10_N41"] = trunc
     return res
 
 
