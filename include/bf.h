@@ -245,6 +245,27 @@ bf_status bf_backward_noalloc(const void* img, const float* out, const float* gr
                               int N, float* grad_img, float* grad_sigma, const bf_opts* opts,
                               void* stream);
 
+/*
+ * Algorithm 2 with a shiftable spatial kernel as well (Sec. 2), and
+ * Algorithm 1 as its case N = 0: the neighbourhood filter
+ *   out(x) = sum_y phi(y - x) w(f(y) - f(x)) f(y) / sum_y phi(y - x) w(f(y) - f(x))
+ * over the (2r+1)^2 window (truncated at the image border), with the
+ * separable spatial kernel phi(d) = q_M(d1) q_M(d2) of Sec. 3, q_M(d) =
+ * cos^M(pi d / (2r + 1)) (q_M on [-(r + 1/2), r + 1/2], so the window lies
+ * inside its support), and the range kernel w = q_N of bf_forward (N = 0: no
+ * range kernel, i.e. the linear spatial filter of Eq. filter1 / Algorithm 1;
+ * N < 0: derived from sigma_r like bf_forward's N <= 0). Computed from
+ * (M+1)^2 (N+1) shiftable basis functions by moving sums, in one fused pass.
+ *   img, out  device H x W FP32 (out must not alias img).
+ *   M         1..4, 6 or 8 when N = 0; 1 or 2 when 1 <= N <= 4.
+ *   r         0..56.
+ *   opts      NULL or defaults; gamma_mode and tile_h are honoured; BF16
+ *             input, Kahan and trunc_tol give BF_ERR_UNSUPPORTED.
+ * Errors: BF_ERR_INVALID_ARG, BF_ERR_UNSUPPORTED (other M, N, r), BF_ERR_CUDA.
+ */
+bf_status bf_spatial_forward(const void* img, int H, int W, int r, int M, float sigma_r, float T,
+                             int N, float* out, const bf_opts* opts, void* stream);
+
 /* Workspace bytes bf_batch needs for n descriptors (device tile table). */
 size_t bf_batch_workspace_bytes(const bf_desc* descs, int n, const bf_opts* opts);
 

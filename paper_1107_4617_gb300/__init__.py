@@ -23,6 +23,7 @@ __all__ = [
     "bf_batch_launch", "bf_backward3d_workspace_bytes",
     "bf_resolve_N", "bf_coeffs", "bf_trunc_harmonics", "bf_gamma", "bf_saved_bytes", "bf_backward_workspace_bytes",
     "bf_batch_workspace_bytes", "bf_status_string", "bf_last_cuda_error", "bilateral",
+    "bf_spatial_forward",
     "GAMMA_FIXED", "GAMMA_FROM_SIGMA", "F32", "BF16", "N_MAX", "R_MAX",
 ]
 
@@ -100,6 +101,8 @@ def load():
                                       c_int, vp, vp, vp, c_size, P_opts, vp]),
             "bf_backward": (c_int, [vp, vp, vp, vp, c_int, c_int, c_int, c_float, c_float, c_int,
                                     vp, vp, vp, c_size, P_opts, vp]),
+            "bf_spatial_forward": (c_int, [vp, c_int, c_int, c_int, c_int, c_float, c_float,
+                                           c_int, vp, P_opts, vp]),
             "bf_batch_workspace_bytes": (c_size, [P_desc, c_int, P_opts]),
             "bf_batch": (c_int, [P_desc, c_int, P_opts, vp, c_size, vp]),
             "bf_batch_prepare": (c_int, [P_desc, c_int, P_opts, vp, c_size, vp]),
@@ -250,6 +253,26 @@ def bf_backward(img, out, grad_out, saved, r: int, sigma_r: float, T: float = 1.
                             _dptr(workspace, "workspace") if workspace is not None else None,
                             ws_bytes, ctypes.byref(opts), _stream_handle(stream))
     _check("bf_backward", st)
+
+
+def bf_spatial_forward(img, r: int, M: int, sigma_r: float = 0.0, T: float = 1.0, N: int = 0,
+                       out=None, opts: BfOpts | None = None, stream=None):
+    """Neighbourhood filter with the separable spatial kernel q_M(d1) q_M(d2)
+    (q_M on [-(r+1/2), r+1/2]) and range kernel q_N (N = 0: none, i.e.
+    Algorithm 1; N < 0: from sigma_r): Algorithm 2 with a shiftable spatial
+    kernel. 2-D float32 CUDA tensor -> float32."""
+    import torch
+    if img.dim() != 2 or img.dtype != torch.float32:
+        raise ValueError("img must be a 2-D float32 tensor")
+    H, W = img.shape
+    if out is None:
+        out = torch.empty((H, W), dtype=torch.float32, device=img.device)
+    st = load().bf_spatial_forward(_dptr(img, "img"), H, W, int(r), int(M), float(sigma_r),
+                                   float(T), int(N), _dptr(out, "out"),
+                                   ctypes.byref(opts) if opts is not None else None,
+                                   _stream_handle(stream))
+    _check("bf_spatial_forward", st)
+    return out
 
 
 def bf_backward3d_workspace_bytes(B: int, H: int, W: int, r: int, sigma_r: float = 0.2,

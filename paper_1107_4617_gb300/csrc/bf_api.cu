@@ -135,8 +135,10 @@ static bool sys_tiles(int H, int W, int r, const bf_opts* o, Tiles* t) {
     if (o && o->tile_h > 0) {
         t->Hb = o->tile_h;
     } else {
+        // one wave of resident CTAs (rounding the band count up would start a
+        // second, nearly empty wave)
         const int target = (wi <= 128 ? 2 : 1) * sm_count();
-        int nb = (target + t->gx - 1) / t->gx;
+        int nb = target / t->gx;
         if (nb < 1) nb = 1;
         int hb = (H + nb - 1) / nb;
         if (hb < 32) hb = 32;

@@ -219,3 +219,13 @@ def test_kp_max_chunks(cuda_lib, kp_max):
     s1, s2 = np.moveaxis(sv1.cpu().numpy(), 2, 0), np.moveaxis(sv2.cpu().numpy(), 2, 0)
     scale = np.abs(s2).max(axis=(1, 2), keepdims=True)
     assert np.all(np.abs(s1 - s2) <= 1e-4 * scale)
+
+
+@pytest.mark.parametrize("H,W,r", [(300, 333, 0), (300, 333, 1), (64, 1000, 2), (512, 700, 1)])
+def test_small_r_wide_images(cuda_lib, H, W, r):
+    """Small windows (den close to 1 where neighbours differ) on wide images,
+    where the horizontal chain runs through all 128 lanes of a strip."""
+    f = synth.rectangles(H, W, seed=H + r)
+    got = run_fwd(cuda_lib, f, r, 0.1, 1.0, 0)
+    ref, _ = oracle_ref(f, r, 0.1, 1.0, 0)
+    assert rel_err(got, ref).max() <= TOL

@@ -270,3 +270,76 @@ def test_truncated_filter_brute_force_and_bound():
     tail = sum(a[K:])
     n = (2 * r + 1) ** 2
     assert np.all(np.abs(got - exact) <= n * tail / den + 1e-12)
+
+
+# ---- shiftable spatial kernel (Algorithm 1; Algorithm 2 with M > 0) ---------
+
+def test_spatial_kernel_closed_form():
+    """q_M(d) = cos^M(pi d / (2 Ts)) with Ts = r + 1/2 (Sec. 3): unimodal,
+    1 at d = 0, positive on the window |d| <= r."""
+    for r, M in [(1, 1), (5, 2), (10, 4), (3, 8)]:
+        vals = [oracle.spatial_weight(d, r, M) for d in range(-r, r + 1)]
+        for d, v in zip(range(-r, r + 1), vals):
+            assert abs(v - math.cos(math.pi * d / (2 * r + 1)) ** M) <= 1e-15
+        assert vals[r] == 1.0 and min(vals) > 0
+        assert all(vals[i] <= vals[i + 1] for i in range(r))
+
+
+@pytest.mark.parametrize("r,M", [(1, 1), (3, 2), (5, 4), (7, 6)])
+def test_algorithm1_is_normalised_separable_correlation(r, M):
+    """Without a range kernel the filter is the linear spatial filter of
+    Eq. filter1 normalised over the in-image part of the window: a separable
+    correlation of f and of the all-ones image with the 1-D q_M taps
+    (scipy.ndimage, zero padding), divided."""
+    ndimage = pytest.importorskip("scipy.ndimage")
+    f = synth.sinusoids(23, 31, seed=r + M).astype(np.float64)
+    taps = np.array([math.cos(math.pi * d / (2 * r + 1)) ** M for d in range(-r, r + 1)])
+
+    def sep(a):
+        a = ndimage.correlate1d(a, taps, axis=0, mode="constant", cval=0.0)
+        return ndimage.correlate1d(a, taps, axis=1, mode="constant", cval=0.0)
+    ref = sep(f) / sep(np.ones_like(f))
+    got = oracle.bilateral_general(f, r, spatial=oracle.SPATIAL_QM, M=M,
+                                   range_kind=oracle.RANGE_NONE)
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-13)
+
+
+def test_spatial_M0_is_box():
+    f = synth.rectangles(12, 15, seed=2).astype(np.float64)
+    np.testing.assert_allclose(
+        oracle.bilateral_general(f, 3, spatial=oracle.SPATIAL_QM, M=0, gamma=GAMMA1, N=11),
+        oracle.bilateral(f, 3, GAMMA1, 11), rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("r,M,N", [(2, 2, 4), (3, 1, 3), (1, 2, 0)])
+def test_spatial_range_brute_force(r, M, N):
+    """Algorithm 2's target, Eq. filter2 with phi = q_M x q_M and phi_range = q_N,
+    against an independent Python quadruple loop."""
+    f = np.random.default_rng(r * 7 + M + N).uniform(0, 1, (7, 8))
+    H, W = f.shape
+    ref = np.zeros((H, W))
+    for y in range(H):
+        for x in range(W):
+            num = eta = 0.0
+            for yy in range(max(0, y - r), min(H, y + r + 1)):
+                for xx in range(max(0, x - r), min(W, x + r + 1)):
+                    ws = (math.cos(math.pi * (yy - y) / (2 * r + 1)) ** M *
+                          math.cos(math.pi * (xx - x) / (2 * r + 1)) ** M)
+                    wr = math.cos(GAMMA1 * (f[yy, xx] - f[y, x])) ** N
+                    num += ws * wr * f[yy, xx]
+                    eta += ws * wr
+            ref[y, x] = num / eta
+    got = oracle.bilateral_general(f, r, spatial=oracle.SPATIAL_QM, M=M,
+                                   range_kind=oracle.RANGE_COSN if N else oracle.RANGE_NONE,
+                                   gamma=GAMMA1, N=N)
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-13)
+
+
+def test_spatial_constant_image_and_convexity():
+    c = np.full((9, 13), 0.37)
+    np.testing.assert_allclose(
+        oracle.bilateral_general(c, 4, spatial=oracle.SPATIAL_QM, M=2, gamma=GAMMA1, N=4), c,
+        rtol=0, atol=1e-15)
+    f = synth.rectangles(20, 20, seed=9).astype(np.float64)
+    out = oracle.bilateral_general(f, 3, spatial=oracle.SPATIAL_QM, M=2, gamma=GAMMA1, N=4)
+    assert out.min() >= f.min() - 1e-15 and out.max() <= f.max() + 1e-15
