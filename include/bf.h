@@ -266,6 +266,29 @@ bf_status bf_backward_noalloc(const void* img, const float* out, const float* gr
 bf_status bf_spatial_forward(const void* img, int H, int W, int r, int M, float sigma_r, float T,
                              int N, float* out, const bf_opts* opts, void* stream);
 
+/* Order of the polynomial range kernel p_N for a target Gaussian width:
+   N = ceil(T^2 / (2 sigma_r^2)), from Eq. approx1 (p_N(t / sqrt N) ->
+   exp(-t^2 / T^2), so p_N(t) ~ exp(-N t^2 / T^2)). -1 on bad arguments.
+   Host only. */
+int bf_poly_resolve_N(float sigma_r, float T);
+
+/*
+ * Bilateral filter with the box spatial kernel and the polynomial range
+ * kernel p_N(t) = (1 - t^2 / T^2)^N of Sec. 3 (order of shiftability 2N+1),
+ * by moving sums of the 2N+2 power images of u = f / T - 1/2 (Algorithm 2
+ * with a polynomial basis).
+ *   img, out  device H x W FP32 (out must not alias img). Precondition as
+ *             for bf_forward: values in [0, T].
+ *   N         1..8; N <= 0 derives it from sigma_r (bf_poly_resolve_N).
+ *   r         0..56.
+ *   opts      NULL or defaults (tile_h honoured); BF16 input, Kahan,
+ *             trunc_tol or BF_GAMMA_FROM_SIGMA give BF_ERR_UNSUPPORTED.
+ * Errors: BF_ERR_INVALID_ARG, BF_ERR_UNSUPPORTED (N > 8, r > 56),
+ * BF_ERR_CUDA.
+ */
+bf_status bf_poly_forward(const void* img, int H, int W, int r, float sigma_r, float T, int N,
+                          float* out, const bf_opts* opts, void* stream);
+
 /* Workspace bytes bf_batch needs for n descriptors (device tile table). */
 size_t bf_batch_workspace_bytes(const bf_desc* descs, int n, const bf_opts* opts);
 

@@ -23,7 +23,7 @@ __all__ = [
     "bf_batch_launch", "bf_backward3d_workspace_bytes",
     "bf_resolve_N", "bf_coeffs", "bf_trunc_harmonics", "bf_gamma", "bf_saved_bytes", "bf_backward_workspace_bytes",
     "bf_batch_workspace_bytes", "bf_status_string", "bf_last_cuda_error", "bilateral",
-    "bf_spatial_forward",
+    "bf_spatial_forward", "bf_poly_forward", "bf_poly_resolve_N",
     "GAMMA_FIXED", "GAMMA_FROM_SIGMA", "F32", "BF16", "N_MAX", "R_MAX",
 ]
 
@@ -103,6 +103,9 @@ def load():
                                     vp, vp, vp, c_size, P_opts, vp]),
             "bf_spatial_forward": (c_int, [vp, c_int, c_int, c_int, c_int, c_float, c_float,
                                            c_int, vp, P_opts, vp]),
+            "bf_poly_resolve_N": (c_int, [c_float, c_float]),
+            "bf_poly_forward": (c_int, [vp, c_int, c_int, c_int, c_float, c_float, c_int, vp,
+                                        P_opts, vp]),
             "bf_batch_workspace_bytes": (c_size, [P_desc, c_int, P_opts]),
             "bf_batch": (c_int, [P_desc, c_int, P_opts, vp, c_size, vp]),
             "bf_batch_prepare": (c_int, [P_desc, c_int, P_opts, vp, c_size, vp]),
@@ -272,6 +275,28 @@ def bf_spatial_forward(img, r: int, M: int, sigma_r: float = 0.0, T: float = 1.0
                                    ctypes.byref(opts) if opts is not None else None,
                                    _stream_handle(stream))
     _check("bf_spatial_forward", st)
+    return out
+
+
+def bf_poly_resolve_N(sigma_r: float, T: float = 1.0) -> int:
+    return int(load().bf_poly_resolve_N(float(sigma_r), float(T)))
+
+
+def bf_poly_forward(img, r: int, sigma_r: float = 0.0, T: float = 1.0, N: int = 0, out=None,
+                    opts: BfOpts | None = None, stream=None):
+    """Bilateral filter with the polynomial range kernel p_N(t) = (1 -
+    t^2/T^2)^N (Sec. 3) and the box window. 2-D float32 CUDA tensor."""
+    import torch
+    if img.dim() != 2 or img.dtype != torch.float32:
+        raise ValueError("img must be a 2-D float32 tensor")
+    H, W = img.shape
+    if out is None:
+        out = torch.empty((H, W), dtype=torch.float32, device=img.device)
+    st = load().bf_poly_forward(_dptr(img, "img"), H, W, int(r), float(sigma_r), float(T),
+                                int(N), _dptr(out, "out"),
+                                ctypes.byref(opts) if opts is not None else None,
+                                _stream_handle(stream))
+    _check("bf_poly_forward", st)
     return out
 
 

@@ -182,3 +182,11 @@ def test_truncated_basis_rule_rejects_bad_arguments():
     assert bf.bf_trunc_harmonics(11, -1, 0.0) == -1
     assert bf.bf_trunc_harmonics(11, 3, 1.0) == -1
     assert bf.bf_trunc_harmonics(11, 3, -0.5) == -1
+
+
+def test_poly_order_rule():
+    """N = ceil(T^2 / (2 sigma_r^2)) from Eq. approx1."""
+    for sigma, T, N in [(0.3, 1.0, 6), (0.25, 1.0, 8), (0.5, 1.0, 2), (0.4, 1.0, 4), (1.0, 2.0, 2)]:
+        assert bf.bf_poly_resolve_N(sigma, T) == N
+        assert N == max(1, math.ceil(T * T / (2 * sigma * sigma) - 1e-9))
+    assert bf.bf_poly_resolve_N(0.0, 1.0) == -1

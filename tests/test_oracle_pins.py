@@ -343,3 +343,44 @@ def test_spatial_constant_image_and_convexity():
     f = synth.rectangles(20, 20, seed=9).astype(np.float64)
     out = oracle.bilateral_general(f, 3, spatial=oracle.SPATIAL_QM, M=2, gamma=GAMMA1, N=4)
     assert out.min() >= f.min() - 1e-15 and out.max() <= f.max() + 1e-15
+
+
+# ---- polynomial range kernel p_N (Sec. 3) -----------------------------------
+
+def test_poly_kernel_gaussian_limit():
+    """Eq. approx1: p_N(t / sqrt(N)) -> exp(-t^2 / T^2), monotonically in N on
+    [-T, T] (T = 1 here), with the direct oracle filter converging to the
+    exact-Gaussian filter of variance T^2 / 2."""
+    t = np.linspace(-1, 1, 201)
+    gaps = []
+    for N in (1, 2, 4, 8, 16, 64, 256):
+        pn = (1 - (t / math.sqrt(N)) ** 2) ** N
+        gaps.append(np.max(np.abs(pn - np.exp(-t ** 2))))
+    assert all(a > b for a, b in zip(gaps, gaps[1:])) and gaps[-1] < 2e-3
+    f = synth.rectangles(24, 24, seed=4).astype(np.float64)
+    # p_N with T_r = sqrt(N) T: kernel (1 - t^2/(N T^2))^N -> exp(-t^2/T^2) = Gaussian sigma^2 = 1/2
+    g = oracle.bilateral_gauss(f, 3, math.sqrt(0.5))
+    errs = [np.abs(oracle.bilateral_general(f, 3, range_kind=oracle.RANGE_POLY, N=N,
+                                            Tr=math.sqrt(N)) - g).max() for N in (2, 8, 32)]
+    assert errs[0] > errs[1] > errs[2]
+
+
+def test_poly_filter_brute_force_and_N0():
+    N, r = 3, 2
+    f = np.random.default_rng(8).uniform(0, 1, (6, 9))
+    H, W = f.shape
+    ref = np.zeros((H, W))
+    for y in range(H):
+        for x in range(W):
+            num = eta = 0.0
+            for yy in range(max(0, y - r), min(H, y + r + 1)):
+                for xx in range(max(0, x - r), min(W, x + r + 1)):
+                    w = (1.0 - (f[yy, xx] - f[y, x]) ** 2) ** N
+                    num += w * f[yy, xx]
+                    eta += w
+            ref[y, x] = num / eta
+    got = oracle.bilateral_general(f, r, range_kind=oracle.RANGE_POLY, N=N, Tr=1.0)
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-13)
+    # p_0 = 1: the box mean
+    np.testing.assert_allclose(oracle.bilateral_general(f, r, range_kind=oracle.RANGE_POLY, N=0),
+                               box_sum(f, r) / box_sum(np.ones_like(f), r), rtol=0, atol=1e-14)

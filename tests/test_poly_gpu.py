@@ -1,0 +1,56 @@
+"""GPU parity of bf_poly_forward (polynomial range kernel p_N of Sec. 3,
+box window) against the oracle's direct definition, element by element:
+|gpu - oracle| / max(|oracle|, 1e-2) <= 1e-4."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1107_4617_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-4
+
+
+def rel_err(got, ref):
+    return np.abs(np.asarray(got, np.float64) - ref) / np.maximum(np.abs(ref), 1e-2)
+
+
+def run(bf, f, r, N, T=1.0):
+    out = bf.bf_poly_forward(torch.from_numpy(np.ascontiguousarray(f)).cuda(), r, 0.0, T, N)
+    return out.cpu().numpy()
+
+
+def ref(f, r, N, T=1.0):
+    return oracle.bilateral_general(f.astype(np.float64), r, range_kind=oracle.RANGE_POLY, N=N,
+                                    Tr=T)
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4, 5, 6, 7, 8])
+def test_poly_orders(cuda_lib, N):
+    f = synth.rectangles(200, 250, seed=N)
+    assert rel_err(run(cuda_lib, f, 5, N), ref(f, 5, N)).max() <= TOL
+
+
+@pytest.mark.parametrize("H,W,r,N", [(1, 1, 2, 6), (1, 300, 3, 6), (300, 1, 3, 6), (512, 512, 10, 6),
+                                     (97, 333, 30, 8), (140, 260, 56, 4), (64, 64, 0, 6)])
+def test_poly_shapes_and_windows(cuda_lib, H, W, r, N):
+    f = synth.sinusoids(H, W, seed=H + W)
+    assert rel_err(run(cuda_lib, f, r, N), ref(f, r, N)).max() <= TOL
+
+
+def test_poly_range_bound_T(cuda_lib):
+    """Values in [0, T] with T = 2: the kernel is p_N(t) = (1 - t^2/4)^N."""
+    f = 2.0 * synth.rectangles(150, 180, seed=3)
+    assert rel_err(run(cuda_lib, f, 6, 5, T=2.0), ref(f, 6, 5, T=2.0)).max() <= TOL
+
+
+def test_poly_order_from_sigma(cuda_lib):
+    bf = cuda_lib
+    f = torch.from_numpy(synth.rectangles(64, 80, seed=1)).cuda()
+    a = bf.bf_poly_forward(f, 4, 0.3, 1.0, 0)
+    b = bf.bf_poly_forward(f, 4, 0.0, 1.0, bf.bf_poly_resolve_N(0.3, 1.0))
+    assert torch.equal(a, b)
+    with pytest.raises(bf.BfError):
+        bf.bf_poly_forward(f, 4, 0.0, 1.0, 9)
