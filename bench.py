@@ -355,6 +355,60 @@ def extras(dev, flush, stream):
             "err_vs_fp64_exact_qN": _err_stats(got, ref_e),
             "rows_checked": rows}
     res["truncated_basis_4096sq_r10_N41"] = trunc
+    del img, g_t, out, sv, gimg
+
+    # Algorithm 2 with a shiftable spatial kernel (q_M x q_M), Algorithm 1
+    # (no range kernel), and the polynomial range kernel p_N
+    def basis_flops(n_basis):
+        return 17 * n_basis + 10  # per output pixel, same per-basis-function model
+
+    spatial = {}
+    f512 = synth.rectangles(512, 512, seed=0)
+    t512 = torch.from_numpy(f512).to(dev)
+    o512 = torch.empty_like(t512)
+    call = lambda: bf.bf_spatial_forward(t512, 5, 2, 0.0, 1.0, 4, out=o512, stream=stream)
+    call()
+    ms = _time_ms(call, flush, stream)
+    ref512 = oracle.bilateral_general(f512.astype(np.float64), 5, spatial=oracle.SPATIAL_QM, M=2,
+                                      range_kind=oracle.RANGE_COSN,
+                                      gamma=oracle.gamma_fixed(1.0), N=4)
+    spatial["paper_instance_512sq_T5_3x3x5"] = {
+        "ms": ms, "mpx_s": 512 * 512 / ms / 1e3, "basis_functions": 45,
+        "paper_matlab_s": 2.5, "err_vs_fp64": _err_stats(o512.cpu().numpy(), ref512)}
+    img = torch.from_numpy(f_np).to(dev)
+    out = torch.empty_like(img)
+    for name, M, N_, kind in [("alg2_4096sq_r10_M2_N4", 2, 4, oracle.RANGE_COSN),
+                              ("alg1_4096sq_r10_M2", 2, 0, oracle.RANGE_NONE)]:
+        call = lambda M=M, N_=N_: bf.bf_spatial_forward(img, R, M, 0.0, 1.0, N_, out=out,
+                                                        stream=stream)
+        call()
+        ms = _time_ms(call, flush, stream)
+        o_np = out.cpu().numpy()
+        got = np.concatenate([o_np[y] for y in rows])
+        ref_s = np.concatenate([oracle.bilateral_general(f64, R, spatial=oracle.SPATIAL_QM, M=M,
+                                                         range_kind=kind,
+                                                         gamma=oracle.gamma_fixed(1.0), N=N_,
+                                                         rows=(y, y + 1))[0] for y in rows])
+        nb = (M + 1) ** 2 * (N_ + 1)
+        tf = basis_flops(nb) * H * W / (ms * 1e-3) / 1e12
+        spatial[name] = {"ms": ms, "mpx_s": H * W / ms / 1e3, "basis_functions": nb,
+                         "tflops_algorithmic": tf, "frac_of_fp32_peak": tf / FP32_PEAK_TFLOPS,
+                         "err_vs_fp64": _err_stats(got, ref_s)}
+    res["spatial_kernel"] = spatial
+
+    Np = bf.bf_poly_resolve_N(0.3, 1.0)
+    call = lambda: bf.bf_poly_forward(img, R, 0.3, 1.0, 0, out=out, stream=stream)
+    call()
+    ms = _time_ms(call, flush, stream)
+    o_np = out.cpu().numpy()
+    got = np.concatenate([o_np[y] for y in rows])
+    ref_p = np.concatenate([oracle.bilateral_general(f64, R, range_kind=oracle.RANGE_POLY, N=Np,
+                                                     Tr=1.0, rows=(y, y + 1))[0] for y in rows])
+    tf = basis_flops(2 * Np + 1) * H * W / (ms * 1e-3) / 1e12
+    res[f"poly_range_4096sq_r10_sigma0.3_N{Np}"] = {
+        "ms": ms, "mpx_s": H * W / ms / 1e3, "basis_functions": 2 * Np + 1,
+        "tflops_algorithmic": tf, "frac_of_fp32_peak": tf / FP32_PEAK_TFLOPS,
+        "err_vs_fp64": _err_stats(got, ref_p)}
     return res
 
 
@@ -401,6 +455,10 @@ def main():
     ap.add_argument("--kernels-only", action="store_true",
                     help="time the device step only (no e2e, N=40, CPU or accuracy legs); "
                          "used for profiler captures")
+    ap.add_argument("--profile-workload", default=None,
+                    choices=["spatial_M2_N4", "alg1_M2", "poly_N6", "trunc_1e-3"],
+                    help="launch only this 4096^2 r=10 workload's kernel, warmup + steps "
+                         "times (profiler captures of the extra workloads)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -441,6 +499,26 @@ def main():
     flush = torch.empty((L2_FLUSH_BYTES // 4,), dtype=torch.float32, device=dev)
     opts = bf._opts(save=True)
     stream = torch.cuda.current_stream(dev)
+
+    if args.profile_workload:
+        pw = args.profile_workload
+        if pw == "spatial_M2_N4":
+            call = lambda: bf.bf_spatial_forward(img, R, 2, 0.0, 1.0, 4, out=out, stream=stream)
+        elif pw == "alg1_M2":
+            call = lambda: bf.bf_spatial_forward(img, R, 2, 0.0, 1.0, 0, out=out, stream=stream)
+        elif pw == "poly_N6":
+            call = lambda: bf.bf_poly_forward(img, R, 0.0, 1.0, 6, out=out, stream=stream)
+        else:
+            to = bf._opts(save=True, trunc_tol=1e-3)
+            call = lambda: bf.bf_forward(img, R, SIGMA, T_RANGE, N, out=out, opts=to, saved=saved,
+                                         stream=stream)
+        for _ in range(args.warmup):
+            call()
+        ms = _time_ms(call, flush, stream, reps=args.steps)
+        if rank == 0:
+            print(json.dumps({"profile_workload": pw, "ms": ms, "mpx_s": H * W / ms / 1e3}),
+                  flush=True)
+        return
 
     def step():
         bf.bf_forward(img, R, SIGMA, T_RANGE, N, out=out, opts=opts, saved=saved, stream=stream)

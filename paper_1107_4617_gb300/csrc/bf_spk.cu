@@ -99,14 +99,17 @@ __device__ __forceinline__ void range_harmonics(float f, float gamma, float2 (&z
     }
 }
 
-// Row phases e^{i b gs row} for signed b = -M, ..., M (step 2).
+// Longest phase table: 2 (2r + 1) entries for r <= 56.
+constexpr int PTAB_CAP = 2 * (2 * 56 + 1);
+
+// Row phases e^{i b gs row} for signed b = -M, ..., M (step 2), from the
+// table tab[q] = e^{i pi q / (2r+1)} and the row's indices q[b] = b row mod
+// 2 (2r + 1) of the non-negative b (ib >= M / 2).
 template <int M>
-__device__ __forceinline__ void row_phases(int row, int r, float2 (&p)[M + 1]) {
+__device__ __forceinline__ void row_phases(const float2* tab, const int (&q)[M + 1],
+                                           float2 (&p)[M + 1]) {
 #pragma unroll
-    for (int ib = 0; ib <= M; ++ib) {
-        const int b = -M + 2 * ib;
-        if (b >= 0) p[ib] = phase(b, row, r);
-    }
+    for (int ib = M / 2 + (M & 1 ? 1 : 0); ib <= M; ++ib) p[ib] = tab[q[ib]];
 #pragma unroll
     for (int ib = 0; ib <= M; ++ib)
         if (-M + 2 * ib < 0) p[ib] = conj2(p[M - ib]);
@@ -137,6 +140,25 @@ __global__ void __launch_bounds__(WMAX, 2) spk_kernel(Params p) {
     const float sgn2 = (M & 1) ? 1.f : -1.f;  // -(-1)^M: weight of the second column
 
     for (int i = j; i < 2 * BUF; i += Wi) smem[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int P = 2 * (2 * r + 1);  // period of e^{i gs n} in n
+    float2* ptab = reinterpret_cast<float2*>(smem + 2 * BUF);
+    for (int q = j; q < P; q += Wi) {
+        float s, c;
+        sincospif((float)q / (float)(2 * r + 1), &s, &c);
+        ptab[q] = make_float2(c, s);
+    }
+    // phase indices b row mod P of the entering row (advanced by b per step)
+    // and their offsets to the centre row rho = e - r
+    int qe[M + 1], qoff[M + 1];
+#pragma unroll
+    for (int ib = 0; ib <= M; ++ib) {
+        const int b = -M + 2 * ib;
+        const int bb = b < 0 ? 0 : b;
+        int q0 = (int)(((long long)bb * (long long)(y0 - r - j)) % P);
+        if (q0 < 0) q0 += P;
+        qe[ib] = q0;
+        qoff[ib] = (bb * r) % P;
+    }
 
     // column phases e^{i a gs c} of the own and of the centre column
     float2 cph[D::NA], cphc[D::NA];
@@ -152,7 +174,13 @@ __global__ void __launch_bounds__(WMAX, 2) spk_kernel(Params p) {
     for (int d = 0; d < D::ND; ++d) { Dg[d] = make_float2(0.f, 0.f); Dh[d] = Dg[d]; }
     __syncthreads();
 
-    for (int t = 0; t < steps; ++t) {
+    for (int t = 0; t < steps; ++t, [&] {
+#pragma unroll
+             for (int ib = 0; ib <= M; ++ib) {
+                 const int b = -M + 2 * ib;
+                 if (b > 0) { qe[ib] += b; if (qe[ib] >= P) qe[ib] -= P; }
+             }
+         }()) {
         const int warp_first = t - (w * 32 + 31);
         const int warp_last = t - w * 32;
         if (warp_last >= 0 && warp_first < span) {
@@ -175,7 +203,7 @@ __global__ void __launch_bounds__(WMAX, 2) spk_kernel(Params p) {
             // vertical: entering row's phases; the leaving row's differ by
             // e^{-i b gs (2r+1)} = (-1)^M for every b of this parity
             float2 rp[M + 1];
-            row_phases<M>(e, r, rp);
+            row_phases<M>(ptab, qe, rp);
             const float lsg = (M & 1) ? -1.f : 1.f;
             auto accumulate = [&](float f, float wgt, float rsg) {
                 float2 z[N + 1];
@@ -203,7 +231,15 @@ __global__ void __launch_bounds__(WMAX, 2) spk_kernel(Params p) {
 
             // horizontal and recombination with the centre's conj(E_c)
             float2 rpc[M + 1];
-            row_phases<M>(rho, r, rpc);
+            {
+                int qc[M + 1];
+#pragma unroll
+                for (int ib = 0; ib <= M; ++ib) {
+                    qc[ib] = qe[ib] - qoff[ib];
+                    if (qc[ib] < 0) qc[ib] += P;
+                }
+                row_phases<M>(ptab, qc, rpc);
+            }
             float2 zc[N + 1];
             range_harmonics<N>(fc, p.gamma, zc);
             const float4* rd = smem + ((t + 1) & 1) * BUF + j;
@@ -241,7 +277,8 @@ static cudaError_t launch(const Params& p, int gx, int gy, cudaStream_t s) {
     using D = Dims<M, N>;
     static_assert(D::NS <= NS_CAP, "combo table");
     auto kern = spk_kernel<M, N>;
-    const size_t smem = sizeof(float4) * 2 * (size_t)D::NS * (WMAX + 1);
+    const size_t smem = sizeof(float4) * 2 * (size_t)D::NS * (WMAX + 1) +
+                        sizeof(float2) * PTAB_CAP;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
