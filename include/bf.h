@@ -313,6 +313,15 @@ bf_status bf_batch_prepare(const bf_desc* descs, int n, const bf_opts* opts, voi
    carry the same kahan / in_dtype as the prepare call. */
 bf_status bf_batch_launch(void* workspace, size_t ws_bytes, const bf_opts* opts, void* stream);
 
+/* Minimum and maximum of an H x W device image (dtype BF_F32 or BF_BF16), for
+   checking the filters' precondition max f - min f <= T (Sec. 3: the range
+   kernels are valid kernels on [-T, T] only). Writes the two floats (min,
+   max) to the DEVICE pointer minmax (8-byte aligned), asynchronously on
+   `stream`. NaN values are not supported. Paper counterpart: the a-priori
+   bound on the data that Sec. 3 assumes. Errors: BF_ERR_INVALID_ARG,
+   BF_ERR_CUDA. */
+bf_status bf_check_range(const void* img, int H, int W, int in_dtype, float* minmax, void* stream);
+
 /* Static message for a status code. */
 const char* bf_status_string(bf_status s);
 

@@ -23,7 +23,7 @@ __all__ = [
     "bf_batch_launch", "bf_backward3d_workspace_bytes",
     "bf_resolve_N", "bf_coeffs", "bf_trunc_harmonics", "bf_gamma", "bf_saved_bytes", "bf_backward_workspace_bytes",
     "bf_batch_workspace_bytes", "bf_status_string", "bf_last_cuda_error", "bilateral",
-    "bf_spatial_forward", "bf_poly_forward", "bf_poly_resolve_N",
+    "bf_spatial_forward", "bf_poly_forward", "bf_poly_resolve_N", "bf_check_range",
     "GAMMA_FIXED", "GAMMA_FROM_SIGMA", "F32", "BF16", "N_MAX", "R_MAX",
 ]
 
@@ -106,6 +106,7 @@ def load():
             "bf_poly_resolve_N": (c_int, [c_float, c_float]),
             "bf_poly_forward": (c_int, [vp, c_int, c_int, c_int, c_float, c_float, c_int, vp,
                                         P_opts, vp]),
+            "bf_check_range": (c_int, [vp, c_int, c_int, c_int, vp, vp]),
             "bf_batch_workspace_bytes": (c_size, [P_desc, c_int, P_opts]),
             "bf_batch": (c_int, [P_desc, c_int, P_opts, vp, c_size, vp]),
             "bf_batch_prepare": (c_int, [P_desc, c_int, P_opts, vp, c_size, vp]),
@@ -298,6 +299,20 @@ def bf_poly_forward(img, r: int, sigma_r: float = 0.0, T: float = 1.0, N: int = 
                                 _stream_handle(stream))
     _check("bf_poly_forward", st)
     return out
+
+
+def bf_check_range(img, stream=None):
+    """(min, max) of a 2-D float32/bfloat16 CUDA tensor as a device tensor of 2
+    floats (the filters need max - min <= T)."""
+    import torch
+    if img.dim() != 2:
+        raise ValueError("img must be 2-D")
+    H, W = img.shape
+    mm = torch.empty((2,), dtype=torch.float32, device=img.device)
+    st = load().bf_check_range(_dptr(img, "img"), H, W, _in_dtype(img), _dptr(mm, "minmax"),
+                               _stream_handle(stream))
+    _check("bf_check_range", st)
+    return mm
 
 
 def bf_backward3d_workspace_bytes(B: int, H: int, W: int, r: int, sigma_r: float = 0.2,

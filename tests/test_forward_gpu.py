@@ -229,3 +229,40 @@ def test_small_r_wide_images(cuda_lib, H, W, r):
     got = run_fwd(cuda_lib, f, r, 0.1, 1.0, 0)
     ref, _ = oracle_ref(f, r, 0.1, 1.0, 0)
     assert rel_err(got, ref).max() <= TOL
+
+
+@pytest.mark.parametrize("size", [1024, 4096])
+@pytest.mark.parametrize("kind", ["rect", "sin"])
+@pytest.mark.parametrize("r,sigma", [(3, 0.1), (10, 0.2), (30, 0.3)])
+def test_sweep_full_size_sampled(cuda_lib, size, kind, r, sigma):
+    """The forward sweep at its own sizes (1024^2 and 4096^2, rectangles+noise
+    and the sinusoid field, r in {3, 10, 30}, sigma_r 0.1/0.2/0.3 -> N =
+    41/11/5) in the default launch configuration: 400 sampled pixels plus
+    the corners and edge midpoints against the oracle, evaluated one by one."""
+    f = synth.image(kind, size, size, seed=2)
+    got = run_fwd(cuda_lib, f, r, sigma, 1.0, 0)
+    rng = np.random.default_rng(size + r)
+    n = size * size
+    idx = np.concatenate([rng.integers(0, n, 400),
+                          [0, size - 1, n - size, n - 1, size // 2, (size // 2) * size,
+                           (size // 2) * size + size - 1, n - size + size // 2]])
+    ref = oracle.bilateral_points(f.astype(np.float64), r, math.pi / 2,
+                                  oracle.resolve_N(sigma, 1.0), idx)
+    assert rel_err(got.ravel()[idx], ref).max() <= TOL
+    assert np.isfinite(got).all()
+
+
+@pytest.mark.parametrize("H,W", [(1, 1), (7, 3), (512, 700), (2048, 2048)])
+def test_check_range(cuda_lib, H, W):
+    """bf_check_range reports the image's min and max (the precondition
+    max - min <= T of the range kernels), FP32 and BF16."""
+    bf = cuda_lib
+    rng = np.random.default_rng(H + W)
+    f = rng.normal(0.3, 2.0, (H, W)).astype(np.float32)
+    t = torch.from_numpy(f).cuda()
+    mm = bf.bf_check_range(t).cpu().numpy()
+    assert mm[0] == f.min() and mm[1] == f.max()
+    tb = t.to(torch.bfloat16)
+    mb = bf.bf_check_range(tb).cpu().numpy()
+    fb = tb.float().cpu().numpy()
+    assert mb[0] == fb.min() and mb[1] == fb.max()
