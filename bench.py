@@ -59,10 +59,15 @@ def bwd_flops_per_px(N: int) -> int:
     return 26 * (N + 1) + 30
 
 
+# sources that define the headline kernels and their launch shape
+HEADLINE_SOURCES = ("bf_api.cu", "bf_internal.cuh", "bf_sys.cu", "bf_sys_engine.cuh",
+                    "bf_sys_w128.cu")
+
+
 def src_hash() -> str:
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1107_4617_gb300", "csrc")
-    for fn in sorted(os.listdir(d)):
+    for fn in HEADLINE_SOURCES:
         with open(os.path.join(d, fn), "rb") as fh:
             h.update(fn.encode())
             h.update(fh.read())
@@ -155,6 +160,16 @@ def cpu_baseline(sample_rows: int = 512):
     return px / dt / 1e6, oracle.num_threads(), (
         f"oracle forward + reference gradient on rows 0..{sample_rows - 1} "
         f"({sample_rows}x{W} px) of the 4096x4096 r=10 N=41 workload, {dt:.1f} s")
+
+
+def _oracle_timed(fn, px):
+    """Runs an oracle computation of px output pixels on the host cores and
+    returns (result, {Mpixel/s, seconds, cores})."""
+    import oracle
+    t0 = time.perf_counter()
+    res = fn()
+    dt = time.perf_counter() - t0
+    return res, {"mpx_s": px / dt / 1e6, "s": dt, "cores": oracle.num_threads(), "pixels": px}
 
 
 def _time_ms(fn, flush, stream, reps=3):
@@ -342,10 +357,10 @@ def extras(dev, flush, stream):
         fo()
         o_np = out.cpu().numpy()
         got = np.concatenate([o_np[y] for y in rows])
-        ref_t = np.concatenate([oracle.bilateral_general(f64, R, range_kind=oracle.RANGE_TRUNC,
-                                                         gamma=oracle.gamma_fixed(T_RANGE), N=Nt,
-                                                         K_keep=K, rows=(y, y + 1))[0]
-                                for y in rows])
+        ref_t, o_t = _oracle_timed(lambda: np.concatenate([
+            oracle.bilateral_general(f64, R, range_kind=oracle.RANGE_TRUNC,
+                                     gamma=oracle.gamma_fixed(T_RANGE), N=Nt, K_keep=K,
+                                     rows=(y, y + 1))[0] for y in rows]), len(rows) * W)
         ref_e = np.concatenate([exact[y] for y in rows])
         trunc[f"tol_{tol:g}"] = {
             "harmonics_kept": K, "harmonics_exact": Nt // 2 + 1,
@@ -353,7 +368,7 @@ def extras(dev, flush, stream):
             "fwd_bwd_ms": ms_fb, "fwd_bwd_mpx_s": H * W / ms_fb / 1e3,
             "err_vs_fp64_truncated_kernel": _err_stats(got, ref_t),
             "err_vs_fp64_exact_qN": _err_stats(got, ref_e),
-            "rows_checked": rows}
+            "rows_checked": rows, "oracle_forward": o_t}
     res["truncated_basis_4096sq_r10_N41"] = trunc
     del img, g_t, out, sv, gimg
 
@@ -369,12 +384,14 @@ def extras(dev, flush, stream):
     call = lambda: bf.bf_spatial_forward(t512, 5, 2, 0.0, 1.0, 4, out=o512, stream=stream)
     call()
     ms = _time_ms(call, flush, stream)
-    ref512 = oracle.bilateral_general(f512.astype(np.float64), 5, spatial=oracle.SPATIAL_QM, M=2,
-                                      range_kind=oracle.RANGE_COSN,
-                                      gamma=oracle.gamma_fixed(1.0), N=4)
+    ref512, o512t = _oracle_timed(
+        lambda: oracle.bilateral_general(f512.astype(np.float64), 5, spatial=oracle.SPATIAL_QM,
+                                         M=2, range_kind=oracle.RANGE_COSN,
+                                         gamma=oracle.gamma_fixed(1.0), N=4), 512 * 512)
     spatial["paper_instance_512sq_T5_3x3x5"] = {
         "ms": ms, "mpx_s": 512 * 512 / ms / 1e3, "basis_functions": 45,
-        "paper_matlab_s": 2.5, "err_vs_fp64": _err_stats(o512.cpu().numpy(), ref512)}
+        "paper_matlab_s": 2.5, "err_vs_fp64": _err_stats(o512.cpu().numpy(), ref512),
+        "oracle_forward": o512t}
     img = torch.from_numpy(f_np).to(dev)
     out = torch.empty_like(img)
     for name, M, N_, kind in [("alg2_4096sq_r10_M2_N4", 2, 4, oracle.RANGE_COSN),
@@ -385,15 +402,15 @@ def extras(dev, flush, stream):
         ms = _time_ms(call, flush, stream)
         o_np = out.cpu().numpy()
         got = np.concatenate([o_np[y] for y in rows])
-        ref_s = np.concatenate([oracle.bilateral_general(f64, R, spatial=oracle.SPATIAL_QM, M=M,
-                                                         range_kind=kind,
-                                                         gamma=oracle.gamma_fixed(1.0), N=N_,
-                                                         rows=(y, y + 1))[0] for y in rows])
+        ref_s, o_s = _oracle_timed(lambda M=M, N_=N_, kind=kind: np.concatenate([
+            oracle.bilateral_general(f64, R, spatial=oracle.SPATIAL_QM, M=M, range_kind=kind,
+                                     gamma=oracle.gamma_fixed(1.0), N=N_, rows=(y, y + 1))[0]
+            for y in rows]), len(rows) * W)
         nb = (M + 1) ** 2 * (N_ + 1)
         tf = basis_flops(nb) * H * W / (ms * 1e-3) / 1e12
         spatial[name] = {"ms": ms, "mpx_s": H * W / ms / 1e3, "basis_functions": nb,
                          "tflops_algorithmic": tf, "frac_of_fp32_peak": tf / FP32_PEAK_TFLOPS,
-                         "err_vs_fp64": _err_stats(got, ref_s)}
+                         "err_vs_fp64": _err_stats(got, ref_s), "oracle_forward": o_s}
     res["spatial_kernel"] = spatial
 
     Np = bf.bf_poly_resolve_N(0.3, 1.0)
@@ -402,13 +419,14 @@ def extras(dev, flush, stream):
     ms = _time_ms(call, flush, stream)
     o_np = out.cpu().numpy()
     got = np.concatenate([o_np[y] for y in rows])
-    ref_p = np.concatenate([oracle.bilateral_general(f64, R, range_kind=oracle.RANGE_POLY, N=Np,
-                                                     Tr=1.0, rows=(y, y + 1))[0] for y in rows])
+    ref_p, o_p = _oracle_timed(lambda: np.concatenate([
+        oracle.bilateral_general(f64, R, range_kind=oracle.RANGE_POLY, N=Np, Tr=1.0,
+                                 rows=(y, y + 1))[0] for y in rows]), len(rows) * W)
     tf = basis_flops(2 * Np + 1) * H * W / (ms * 1e-3) / 1e12
     res[f"poly_range_4096sq_r10_sigma0.3_N{Np}"] = {
         "ms": ms, "mpx_s": H * W / ms / 1e3, "basis_functions": 2 * Np + 1,
         "tflops_algorithmic": tf, "frac_of_fp32_peak": tf / FP32_PEAK_TFLOPS,
-        "err_vs_fp64": _err_stats(got, ref_p)}
+        "err_vs_fp64": _err_stats(got, ref_p), "oracle_forward": o_p}
     return res
 
 
