@@ -64,6 +64,23 @@ __global__ void __launch_bounds__(WMAX, 2) poly_kernel(Params p) {
     float D[NQ * 4];
 #pragma unroll
     for (int m = 0; m < NQ * 4; ++m) D[m] = 0.f;
+    // the five pixels of step tt (own / second column, entering / leaving row,
+    // centre), 0 where masked
+    float nv[5];
+    auto load_step = [&](int tt) {
+        const int tau = tt - j;
+        const bool act = tau >= 0 && tau < span;
+        const int e = y0 - r + tau, l = e - 2 * r - 1, rho = e - r;
+        const bool in_e = act && e >= 0 && e < p.H;
+        const bool in_l = act && tau >= 2 * r + 1 && l >= 0 && l < p.H;
+        const bool out = act && tau >= 2 * r && out_lane;
+        nv[0] = (in_e && own_in) ? __ldg(p.img + (size_t)e * W + cw) : 0.f;
+        nv[1] = (in_e && sec_in) ? __ldg(p.img + (size_t)e * W + c2) : 0.f;
+        nv[2] = (in_l && own_in) ? __ldg(p.img + (size_t)l * W + cw) : 0.f;
+        nv[3] = (in_l && sec_in) ? __ldg(p.img + (size_t)l * W + c2) : 0.f;
+        nv[4] = out ? __ldg(p.img + (size_t)rho * W + co) : 0.f;
+    };
+    load_step(w * 32);  // a warp is first active at step 32 w
     __syncthreads();
 
     for (int t = 0; t < steps; ++t) {
@@ -80,11 +97,10 @@ __global__ void __launch_bounds__(WMAX, 2) poly_kernel(Params p) {
             const bool out = act && tau >= 2 * r && out_lane;
             const bool m0 = in_e && own_in, m1 = in_e && sec_in;
             const bool m2 = in_l && own_in, m3 = in_l && sec_in;
-            const float f0 = m0 ? __ldg(p.img + (size_t)e * W + cw) : 0.f;
-            const float f1 = m1 ? __ldg(p.img + (size_t)e * W + c2) : 0.f;
-            const float f2 = m2 ? __ldg(p.img + (size_t)l * W + cw) : 0.f;
-            const float f3 = m3 ? __ldg(p.img + (size_t)l * W + c2) : 0.f;
-            const float fc = out ? __ldg(p.img + (size_t)rho * W + co) : 0.f;
+            // this step's pixels were loaded during the previous step; start
+            // the loads of the next one so their latency hides under this step
+            const float f0 = nv[0], f1 = nv[1], f2 = nv[2], f3 = nv[3], fc = nv[4];
+            load_step(t + 1);
             // + own enter, - second enter, - own leave, + second leave
             auto accumulate = [&](float f, float wgt) {
                 const float u = fmaf(f, p.invT, -0.5f);

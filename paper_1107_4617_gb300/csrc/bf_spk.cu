@@ -172,6 +172,23 @@ __global__ void __launch_bounds__(WMAX, 2) spk_kernel(Params p) {
     float2 Dg[D::ND], Dh[D::ND];
 #pragma unroll
     for (int d = 0; d < D::ND; ++d) { Dg[d] = make_float2(0.f, 0.f); Dh[d] = Dg[d]; }
+    // the five pixels of step tt (own / second column, entering / leaving row,
+    // centre), 0 where masked
+    float nv[5];
+    auto load_step = [&](int tt) {
+        const int tau = tt - j;
+        const bool act = tau >= 0 && tau < span;
+        const int e = y0 - r + tau, l = e - 2 * r - 1, rho = e - r;
+        const bool in_e = act && e >= 0 && e < p.H;
+        const bool in_l = act && tau >= 2 * r + 1 && l >= 0 && l < p.H;
+        const bool out = act && tau >= 2 * r && out_lane;
+        nv[0] = (in_e && own_in) ? __ldg(p.img + (size_t)e * W + cw) : 0.f;
+        nv[1] = (in_e && sec_in) ? __ldg(p.img + (size_t)e * W + c2) : 0.f;
+        nv[2] = (in_l && own_in) ? __ldg(p.img + (size_t)l * W + cw) : 0.f;
+        nv[3] = (in_l && sec_in) ? __ldg(p.img + (size_t)l * W + c2) : 0.f;
+        nv[4] = out ? __ldg(p.img + (size_t)rho * W + co) : 0.f;
+    };
+    load_step(w * 32);  // a warp is first active at step 32 w
     __syncthreads();
 
     for (int t = 0; t < steps; ++t, [&] {
@@ -194,11 +211,10 @@ __global__ void __launch_bounds__(WMAX, 2) spk_kernel(Params p) {
             const bool out = act && tau >= 2 * r && out_lane;
             const bool m0 = in_e && own_in, m1 = in_e && sec_in;
             const bool m2 = in_l && own_in, m3 = in_l && sec_in;
-            const float f0 = m0 ? __ldg(p.img + (size_t)e * W + cw) : 0.f;
-            const float f1 = m1 ? __ldg(p.img + (size_t)e * W + c2) : 0.f;
-            const float f2 = m2 ? __ldg(p.img + (size_t)l * W + cw) : 0.f;
-            const float f3 = m3 ? __ldg(p.img + (size_t)l * W + c2) : 0.f;
-            const float fc = out ? __ldg(p.img + (size_t)rho * W + co) : 0.f;
+            // this step's pixels were loaded during the previous step; start
+            // the loads of the next one so their latency hides under this step
+            const float f0 = nv[0], f1 = nv[1], f2 = nv[2], f3 = nv[3], fc = nv[4];
+            load_step(t + 1);
 
             // vertical: entering row's phases; the leaving row's differ by
             // e^{-i b gs (2r+1)} = (-1)^M for every b of this parity
