@@ -263,8 +263,14 @@ __device__ __forceinline__ void sys_tile(const SysParams& p, int bx, int by, siz
             // the other four streams re-read pixels the strip touched recently
             {
                 const int ef = e0 + t + PREFETCH_ROWS;
-                // (forward only: the adjoint's extra streams made it slower)
-                if (!BWD && own_in && ef >= 0 && ef < p.H) prefetch_l2(b.img + ef * W + cw);
+                if (own_in && ef >= 0 && ef < p.H) {
+                    if constexpr (!BWD) {
+                        prefetch_l2(b.img + ef * W + cw);
+                    } else {
+                        prefetch_l2(b.bsv + ef * W + cw);
+                        prefetch_l2(b.gout + ef * W + cw);
+                    }
+                }
             }
             // prefetch the next step's pixels; their latency hides under this step
             g = geometry(t + 1);
