@@ -604,6 +604,16 @@ def main():
         torch.cuda.synchronize(dev)
         t40 += e40[0].elapsed_time(e40[1]) / 1e3
     fwd40_value = px * max(3, args.steps // 2) / t40 / 1e6
+    # the plain forward at N = 41 (inference: no saved quads for an adjoint)
+    tp = 0.0
+    for _ in range(max(3, args.steps // 2)):
+        flush.zero_()
+        e40[0].record(stream)
+        bf.bf_forward(img, R, SIGMA, T_RANGE, N, out=out, opts=bf._opts(), stream=stream)
+        e40[1].record(stream)
+        torch.cuda.synchronize(dev)
+        tp += e40[0].elapsed_time(e40[1]) / 1e3
+    fwd_plain_value = px * max(3, args.steps // 2) / tp / 1e6
 
     # end to end through the C ABI from pinned host buffers
     h_img = torch.from_numpy(f_np).pin_memory()
@@ -696,6 +706,7 @@ def main():
                        "H": H, "W": W, "r": R, "N": N, "images_per_rank": 1,
                        "l2": "flushed between timed steps (256 MiB write)"},
             "fwd_mpx_s": fwd_value, "fwd_n40_mpx_s": fwd40_value,
+            "fwd_plain_n41_mpx_s": fwd_plain_value,
             "clocks": clocks,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * px * 4,
                     "d2h_bytes_per_step": 2 * px * 4},

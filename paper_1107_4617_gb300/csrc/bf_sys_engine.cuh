@@ -342,11 +342,11 @@ __device__ __forceinline__ void sys_tile(const SysParams& p, int bx, int by, siz
                         if (i + 1 < KP) advance(q, i, i + 2 < KP);
                     }
                 };
-                accumulate(c0.f, U0, V0);
-                accumulate(c1.f, U1, V1);
-                accumulate(c2v.f, U2, V2);
-                accumulate(c3.f, U3, V3);
-                Strm sc = seed(cc.f, p.gamma, p.k0);
+                accumulate(pix_f(c0), U0, V0);
+                accumulate(pix_f(c1), U1, V1);
+                accumulate(pix_f(c2v), U2, V2);
+                accumulate(pix_f(c3), U3, V3);
+                Strm sc = seed(pix_f(cc), p.gamma, p.k0);
 #pragma unroll
                 for (int i = 0; i < KP; ++i) {
                     const float4 A = rd[(2 * i) * LD];
