@@ -259,12 +259,32 @@ bf_status bf_backward_noalloc(const void* img, const float* out, const float* gr
  *   img, out  device H x W FP32 (out must not alias img).
  *   M         1..4, 6 or 8 when N = 0; 1 or 2 when 1 <= N <= 4.
  *   r         0..56.
- *   opts      NULL or defaults; gamma_mode and tile_h are honoured; BF16
- *             input, Kahan and trunc_tol give BF_ERR_UNSUPPORTED.
+ *   opts      NULL or defaults; tile_h is honoured; BF16 input, Kahan,
+ *             trunc_tol and BF_GAMMA_FROM_SIGMA give BF_ERR_UNSUPPORTED.
+ *   saved     NULL, or device buffer of bf_saved_bytes(H, W) (16-byte aligned)
+ *             receiving the quads (f, 1/den, out, dnum_s - out dden_s) for
+ *             bf_spatial_backward.
  * Errors: BF_ERR_INVALID_ARG, BF_ERR_UNSUPPORTED (other M, N, r), BF_ERR_CUDA.
  */
 bf_status bf_spatial_forward(const void* img, int H, int W, int r, int M, float sigma_r, float T,
-                             int N, float* out, const bf_opts* opts, void* stream);
+                             int N, float* out, const bf_opts* opts, void* saved, void* stream);
+
+/*
+ * Adjoint of bf_spatial_forward for L with dL/dout = grad_out: dL/dimg,
+ * derived from Eq. filter2 with the spatial kernel; the window and q_M x q_M
+ * are symmetric, so every neighbour term is again a moving sum centred on
+ * the pixel whose gradient is formed (the same fused pass on the planes
+ * alpha E_c, beta E_c, alpha = g / den, beta = -alpha out).
+ *   grad_out  device H x W FP32.
+ *   saved     the quads bf_spatial_forward wrote (device, bf_saved_bytes(H, W)).
+ *   grad_img  device H x W FP32 output.
+ * Same H, W, r, M, sigma_r, T, N, opts as the forward. The range frequency is
+ * fixed (gamma = pi / (2T)), so dL/dsigma_r is 0 and not computed.
+ * Errors: as bf_spatial_forward.
+ */
+bf_status bf_spatial_backward(const float* grad_out, const void* saved, int H, int W, int r, int M,
+                              float sigma_r, float T, int N, float* grad_img, const bf_opts* opts,
+                              void* stream);
 
 /* Order of the polynomial range kernel p_N for a target Gaussian width:
    N = ceil(T^2 / (2 sigma_r^2)), from Eq. approx1 (p_N(t / sqrt N) ->

@@ -23,7 +23,7 @@ __all__ = [
     "bf_batch_launch", "bf_backward3d_workspace_bytes",
     "bf_resolve_N", "bf_coeffs", "bf_trunc_harmonics", "bf_gamma", "bf_saved_bytes", "bf_backward_workspace_bytes",
     "bf_batch_workspace_bytes", "bf_status_string", "bf_last_cuda_error", "bilateral",
-    "bf_spatial_forward", "bf_poly_forward", "bf_poly_resolve_N", "bf_check_range",
+    "bf_spatial_forward", "bf_spatial_backward", "bilateral_spatial", "bf_poly_forward", "bf_poly_resolve_N", "bf_check_range",
     "GAMMA_FIXED", "GAMMA_FROM_SIGMA", "F32", "BF16", "N_MAX", "R_MAX",
 ]
 
@@ -102,7 +102,9 @@ def load():
             "bf_backward": (c_int, [vp, vp, vp, vp, c_int, c_int, c_int, c_float, c_float, c_int,
                                     vp, vp, vp, c_size, P_opts, vp]),
             "bf_spatial_forward": (c_int, [vp, c_int, c_int, c_int, c_int, c_float, c_float,
-                                           c_int, vp, P_opts, vp]),
+                                           c_int, vp, P_opts, vp, vp]),
+            "bf_spatial_backward": (c_int, [vp, vp, c_int, c_int, c_int, c_int, c_float, c_float,
+                                            c_int, vp, P_opts, vp]),
             "bf_poly_resolve_N": (c_int, [c_float, c_float]),
             "bf_poly_forward": (c_int, [vp, c_int, c_int, c_int, c_float, c_float, c_int, vp,
                                         P_opts, vp]),
@@ -260,7 +262,7 @@ def bf_backward(img, out, grad_out, saved, r: int, sigma_r: float, T: float = 1.
 
 
 def bf_spatial_forward(img, r: int, M: int, sigma_r: float = 0.0, T: float = 1.0, N: int = 0,
-                       out=None, opts: BfOpts | None = None, stream=None):
+                       out=None, opts: BfOpts | None = None, saved=None, stream=None):
     """Neighbourhood filter with the separable spatial kernel q_M(d1) q_M(d2)
     (q_M on [-(r+1/2), r+1/2]) and range kernel q_N (N = 0: none, i.e.
     Algorithm 1; N < 0: from sigma_r): Algorithm 2 with a shiftable spatial
@@ -274,9 +276,26 @@ def bf_spatial_forward(img, r: int, M: int, sigma_r: float = 0.0, T: float = 1.0
     st = load().bf_spatial_forward(_dptr(img, "img"), H, W, int(r), int(M), float(sigma_r),
                                    float(T), int(N), _dptr(out, "out"),
                                    ctypes.byref(opts) if opts is not None else None,
+                                   _dptr(saved, "saved") if saved is not None else None,
                                    _stream_handle(stream))
     _check("bf_spatial_forward", st)
     return out
+
+
+def bf_spatial_backward(grad_out, saved, r: int, M: int, sigma_r: float = 0.0, T: float = 1.0,
+                        N: int = 0, grad_img=None, opts: BfOpts | None = None, stream=None):
+    """Adjoint of bf_spatial_forward (saved = its quads); returns dL/dimg."""
+    import torch
+    H, W = grad_out.shape
+    if grad_img is None:
+        grad_img = torch.empty((H, W), dtype=torch.float32, device=grad_out.device)
+    st = load().bf_spatial_backward(_dptr(grad_out, "grad_out"), _dptr(saved, "saved"), H, W,
+                                    int(r), int(M), float(sigma_r), float(T), int(N),
+                                    _dptr(grad_img, "grad_img"),
+                                    ctypes.byref(opts) if opts is not None else None,
+                                    _stream_handle(stream))
+    _check("bf_spatial_backward", st)
+    return grad_img
 
 
 def bf_poly_resolve_N(sigma_r: float, T: float = 1.0) -> int:
@@ -453,6 +472,44 @@ def _make_function():
 
 
 _fn = None
+_spatial_fn = None
+
+
+def _make_spatial_function():
+    import torch
+
+    class BilateralSpatial(torch.autograd.Function):
+        """Algorithm 2 with the q_M x q_M spatial kernel and range q_N (Algorithm
+        1 for N = 0); differentiable in the image."""
+
+        @staticmethod
+        def forward(ctx, f, r, M, sigma_r, T, N):
+            f = f.contiguous()
+            H, W = f.shape
+            saved = torch.empty((H, W, 4), dtype=torch.float32, device=f.device)
+            out = bf_spatial_forward(f, r, M, sigma_r, T, N, saved=saved)
+            ctx.save_for_backward(saved)
+            ctx.cfg = (r, M, sigma_r, T, N)
+            return out
+
+        @staticmethod
+        def backward(ctx, g):
+            (saved,) = ctx.saved_tensors
+            r, M, sigma_r, T, N = ctx.cfg
+            gi = bf_spatial_backward(g.contiguous().float(), saved, r, M, sigma_r, T, N)
+            return gi, None, None, None, None, None
+
+    return BilateralSpatial
+
+
+def bilateral_spatial(f, r: int, M: int, sigma_r: float = 0.0, T: float = 1.0, N: int = 0):
+    """Neighbourhood filter with the separable spatial kernel q_M x q_M and
+    range kernel q_N (N = 0: the linear filter of Algorithm 1; N < 0: from
+    sigma_r) of a 2-D float32 CUDA tensor, differentiable in f."""
+    global _spatial_fn
+    if _spatial_fn is None:
+        _spatial_fn = _make_spatial_function()
+    return _spatial_fn.apply(f, int(r), int(M), float(sigma_r), float(T), int(N))
 
 
 def bilateral(f, r: int, sigma_r, T: float = 1.0, N: int = 0, kahan: bool = False,

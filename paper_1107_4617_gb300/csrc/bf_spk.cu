@@ -51,12 +51,20 @@ struct Dims {
 constexpr int NS_CAP = 64;
 
 struct Params {
-    const float* img;
-    float* out;
+    const float* img;      // forward input (forward modes)
+    float* out;            // forward output
+    float4* sv;            // forward with saved quads: (f, 1/den, out, dnum_s - out dden_s)
+    const float4* bsv;     // adjoint: the forward's saved quads
+    const float* gout;     // adjoint: dL/dout
+    float* gimg;           // adjoint: dL/dimg
     int H, W, r, Hb, Tw;
     float gamma;           // range kernel frequency (unused when N = 0)
     float coef[NS_CAP];    // coef_c, in combo order
+    float ck[NS_CAP];      // coef_c k_c (k_c: signed range harmonic of combo c)
 };
+
+// Launch modes: forward, forward that also saves the adjoint's quads, adjoint.
+enum Mode { FWD = 0, FWD_SAVE = 1, ADJ = 2 };
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
@@ -115,7 +123,16 @@ __device__ __forceinline__ void row_phases(const float2* tab, const int (&q)[M +
         if (-M + 2 * ib < 0) p[ib] = conj2(p[M - ib]);
 }
 
-template <int M, int N>
+// MODE = ADJ runs the same moving sums on the planes (alpha E_c, beta E_c),
+// alpha = g / den, beta = -alpha out (the window and the spatial kernel are
+// symmetric, so the adjoint's neighbour sums are again moving sums centred
+// on the pixel whose gradient is formed), and combines them into
+//   dL/df(p) = sum_c coef_c Re(conj E_c(p) A_c)
+//            + gamma [sum_c coef_c k_c Im(conj E_c(p) (f(p) A_c + B_c)) + alpha(p) X(p)],
+// A_c = Sum(alpha E_c), B_c = Sum(beta E_c), X = dnum_s - out dden_s saved by the
+// forward (dnum_s = sum_c coef_c k_c Im(conj E_c S_c(f E)), the derivative of
+// num through the centre value, divided by gamma).
+template <int M, int N, int MODE>
 __global__ void __launch_bounds__(WMAX, 2) spk_kernel(Params p) {
     using D = Dims<M, N>;
     constexpr int LD = WMAX + 1;
@@ -173,8 +190,18 @@ __global__ void __launch_bounds__(WMAX, 2) spk_kernel(Params p) {
 #pragma unroll
     for (int d = 0; d < D::ND; ++d) { Dg[d] = make_float2(0.f, 0.f); Dh[d] = Dg[d]; }
     // the five pixels of step tt (own / second column, entering / leaving row,
-    // centre), 0 where masked
-    float nv[5];
+    // centre), 0 where masked; the adjoint reads the saved quad (whose .x
+    // is f) and dL/dout instead
+    float4 nq[5];
+    float ng[5];
+    auto load_one = [&](int k, bool on, size_t q) {
+        if constexpr (MODE == ADJ) {
+            nq[k] = on ? __ldg(p.bsv + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+            ng[k] = on ? __ldg(p.gout + q) : 0.f;
+        } else {
+            nq[k].x = on ? __ldg(p.img + q) : 0.f;
+        }
+    };
     auto load_step = [&](int tt) {
         const int tau = tt - j;
         const bool act = tau >= 0 && tau < span;
@@ -182,11 +209,11 @@ __global__ void __launch_bounds__(WMAX, 2) spk_kernel(Params p) {
         const bool in_e = act && e >= 0 && e < p.H;
         const bool in_l = act && tau >= 2 * r + 1 && l >= 0 && l < p.H;
         const bool out = act && tau >= 2 * r && out_lane;
-        nv[0] = (in_e && own_in) ? __ldg(p.img + (size_t)e * W + cw) : 0.f;
-        nv[1] = (in_e && sec_in) ? __ldg(p.img + (size_t)e * W + c2) : 0.f;
-        nv[2] = (in_l && own_in) ? __ldg(p.img + (size_t)l * W + cw) : 0.f;
-        nv[3] = (in_l && sec_in) ? __ldg(p.img + (size_t)l * W + c2) : 0.f;
-        nv[4] = out ? __ldg(p.img + (size_t)rho * W + co) : 0.f;
+        load_one(0, in_e && own_in, (size_t)e * W + cw);
+        load_one(1, in_e && sec_in, (size_t)e * W + c2);
+        load_one(2, in_l && own_in, (size_t)l * W + cw);
+        load_one(3, in_l && sec_in, (size_t)l * W + c2);
+        load_one(4, out, (size_t)rho * W + co);
     };
     load_step(w * 32);  // a warp is first active at step 32 w
     __syncthreads();
@@ -213,7 +240,11 @@ __global__ void __launch_bounds__(WMAX, 2) spk_kernel(Params p) {
             const bool m2 = in_l && own_in, m3 = in_l && sec_in;
             // this step's pixels were loaded during the previous step; start
             // the loads of the next one so their latency hides under this step
-            const float f0 = nv[0], f1 = nv[1], f2 = nv[2], f3 = nv[3], fc = nv[4];
+            float4 q[5];
+            float gq[5];
+#pragma unroll
+            for (int k = 0; k < 5; ++k) { q[k] = nq[k]; gq[k] = MODE == ADJ ? ng[k] : 0.f; }
+            const float f0 = q[0].x, f1 = q[1].x, f2 = q[2].x, f3 = q[3].x, fc = q[4].x;
             load_step(t + 1);
 
             // vertical: entering row's phases; the leaving row's differ by
@@ -221,10 +252,19 @@ __global__ void __launch_bounds__(WMAX, 2) spk_kernel(Params p) {
             float2 rp[M + 1];
             row_phases<M>(ptab, qe, rp);
             const float lsg = (M & 1) ? -1.f : 1.f;
-            auto accumulate = [&](float f, float wgt, float rsg) {
+            // plane weights: (f, 1) in the forward, (alpha, beta) in the adjoint
+            auto accumulate = [&](int k, float wgt, float rsg) {
                 float2 z[N + 1];
-                range_harmonics<N>(f, p.gamma, z);
-                const float wf = wgt * f;
+                range_harmonics<N>(q[k].x, p.gamma, z);
+                float ug, uh;
+                if constexpr (MODE == ADJ) {
+                    const float al = gq[k] * q[k].y;
+                    ug = wgt * al;
+                    uh = -wgt * al * q[k].z;
+                } else {
+                    ug = wgt * q[k].x;
+                    uh = wgt;
+                }
 #pragma unroll
                 for (int ib = 0; ib <= M; ++ib) {
                     const float2 rb = make_float2(rsg * rp[ib].x, rsg * rp[ib].y);
@@ -232,18 +272,19 @@ __global__ void __launch_bounds__(WMAX, 2) spk_kernel(Params p) {
                     for (int ik = 0; ik <= N; ++ik) {
                         const float2 E = cmul(rb, z[ik]);
                         const int d = ib * (N + 1) + ik;
-                        Dg[d].x = fmaf(wf, E.x, Dg[d].x);
-                        Dg[d].y = fmaf(wf, E.y, Dg[d].y);
-                        Dh[d].x = fmaf(wgt, E.x, Dh[d].x);
-                        Dh[d].y = fmaf(wgt, E.y, Dh[d].y);
+                        Dg[d].x = fmaf(ug, E.x, Dg[d].x);
+                        Dg[d].y = fmaf(ug, E.y, Dg[d].y);
+                        Dh[d].x = fmaf(uh, E.x, Dh[d].x);
+                        Dh[d].y = fmaf(uh, E.y, Dh[d].y);
                     }
                 }
             };
             // + own enter, -(-1)^M second enter, - own leave, +(-1)^M second leave
-            accumulate(f0, m0 ? 1.f : 0.f, 1.f);
-            accumulate(f1, m1 ? sgn2 : 0.f, 1.f);
-            accumulate(f2, m2 ? -1.f : 0.f, lsg);
-            accumulate(f3, m3 ? -sgn2 : 0.f, lsg);
+            accumulate(0, m0 ? 1.f : 0.f, 1.f);
+            accumulate(1, m1 ? sgn2 : 0.f, 1.f);
+            accumulate(2, m2 ? -1.f : 0.f, lsg);
+            accumulate(3, m3 ? -sgn2 : 0.f, lsg);
+            (void)f0; (void)f1; (void)f2; (void)f3;
 
             // horizontal and recombination with the centre's conj(E_c)
             float2 rpc[M + 1];
@@ -260,7 +301,7 @@ __global__ void __launch_bounds__(WMAX, 2) spk_kernel(Params p) {
             range_harmonics<N>(fc, p.gamma, zc);
             const float4* rd = smem + ((t + 1) & 1) * BUF + j;
             float4* wr = smem + (t & 1) * BUF + j + 1;
-            float num = 0.f, den = 0.f;
+            float num = 0.f, den = 0.f, dn = 0.f, dd = 0.f;
             int c = 0;
 #pragma unroll
             for (int ia = 0; ia < D::NA; ++ia) {
@@ -276,23 +317,47 @@ __global__ void __launch_bounds__(WMAX, 2) spk_kernel(Params p) {
                     const float2 hh = make_float2(A.z + sh.x, A.w + sh.y);
                     wr[c * LD] = make_float4(hg.x, hg.y, hh.x, hh.y);
                     const float2 E = cmul(cmul(cphc[ia], rpc[ib]), zc[ik]);
-                    // Re(conj(E) h) = E.x h.x + E.y h.y
-                    num = fmaf(p.coef[c], fmaf(E.x, hg.x, E.y * hg.y), num);
-                    den = fmaf(p.coef[c], fmaf(E.x, hh.x, E.y * hh.y), den);
+                    // Re(conj(E) h) = E.x h.x + E.y h.y, Im(conj(E) h) = E.x h.y - E.y h.x
+                    if constexpr (MODE != ADJ) {
+                        num = fmaf(p.coef[c], fmaf(E.x, hg.x, E.y * hg.y), num);
+                        den = fmaf(p.coef[c], fmaf(E.x, hh.x, E.y * hh.y), den);
+                        if constexpr (MODE == FWD_SAVE) {
+                            dn = fmaf(p.ck[c], fmaf(E.x, hg.y, -E.y * hg.x), dn);
+                            dd = fmaf(p.ck[c], fmaf(E.x, hh.y, -E.y * hh.x), dd);
+                        }
+                    } else {
+                        // hg = A_c = Sum(alpha E_c), hh = B_c = Sum(beta E_c)
+                        num = fmaf(p.coef[c], fmaf(E.x, hg.x, E.y * hg.y), num);
+                        const float vx = fmaf(fc, hg.x, hh.x), vy = fmaf(fc, hg.y, hh.y);
+                        den = fmaf(p.ck[c], fmaf(E.x, vy, -E.y * vx), den);
+                    }
                     ++c;
                 }
             }
-            if (out) p.out[(size_t)rho * W + co] = num / den;
+            if (out) {
+                const size_t o = (size_t)rho * W + co;
+                if constexpr (MODE == ADJ) {
+                    // centre quad: (f, 1/den, out, X)
+                    const float al = gq[4] * q[4].y;
+                    p.gimg[o] = fmaf(p.gamma, fmaf(al, q[4].w, den), num);
+                } else {
+                    const float ov = num / den;
+                    p.out[o] = ov;
+                    if constexpr (MODE == FWD_SAVE)
+                        p.sv[o] = make_float4(fc, 1.0f / den, ov, fmaf(-ov, dd, dn));
+                }
+            }
         }
         __syncthreads();
     }
 }
 
 template <int M, int N>
-static cudaError_t launch(const Params& p, int gx, int gy, cudaStream_t s) {
+static cudaError_t launch(const Params& p, int mode, int gx, int gy, cudaStream_t s) {
     using D = Dims<M, N>;
     static_assert(D::NS <= NS_CAP, "combo table");
-    auto kern = spk_kernel<M, N>;
+    auto kern = mode == ADJ ? spk_kernel<M, N, ADJ>
+                            : (mode == FWD_SAVE ? spk_kernel<M, N, FWD_SAVE> : spk_kernel<M, N, FWD>);
     const size_t smem = sizeof(float4) * 2 * (size_t)D::NS * (WMAX + 1) +
                         sizeof(float2) * PTAB_CAP;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -305,8 +370,9 @@ static cudaError_t launch(const Params& p, int gx, int gy, cudaStream_t s) {
 // Combo order and coefficients, as the kernel enumerates them:
 // coef_c = 1/4 beta_a beta_|b| alpha_|k| m_b m_k (m = 2 for b = 0, k = 0:
 // both sign choices give the same term), doubled for a = 0 except the
-// self-conjugate (0, 0, 0).
-static int combo_coefs(int M, int N, const double* beta, const double* alpha, float* coef) {
+// self-conjugate (0, 0, 0); ck_c = coef_c k_c with the combo's signed k.
+static int combo_coefs(int M, int N, const double* beta, const double* alpha, float* coef,
+                       float* ck) {
     const int NB = M + 1, NK = N + 1, ND = NB * NK, D0 = ND - (ND + 1) / 2;
     int c = 0;
     for (int ia = 0; ia <= M / 2; ++ia) {
@@ -321,7 +387,9 @@ static int combo_coefs(int M, int N, const double* beta, const double* alpha, fl
             if (k == 0) v *= 2.0;
             if (a == 0 && !(b == 0 && k == 0)) v *= 2.0;
             if (c >= NS_CAP) return -1;
-            coef[c++] = (float)v;
+            coef[c] = (float)v;
+            ck[c] = (float)(v * (double)k);
+            ++c;
         }
     }
     return c;
@@ -333,19 +401,79 @@ static bool supported(int M, int N) {
 }
 
 template <int M>
-static cudaError_t dispatch_n(const Params& p, int N, int gx, int gy, cudaStream_t s) {
+static cudaError_t dispatch_n(const Params& p, int mode, int N, int gx, int gy, cudaStream_t s) {
     if constexpr (M == 1 || M == 2) {
         switch (N) {
-            case 0: return launch<M, 0>(p, gx, gy, s);
-            case 1: return launch<M, 1>(p, gx, gy, s);
-            case 2: return launch<M, 2>(p, gx, gy, s);
-            case 3: return launch<M, 3>(p, gx, gy, s);
-            case 4: return launch<M, 4>(p, gx, gy, s);
+            case 0: return launch<M, 0>(p, mode, gx, gy, s);
+            case 1: return launch<M, 1>(p, mode, gx, gy, s);
+            case 2: return launch<M, 2>(p, mode, gx, gy, s);
+            case 3: return launch<M, 3>(p, mode, gx, gy, s);
+            case 4: return launch<M, 4>(p, mode, gx, gy, s);
         }
         return cudaErrorInvalidValue;
     } else {
-        return N == 0 ? launch<M, 0>(p, gx, gy, s) : cudaErrorInvalidValue;
+        return N == 0 ? launch<M, 0>(p, mode, gx, gy, s) : cudaErrorInvalidValue;
     }
+}
+
+// Checks shared by the forward and the adjoint; fills the launch parameters
+// (coefficients, gamma, tiles) and resolves N.
+static bf_status prepare(int H, int W, int r, int M, float sigma_r, float T, int* N,
+                         const bf_opts* opts, Params* p, int* gx, int* gy) {
+    if (H < 1 || W < 1 || r < 0 || M < 1) return BF_ERR_INVALID_ARG;
+    if (!(T > 0.f) || !isfinite(T)) return BF_ERR_INVALID_ARG;
+    bf_status st = check_opts(opts);
+    if (st != BF_OK) return st;
+    if (opts && (opts->in_dtype != BF_F32 || opts->kahan || opts->trunc_tol > 0.f ||
+                 opts->gamma_mode != BF_GAMMA_FIXED))
+        return BF_ERR_UNSUPPORTED;
+    if (*N < 0) {
+        *N = bf_resolve_N(sigma_r, T);
+        if (*N < 0) return BF_ERR_INVALID_ARG;
+    }
+    if (!supported(M, *N)) return BF_ERR_UNSUPPORTED;
+    if (2 * r + 16 > WMAX) return BF_ERR_UNSUPPORTED;
+    double gamma = 0.0;
+    if (*N > 0) {
+        gamma = bf_gamma(sigma_r, T, *N, BF_GAMMA_FIXED);
+        if (!(gamma > 0.0)) return BF_ERR_INVALID_ARG;
+    }
+    double beta[BF_N_MAX / 2 + 1], alpha[BF_N_MAX / 2 + 1];
+    if (bf_coeffs(M, beta, BF_N_MAX / 2 + 1) < 0 || bf_coeffs(*N, alpha, BF_N_MAX / 2 + 1) < 0)
+        return BF_ERR_INTERNAL;
+    memset(p, 0, sizeof(*p));
+    if (combo_coefs(M, *N, beta, alpha, p->coef, p->ck) < 0) return BF_ERR_INTERNAL;
+    p->H = H; p->W = W; p->r = r;
+    p->gamma = (float)gamma;
+    p->Tw = WMAX - 2 * r;
+    *gx = (W + p->Tw - 1) / p->Tw;
+    int hb;
+    if (opts && opts->tile_h > 0) {
+        hb = opts->tile_h;
+    } else {
+        // one wave of resident CTAs: at most 2 per SM (rounding the band count
+        // up would start a second, nearly empty wave)
+        int nb = 2 * sm_count() / *gx;
+        if (nb < 1) nb = 1;
+        hb = (H + nb - 1) / nb;
+        if (hb < 32) hb = 32;
+    }
+    p->Hb = hb;
+    *gy = (H + hb - 1) / hb;
+    return BF_OK;
+}
+
+static cudaError_t dispatch(const Params& p, int mode, int M, int N, int gx, int gy,
+                            cudaStream_t s) {
+    switch (M) {
+        case 1: return dispatch_n<1>(p, mode, N, gx, gy, s);
+        case 2: return dispatch_n<2>(p, mode, N, gx, gy, s);
+        case 3: return dispatch_n<3>(p, mode, N, gx, gy, s);
+        case 4: return dispatch_n<4>(p, mode, N, gx, gy, s);
+        case 6: return dispatch_n<6>(p, mode, N, gx, gy, s);
+        case 8: return dispatch_n<8>(p, mode, N, gx, gy, s);
+    }
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace spk
@@ -355,69 +483,44 @@ using namespace bf;
 
 extern "C" bf_status bf_spatial_forward(const void* img, int H, int W, int r, int M,
                                         float sigma_r, float T, int N, float* out,
-                                        const bf_opts* opts, void* stream) {
-    if (!img || !out || H < 1 || W < 1 || r < 0 || M < 1) return BF_ERR_INVALID_ARG;
+                                        const bf_opts* opts, void* saved, void* stream) {
+    if (!img || !out) return BF_ERR_INVALID_ARG;
     if ((const void*)out == img) return BF_ERR_INVALID_ARG;
-    if (!(T > 0.f) || !isfinite(T)) return BF_ERR_INVALID_ARG;
-    bf_status st = check_opts(opts);
-    if (st != BF_OK) return st;
-    if (opts && (opts->in_dtype != BF_F32 || opts->kahan || opts->trunc_tol > 0.f))
-        return BF_ERR_UNSUPPORTED;
-    if (N < 0) {
-        N = bf_resolve_N(sigma_r, T);
-        if (N < 0) return BF_ERR_INVALID_ARG;
-    }
-    if (!spk::supported(M, N)) return BF_ERR_UNSUPPORTED;
-    if (2 * r + 16 > spk::WMAX) return BF_ERR_UNSUPPORTED;
-    if (r == 0) {
-        // a 1 x 1 window: every kernel weighs the centre alone, out = f
-        cudaError_t e = cudaMemcpyAsync(out, img, sizeof(float) * (size_t)H * W,
-                                        cudaMemcpyDeviceToDevice, (cudaStream_t)stream);
-        return e == cudaSuccess ? BF_OK : set_cuda_error(e);
-    }
-    const int gm = opts ? opts->gamma_mode : BF_GAMMA_FIXED;
-    double gamma = 0.0;
-    if (N > 0) {
-        gamma = bf_gamma(sigma_r, T, N, gm);
-        if (!(gamma > 0.0)) return BF_ERR_INVALID_ARG;
-    }
-    double beta[BF_N_MAX / 2 + 1], alpha[BF_N_MAX / 2 + 1];
-    if (bf_coeffs(M, beta, BF_N_MAX / 2 + 1) < 0 || bf_coeffs(N, alpha, BF_N_MAX / 2 + 1) < 0)
-        return BF_ERR_INTERNAL;
+    if (saved && ((uintptr_t)saved & 15)) return BF_ERR_INVALID_ARG;
+    if (opts && opts->save_for_backward && !saved) return BF_ERR_INVALID_ARG;
     spk::Params p;
-    memset(&p, 0, sizeof(p));
-    if (spk::combo_coefs(M, N, beta, alpha, p.coef) < 0) return BF_ERR_INTERNAL;
+    int gx = 0, gy = 0;
+    bf_status st = spk::prepare(H, W, r, M, sigma_r, T, &N, opts, &p, &gx, &gy);
+    if (st != BF_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
     p.img = static_cast<const float*>(img);
     p.out = out;
-    p.H = H; p.W = W; p.r = r;
-    p.gamma = (float)gamma;
-    p.Tw = spk::WMAX - 2 * r;
-    const int gx = (W + p.Tw - 1) / p.Tw;
-    int hb;
-    if (opts && opts->tile_h > 0) {
-        hb = opts->tile_h;
-    } else {
-        // one wave of resident CTAs: at most 2 per SM (rounding the band count
-        // up would start a second, nearly empty wave)
-        const int target = 2 * sm_count();
-        int nb = target / gx;
-        if (nb < 1) nb = 1;
-        hb = (H + nb - 1) / nb;
-        if (hb < 32) hb = 32;
+    p.sv = static_cast<float4*>(saved);
+    const int mode = saved ? spk::FWD_SAVE : spk::FWD;
+    if (r == 0 && !saved) {
+        // a 1 x 1 window: every kernel weighs the centre alone, out = f
+        cudaError_t e = cudaMemcpyAsync(out, img, sizeof(float) * (size_t)H * W,
+                                        cudaMemcpyDeviceToDevice, s);
+        return e == cudaSuccess ? BF_OK : set_cuda_error(e);
     }
-    p.Hb = hb;
-    const int gy = (H + hb - 1) / hb;
-    cudaError_t e;
-    cudaStream_t s = (cudaStream_t)stream;
-    switch (M) {
-        case 1: e = spk::dispatch_n<1>(p, N, gx, gy, s); break;
-        case 2: e = spk::dispatch_n<2>(p, N, gx, gy, s); break;
-        case 3: e = spk::dispatch_n<3>(p, N, gx, gy, s); break;
-        case 4: e = spk::dispatch_n<4>(p, N, gx, gy, s); break;
-        case 6: e = spk::dispatch_n<6>(p, N, gx, gy, s); break;
-        case 8: e = spk::dispatch_n<8>(p, N, gx, gy, s); break;
-        default: return BF_ERR_UNSUPPORTED;
-    }
+    cudaError_t e = spk::dispatch(p, mode, M, N, gx, gy, s);
+    if (e != cudaSuccess) return set_cuda_error(e);
+    return BF_OK;
+}
+
+extern "C" bf_status bf_spatial_backward(const float* grad_out, const void* saved, int H, int W,
+                                         int r, int M, float sigma_r, float T, int N,
+                                         float* grad_img, const bf_opts* opts, void* stream) {
+    if (!grad_out || !saved || !grad_img) return BF_ERR_INVALID_ARG;
+    if ((uintptr_t)saved & 15) return BF_ERR_INVALID_ARG;
+    spk::Params p;
+    int gx = 0, gy = 0;
+    bf_status st = spk::prepare(H, W, r, M, sigma_r, T, &N, opts, &p, &gx, &gy);
+    if (st != BF_OK) return st;
+    p.bsv = static_cast<const float4*>(saved);
+    p.gout = grad_out;
+    p.gimg = grad_img;
+    cudaError_t e = spk::dispatch(p, spk::ADJ, M, N, gx, gy, (cudaStream_t)stream);
     if (e != cudaSuccess) return set_cuda_error(e);
     return BF_OK;
 }

@@ -78,3 +78,58 @@ def test_rejects_unbuilt_orders(cuda_lib):
             bf.bf_spatial_forward(f, 2, M, 0.0, 1.0, N)
     with pytest.raises(bf.BfError):
         bf.bf_spatial_forward(f, 57, 2, 0.0, 1.0, 4)
+
+
+def fd_grad(f, w, r, M, N, y, x, h=1e-4):
+    """Central difference of L = sum(w * out) in f[y, x] on the FP64 oracle,
+    re-evaluating only the outputs within r of (y, x) (on a crop holding their
+    windows)."""
+    H, W = f.shape
+    y0, y1 = max(0, y - 2 * r), min(H, y + 2 * r + 1)
+    x0, x1 = max(0, x - 2 * r), min(W, x + 2 * r + 1)
+    sub = f[y0:y1, x0:x1].astype(np.float64)
+    mask = np.zeros_like(sub)
+    mask[max(0, y - r) - y0:min(H, y + r + 1) - y0, max(0, x - r) - x0:min(W, x + r + 1) - x0] = 1
+    wsub = w[y0:y1, x0:x1].astype(np.float64) * mask
+    sp = sub.copy(); sp[y - y0, x - x0] += h
+    sm = sub.copy(); sm[y - y0, x - x0] -= h
+    return (np.sum(wsub * ref(sp, r, M, N)) - np.sum(wsub * ref(sm, r, M, N))) / (2 * h)
+
+
+@pytest.mark.parametrize("H,W,r,M,N", [(64, 90, 3, 2, 4), (80, 70, 5, 1, 3), (50, 140, 4, 2, 0),
+                                       (33, 41, 2, 4, 0), (96, 200, 5, 2, 2)])
+def test_spatial_adjoint_vs_central_differences(cuda_lib, H, W, r, M, N):
+    """dL/df of Algorithm 2 with the spatial kernel (and of Algorithm 1 for
+    N = 0), through the autograd wrapper, against FP64 central differences
+    of the oracle at sampled pixels: |gpu - fd| <= 1e-3 max(1, |fd|)."""
+    bf = cuda_lib
+    f = synth.rectangles(H, W, seed=H + M + N)
+    w = synth.weights((H, W), seed=1)
+    ft = torch.from_numpy(f).cuda().requires_grad_(True)
+    out = bf.bilateral_spatial(ft, r, M, 0.0, 1.0, N)
+    assert rel_err(out.detach().cpu().numpy(), ref(f, r, M, N)).max() <= TOL
+    (torch.from_numpy(w).cuda() * out).sum().backward()
+    gg = ft.grad.cpu().numpy()
+    rng = np.random.default_rng(H * W + r)
+    pts = [(0, 0), (H - 1, W - 1)] + [(int(rng.integers(0, H)), int(rng.integers(0, W)))
+                                      for _ in range(8)]
+    for y, x in pts:
+        fd = fd_grad(f, w, r, M, N, y, x)
+        assert abs(gg[y, x] - fd) <= 1e-3 * max(1.0, abs(fd)), (y, x, gg[y, x], fd)
+
+
+def test_spatial_saved_quads(cuda_lib):
+    """The forward's saved quads: f and out exactly as read and written, 1/den
+    equal to the oracle's normaliser's reciprocal."""
+    bf = cuda_lib
+    f = synth.rectangles(70, 90, seed=4)
+    sv = torch.empty((70, 90, 4), device="cuda")
+    out = bf.bf_spatial_forward(torch.from_numpy(f).cuda(), 3, 2, 0.0, 1.0, 4, saved=sv)
+    q = sv.cpu().numpy()
+    got = out.cpu().numpy()
+    r_, den = oracle.bilateral_general(f.astype(np.float64), 3, spatial=oracle.SPATIAL_QM, M=2,
+                                       range_kind=oracle.RANGE_COSN, gamma=G1, N=4,
+                                       return_den=True)
+    np.testing.assert_array_equal(q[..., 0], f)
+    np.testing.assert_array_equal(q[..., 2], got)
+    np.testing.assert_allclose(1.0 / q[..., 1], den, rtol=2e-5, atol=0)
