@@ -303,11 +303,27 @@ int bf_poly_resolve_N(float sigma_r, float T);
  *   r         0..56.
  *   opts      NULL or defaults (tile_h honoured); BF16 input, Kahan,
  *             trunc_tol or BF_GAMMA_FROM_SIGMA give BF_ERR_UNSUPPORTED.
+ *   saved     NULL, or device buffer of bf_saved_bytes(H, W) (16-byte aligned)
+ *             receiving the quads (f, 1/den, out, dnum_s - out dden_s) for
+ *             bf_poly_backward.
  * Errors: BF_ERR_INVALID_ARG, BF_ERR_UNSUPPORTED (N > 8, r > 56),
  * BF_ERR_CUDA.
  */
 bf_status bf_poly_forward(const void* img, int H, int W, int r, float sigma_r, float T, int N,
-                          float* out, const bf_opts* opts, void* stream);
+                          float* out, const bf_opts* opts, void* saved, void* stream);
+
+/*
+ * Adjoint of bf_poly_forward for L with dL/dout = grad_out: dL/dimg (derived
+ * from Eq. filter2; the window and p_N are symmetric, so the neighbour terms
+ * are moving sums of alpha u^m and beta u^m, alpha = g / den, beta = -alpha out).
+ *   grad_out  device H x W FP32.
+ *   saved     the quads bf_poly_forward wrote (device, bf_saved_bytes(H, W)).
+ *   grad_img  device H x W FP32 output.
+ * Same H, W, r, sigma_r, T, N, opts as the forward. Errors: as bf_poly_forward.
+ */
+bf_status bf_poly_backward(const float* grad_out, const void* saved, int H, int W, int r,
+                           float sigma_r, float T, int N, float* grad_img, const bf_opts* opts,
+                           void* stream);
 
 /* Workspace bytes bf_batch needs for n descriptors (device tile table). */
 size_t bf_batch_workspace_bytes(const bf_desc* descs, int n, const bf_opts* opts);

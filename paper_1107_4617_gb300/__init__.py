@@ -23,7 +23,7 @@ __all__ = [
     "bf_batch_launch", "bf_backward3d_workspace_bytes",
     "bf_resolve_N", "bf_coeffs", "bf_trunc_harmonics", "bf_gamma", "bf_saved_bytes", "bf_backward_workspace_bytes",
     "bf_batch_workspace_bytes", "bf_status_string", "bf_last_cuda_error", "bilateral",
-    "bf_spatial_forward", "bf_spatial_backward", "bilateral_spatial", "bf_poly_forward", "bf_poly_resolve_N", "bf_check_range",
+    "bf_spatial_forward", "bf_spatial_backward", "bilateral_spatial", "bf_poly_forward", "bf_poly_backward", "bilateral_poly", "bf_poly_resolve_N", "bf_check_range",
     "GAMMA_FIXED", "GAMMA_FROM_SIGMA", "F32", "BF16", "N_MAX", "R_MAX",
 ]
 
@@ -107,7 +107,9 @@ def load():
                                             c_int, vp, P_opts, vp]),
             "bf_poly_resolve_N": (c_int, [c_float, c_float]),
             "bf_poly_forward": (c_int, [vp, c_int, c_int, c_int, c_float, c_float, c_int, vp,
-                                        P_opts, vp]),
+                                        P_opts, vp, vp]),
+            "bf_poly_backward": (c_int, [vp, vp, c_int, c_int, c_int, c_float, c_float, c_int,
+                                         vp, P_opts, vp]),
             "bf_check_range": (c_int, [vp, c_int, c_int, c_int, vp, vp]),
             "bf_batch_workspace_bytes": (c_size, [P_desc, c_int, P_opts]),
             "bf_batch": (c_int, [P_desc, c_int, P_opts, vp, c_size, vp]),
@@ -303,7 +305,7 @@ def bf_poly_resolve_N(sigma_r: float, T: float = 1.0) -> int:
 
 
 def bf_poly_forward(img, r: int, sigma_r: float = 0.0, T: float = 1.0, N: int = 0, out=None,
-                    opts: BfOpts | None = None, stream=None):
+                    opts: BfOpts | None = None, saved=None, stream=None):
     """Bilateral filter with the polynomial range kernel p_N(t) = (1 -
     t^2/T^2)^N (Sec. 3) and the box window. 2-D float32 CUDA tensor."""
     import torch
@@ -315,9 +317,26 @@ def bf_poly_forward(img, r: int, sigma_r: float = 0.0, T: float = 1.0, N: int = 
     st = load().bf_poly_forward(_dptr(img, "img"), H, W, int(r), float(sigma_r), float(T),
                                 int(N), _dptr(out, "out"),
                                 ctypes.byref(opts) if opts is not None else None,
+                                _dptr(saved, "saved") if saved is not None else None,
                                 _stream_handle(stream))
     _check("bf_poly_forward", st)
     return out
+
+
+def bf_poly_backward(grad_out, saved, r: int, sigma_r: float = 0.0, T: float = 1.0, N: int = 0,
+                     grad_img=None, opts: BfOpts | None = None, stream=None):
+    """Adjoint of bf_poly_forward (saved = its quads); returns dL/dimg."""
+    import torch
+    H, W = grad_out.shape
+    if grad_img is None:
+        grad_img = torch.empty((H, W), dtype=torch.float32, device=grad_out.device)
+    st = load().bf_poly_backward(_dptr(grad_out, "grad_out"), _dptr(saved, "saved"), H, W,
+                                 int(r), float(sigma_r), float(T), int(N),
+                                 _dptr(grad_img, "grad_img"),
+                                 ctypes.byref(opts) if opts is not None else None,
+                                 _stream_handle(stream))
+    _check("bf_poly_backward", st)
+    return grad_img
 
 
 def bf_check_range(img, stream=None):
@@ -500,6 +519,46 @@ def _make_spatial_function():
             return gi, None, None, None, None, None
 
     return BilateralSpatial
+
+
+_poly_fn = None
+
+
+def _make_poly_function():
+    import torch
+
+    class BilateralPoly(torch.autograd.Function):
+        """Bilateral filter with the polynomial range kernel p_N; differentiable
+        in the image."""
+
+        @staticmethod
+        def forward(ctx, f, r, sigma_r, T, N):
+            f = f.contiguous()
+            H, W = f.shape
+            saved = torch.empty((H, W, 4), dtype=torch.float32, device=f.device)
+            out = bf_poly_forward(f, r, sigma_r, T, N, saved=saved)
+            ctx.save_for_backward(saved)
+            ctx.cfg = (r, sigma_r, T, N)
+            return out
+
+        @staticmethod
+        def backward(ctx, g):
+            (saved,) = ctx.saved_tensors
+            r, sigma_r, T, N = ctx.cfg
+            return (bf_poly_backward(g.contiguous().float(), saved, r, sigma_r, T, N),
+                    None, None, None, None)
+
+    return BilateralPoly
+
+
+def bilateral_poly(f, r: int, sigma_r: float = 0.0, T: float = 1.0, N: int = 0):
+    """Bilateral filter with range kernel p_N(t) = (1 - t^2/T^2)^N (N <= 0:
+    from sigma_r) and the box window, of a 2-D float32 CUDA tensor,
+    differentiable in f."""
+    global _poly_fn
+    if _poly_fn is None:
+        _poly_fn = _make_poly_function()
+    return _poly_fn.apply(f, int(r), float(sigma_r), float(T), int(N))
 
 
 def bilateral_spatial(f, r: int, M: int, sigma_r: float = 0.0, T: float = 1.0, N: int = 0):

@@ -28,17 +28,36 @@ constexpr int NMAX = 8;
 constexpr int PCAP = 2 * NMAX + 1;  // psi_m, m = 0..2N
 
 struct Params {
-    const float* img;
-    float* out;
+    const float* img;      // forward input
+    float* out;            // forward output
+    float4* sv;            // forward with saved quads: (f, 1/den, out, dnum_s - out dden_s)
+    const float4* bsv;     // adjoint: the forward's saved quads
+    const float* gout;     // adjoint: dL/dout
+    float* gimg;           // adjoint: dL/dimg
     int H, W, r, Hb, Tw;
     float invT, T;
-    // psi_m(v) = sum_n c[m][n] v^n, m, n = 0..2N
+    // psi_m(v) = sum_n c[m][n] v^n, m, n = 0..2N; dc[m][n] = (n + 1) c[m][n + 1]
+    // (psi_m'(v) = sum_n dc[m][n] v^n)
     float c[PCAP][PCAP];
+    float dc[PCAP][PCAP];
 };
 
-template <int N>
+// Launch modes: forward, forward that also saves the adjoint's quads, adjoint.
+enum Mode { FWD = 0, FWD_SAVE = 1, ADJ = 2 };
+
+// The adjoint (MODE = ADJ) moving-sums alpha u^m and beta u^m (alpha = g / den,
+// beta = -alpha out; the window and p_N are symmetric) and forms
+//   dL/df(p) = sum_m psi_m(u_p) A_m + (1/T) sum_m psi_m'(u_p) (f(p) A_m + B_m)
+//            + alpha(p) X(p),
+// A_m = Sum(alpha u^m), B_m = Sum(beta u^m), X = dnum_s - out dden_s saved by
+// the forward (dnum_s = sum_m psi_m'(u_p) (Sum(u^{m+1}) + Sum(u^m) / 2),
+// dden_s = (1/T) sum_m psi_m'(u_p) Sum(u^m): num and den differentiated
+// through the centre value).
+template <int N, int MODE>
 __global__ void __launch_bounds__(WMAX, 2) poly_kernel(Params p) {
-    constexpr int NP = 2 * N + 2;        // power planes u^0 .. u^{2N+1}
+    // forward: power planes u^0 .. u^{2N+1}; adjoint: alpha u^m and beta u^m, m <= 2N
+    constexpr int NP = MODE == ADJ ? 2 * (2 * N + 1) : 2 * N + 2;
+    constexpr int NA = 2 * N + 1;        // adjoint: first beta plane
     constexpr int NQ = (NP + 3) / 4;     // float4 slots per lane
     constexpr int LD = WMAX + 1;
     constexpr int BUF = NQ * LD;
@@ -65,8 +84,18 @@ __global__ void __launch_bounds__(WMAX, 2) poly_kernel(Params p) {
 #pragma unroll
     for (int m = 0; m < NQ * 4; ++m) D[m] = 0.f;
     // the five pixels of step tt (own / second column, entering / leaving row,
-    // centre), 0 where masked
-    float nv[5];
+    // centre), 0 where masked; the adjoint reads the saved quad (whose .x is f)
+    // and dL/dout instead
+    float4 nq[5];
+    float ng[5];
+    auto load_one = [&](int k, bool on, size_t q) {
+        if constexpr (MODE == ADJ) {
+            nq[k] = on ? __ldg(p.bsv + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+            ng[k] = on ? __ldg(p.gout + q) : 0.f;
+        } else {
+            nq[k].x = on ? __ldg(p.img + q) : 0.f;
+        }
+    };
     auto load_step = [&](int tt) {
         const int tau = tt - j;
         const bool act = tau >= 0 && tau < span;
@@ -74,11 +103,11 @@ __global__ void __launch_bounds__(WMAX, 2) poly_kernel(Params p) {
         const bool in_e = act && e >= 0 && e < p.H;
         const bool in_l = act && tau >= 2 * r + 1 && l >= 0 && l < p.H;
         const bool out = act && tau >= 2 * r && out_lane;
-        nv[0] = (in_e && own_in) ? __ldg(p.img + (size_t)e * W + cw) : 0.f;
-        nv[1] = (in_e && sec_in) ? __ldg(p.img + (size_t)e * W + c2) : 0.f;
-        nv[2] = (in_l && own_in) ? __ldg(p.img + (size_t)l * W + cw) : 0.f;
-        nv[3] = (in_l && sec_in) ? __ldg(p.img + (size_t)l * W + c2) : 0.f;
-        nv[4] = out ? __ldg(p.img + (size_t)rho * W + co) : 0.f;
+        load_one(0, in_e && own_in, (size_t)e * W + cw);
+        load_one(1, in_e && sec_in, (size_t)e * W + c2);
+        load_one(2, in_l && own_in, (size_t)l * W + cw);
+        load_one(3, in_l && sec_in, (size_t)l * W + c2);
+        load_one(4, out, (size_t)rho * W + co);
     };
     load_step(w * 32);  // a warp is first active at step 32 w
     __syncthreads();
@@ -99,22 +128,38 @@ __global__ void __launch_bounds__(WMAX, 2) poly_kernel(Params p) {
             const bool m2 = in_l && own_in, m3 = in_l && sec_in;
             // this step's pixels were loaded during the previous step; start
             // the loads of the next one so their latency hides under this step
-            const float f0 = nv[0], f1 = nv[1], f2 = nv[2], f3 = nv[3], fc = nv[4];
+            float4 q[5];
+            float gq[5];
+#pragma unroll
+            for (int k = 0; k < 5; ++k) { q[k] = nq[k]; gq[k] = MODE == ADJ ? ng[k] : 0.f; }
+            const float fc = q[4].x;
             load_step(t + 1);
             // + own enter, - second enter, - own leave, + second leave
-            auto accumulate = [&](float f, float wgt) {
-                const float u = fmaf(f, p.invT, -0.5f);
-                float pw = wgt;
+            auto accumulate = [&](int k, float wgt) {
+                const float u = fmaf(q[k].x, p.invT, -0.5f);
+                if constexpr (MODE == ADJ) {
+                    const float al = gq[k] * q[k].y;
+                    float pa = wgt * al, pb = -wgt * al * q[k].z;
 #pragma unroll
-                for (int m = 0; m < NP; ++m) {
-                    D[m] += pw;
-                    pw *= u;
+                    for (int m = 0; m < NA; ++m) {
+                        D[m] += pa;
+                        D[NA + m] += pb;
+                        pa *= u;
+                        pb *= u;
+                    }
+                } else {
+                    float pw = wgt;
+#pragma unroll
+                    for (int m = 0; m < NP; ++m) {
+                        D[m] += pw;
+                        pw *= u;
+                    }
                 }
             };
-            accumulate(f0, m0 ? 1.f : 0.f);
-            accumulate(f1, m1 ? -1.f : 0.f);
-            accumulate(f2, m2 ? -1.f : 0.f);
-            accumulate(f3, m3 ? 1.f : 0.f);
+            accumulate(0, m0 ? 1.f : 0.f);
+            accumulate(1, m1 ? -1.f : 0.f);
+            accumulate(2, m2 ? -1.f : 0.f);
+            accumulate(3, m3 ? 1.f : 0.f);
 
             const float4* rd = smem + ((t + 1) & 1) * BUF + j;
             float4* wr = smem + (t & 1) * BUF + j + 1;
@@ -130,17 +175,43 @@ __global__ void __launch_bounds__(WMAX, 2) poly_kernel(Params p) {
             }
             if (out) {
                 const float v = fmaf(fc, p.invT, -0.5f);
-                float num = 0.f, den = 0.f;
+                const size_t o = (size_t)rho * W + co;
+                float num = 0.f, den = 0.f, dn = 0.f, dd = 0.f;
 #pragma unroll
                 for (int m = 0; m <= 2 * N; ++m) {
-                    // psi_m(v) by Horner
+                    // psi_m(v) (and psi_m'(v)) by Horner
                     float psi = p.c[m][2 * N];
 #pragma unroll
                     for (int n = 2 * N - 1; n >= 0; --n) psi = fmaf(psi, v, p.c[m][n]);
-                    num = fmaf(psi, fmaf(0.5f, B[m], B[m + 1]), num);
-                    den = fmaf(psi, B[m], den);
+                    float dpsi = 0.f;
+                    if constexpr (MODE != FWD) {
+                        dpsi = p.dc[m][2 * N - 1];
+#pragma unroll
+                        for (int n = 2 * N - 2; n >= 0; --n) dpsi = fmaf(dpsi, v, p.dc[m][n]);
+                    }
+                    if constexpr (MODE == ADJ) {
+                        // B[m] = A_m, B[NA + m] = B_m
+                        num = fmaf(psi, B[m], num);
+                        den = fmaf(dpsi, fmaf(fc, B[m], B[NA + m]), den);
+                    } else {
+                        const float g = fmaf(0.5f, B[m], B[m + 1]);
+                        num = fmaf(psi, g, num);
+                        den = fmaf(psi, B[m], den);
+                        if constexpr (MODE == FWD_SAVE) {
+                            dn = fmaf(dpsi, g, dn);
+                            dd = fmaf(dpsi, B[m], dd);
+                        }
+                    }
                 }
-                p.out[(size_t)rho * W + co] = p.T * num / den;
+                if constexpr (MODE == ADJ) {
+                    const float al = gq[4] * q[4].y;  // centre quad: (f, 1/den, out, X)
+                    p.gimg[o] = num + fmaf(den, p.invT, al * q[4].w);
+                } else {
+                    const float ov = p.T * num / den;
+                    p.out[o] = ov;
+                    if constexpr (MODE == FWD_SAVE)
+                        p.sv[o] = make_float4(fc, 1.0f / den, ov, fmaf(-ov * p.invT, dd, dn));
+                }
             }
         }
         __syncthreads();
@@ -148,9 +219,11 @@ __global__ void __launch_bounds__(WMAX, 2) poly_kernel(Params p) {
 }
 
 template <int N>
-static cudaError_t launch(const Params& p, int gx, int gy, cudaStream_t s) {
-    constexpr int NQ = (2 * N + 2 + 3) / 4;
-    auto kern = poly_kernel<N>;
+static cudaError_t launch(const Params& p, int mode, int gx, int gy, cudaStream_t s) {
+    const int NP = mode == ADJ ? 2 * (2 * N + 1) : 2 * N + 2;  // planes, as in the kernel
+    const int NQ = (NP + 3) / 4;
+    auto kern = mode == ADJ ? poly_kernel<N, ADJ>
+                            : (mode == FWD_SAVE ? poly_kernel<N, FWD_SAVE> : poly_kernel<N, FWD>);
     const size_t smem = sizeof(float4) * 2 * (size_t)NQ * (WMAX + 1);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
@@ -178,6 +251,65 @@ static void expansion(int N, double c[PCAP][PCAP]) {
     }
 }
 
+// Checks shared by the forward and the adjoint; fills the launch parameters
+// (expansion coefficients and their derivatives, tiles) and resolves N.
+static bf_status prepare(int H, int W, int r, float sigma_r, float T, int* N,
+                         const bf_opts* opts, Params* p, int* gx, int* gy) {
+    if (H < 1 || W < 1 || r < 0) return BF_ERR_INVALID_ARG;
+    if (!(T > 0.f) || !isfinite(T)) return BF_ERR_INVALID_ARG;
+    bf_status st = check_opts(opts);
+    if (st != BF_OK) return st;
+    if (opts && (opts->in_dtype != BF_F32 || opts->kahan || opts->trunc_tol > 0.f ||
+                 opts->gamma_mode != BF_GAMMA_FIXED))
+        return BF_ERR_UNSUPPORTED;
+    if (*N <= 0) {
+        *N = bf_poly_resolve_N(sigma_r, T);
+        if (*N < 0) return BF_ERR_INVALID_ARG;
+    }
+    if (*N > NMAX) return BF_ERR_UNSUPPORTED;
+    if (2 * r + 16 > WMAX) return BF_ERR_UNSUPPORTED;
+    memset(p, 0, sizeof(*p));
+    double c[PCAP][PCAP];
+    expansion(*N, c);
+    for (int m = 0; m < PCAP; ++m)
+        for (int n = 0; n < PCAP; ++n) {
+            p->c[m][n] = (float)c[m][n];
+            p->dc[m][n] = n + 1 < PCAP ? (float)((double)(n + 1) * c[m][n + 1]) : 0.f;
+        }
+    p->H = H; p->W = W; p->r = r;
+    p->T = T;
+    p->invT = 1.0f / T;
+    p->Tw = WMAX - 2 * r;
+    *gx = (W + p->Tw - 1) / p->Tw;
+    int hb;
+    if (opts && opts->tile_h > 0) {
+        hb = opts->tile_h;
+    } else {
+        // one wave of resident CTAs (two per SM)
+        int nb = 2 * sm_count() / *gx;
+        if (nb < 1) nb = 1;
+        hb = (H + nb - 1) / nb;
+        if (hb < 32) hb = 32;
+    }
+    p->Hb = hb;
+    *gy = (H + hb - 1) / hb;
+    return BF_OK;
+}
+
+static cudaError_t dispatch(const Params& p, int mode, int N, int gx, int gy, cudaStream_t s) {
+    switch (N) {
+        case 1: return launch<1>(p, mode, gx, gy, s);
+        case 2: return launch<2>(p, mode, gx, gy, s);
+        case 3: return launch<3>(p, mode, gx, gy, s);
+        case 4: return launch<4>(p, mode, gx, gy, s);
+        case 5: return launch<5>(p, mode, gx, gy, s);
+        case 6: return launch<6>(p, mode, gx, gy, s);
+        case 7: return launch<7>(p, mode, gx, gy, s);
+        case 8: return launch<8>(p, mode, gx, gy, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
 }  // namespace poly
 }  // namespace bf
 
@@ -195,65 +327,43 @@ extern "C" int bf_poly_resolve_N(float sigma_r, float T) {
 }
 
 extern "C" bf_status bf_poly_forward(const void* img, int H, int W, int r, float sigma_r,
-                                     float T, int N, float* out, const bf_opts* opts,
+                                     float T, int N, float* out, const bf_opts* opts, void* saved,
                                      void* stream) {
-    if (!img || !out || H < 1 || W < 1 || r < 0) return BF_ERR_INVALID_ARG;
+    if (!img || !out) return BF_ERR_INVALID_ARG;
     if ((const void*)out == img) return BF_ERR_INVALID_ARG;
-    if (!(T > 0.f) || !isfinite(T)) return BF_ERR_INVALID_ARG;
-    bf_status st = check_opts(opts);
+    if (saved && ((uintptr_t)saved & 15)) return BF_ERR_INVALID_ARG;
+    if (opts && opts->save_for_backward && !saved) return BF_ERR_INVALID_ARG;
+    poly::Params p;
+    int gx = 0, gy = 0;
+    bf_status st = poly::prepare(H, W, r, sigma_r, T, &N, opts, &p, &gx, &gy);
     if (st != BF_OK) return st;
-    if (opts && (opts->in_dtype != BF_F32 || opts->kahan || opts->trunc_tol > 0.f ||
-                 opts->gamma_mode != BF_GAMMA_FIXED))
-        return BF_ERR_UNSUPPORTED;
-    if (N <= 0) {
-        N = bf_poly_resolve_N(sigma_r, T);
-        if (N < 0) return BF_ERR_INVALID_ARG;
-    }
-    if (N > poly::NMAX) return BF_ERR_UNSUPPORTED;
-    if (2 * r + 16 > poly::WMAX) return BF_ERR_UNSUPPORTED;
     cudaStream_t s = (cudaStream_t)stream;
-    if (r == 0) {  // 1 x 1 window: out = f
+    if (r == 0 && !saved) {  // 1 x 1 window: out = f
         cudaError_t e = cudaMemcpyAsync(out, img, sizeof(float) * (size_t)H * W,
                                         cudaMemcpyDeviceToDevice, s);
         return e == cudaSuccess ? BF_OK : set_cuda_error(e);
     }
-    poly::Params p;
-    memset(&p, 0, sizeof(p));
-    double c[poly::PCAP][poly::PCAP];
-    poly::expansion(N, c);
-    for (int m = 0; m < poly::PCAP; ++m)
-        for (int n = 0; n < poly::PCAP; ++n) p.c[m][n] = (float)c[m][n];
     p.img = static_cast<const float*>(img);
     p.out = out;
-    p.H = H; p.W = W; p.r = r;
-    p.T = T;
-    p.invT = 1.0f / T;
-    p.Tw = poly::WMAX - 2 * r;
-    const int gx = (W + p.Tw - 1) / p.Tw;
-    int hb;
-    if (opts && opts->tile_h > 0) {
-        hb = opts->tile_h;
-    } else {
-        // one wave of resident CTAs (two per SM)
-        int nb = 2 * sm_count() / gx;
-        if (nb < 1) nb = 1;
-        hb = (H + nb - 1) / nb;
-        if (hb < 32) hb = 32;
-    }
-    p.Hb = hb;
-    const int gy = (H + hb - 1) / hb;
-    cudaError_t e;
-    switch (N) {
-        case 1: e = poly::launch<1>(p, gx, gy, s); break;
-        case 2: e = poly::launch<2>(p, gx, gy, s); break;
-        case 3: e = poly::launch<3>(p, gx, gy, s); break;
-        case 4: e = poly::launch<4>(p, gx, gy, s); break;
-        case 5: e = poly::launch<5>(p, gx, gy, s); break;
-        case 6: e = poly::launch<6>(p, gx, gy, s); break;
-        case 7: e = poly::launch<7>(p, gx, gy, s); break;
-        case 8: e = poly::launch<8>(p, gx, gy, s); break;
-        default: return BF_ERR_UNSUPPORTED;
-    }
+    p.sv = static_cast<float4*>(saved);
+    cudaError_t e = poly::dispatch(p, saved ? poly::FWD_SAVE : poly::FWD, N, gx, gy, s);
+    if (e != cudaSuccess) return set_cuda_error(e);
+    return BF_OK;
+}
+
+extern "C" bf_status bf_poly_backward(const float* grad_out, const void* saved, int H, int W,
+                                      int r, float sigma_r, float T, int N, float* grad_img,
+                                      const bf_opts* opts, void* stream) {
+    if (!grad_out || !saved || !grad_img) return BF_ERR_INVALID_ARG;
+    if ((uintptr_t)saved & 15) return BF_ERR_INVALID_ARG;
+    poly::Params p;
+    int gx = 0, gy = 0;
+    bf_status st = poly::prepare(H, W, r, sigma_r, T, &N, opts, &p, &gx, &gy);
+    if (st != BF_OK) return st;
+    p.bsv = static_cast<const float4*>(saved);
+    p.gout = grad_out;
+    p.gimg = grad_img;
+    cudaError_t e = poly::dispatch(p, poly::ADJ, N, gx, gy, (cudaStream_t)stream);
     if (e != cudaSuccess) return set_cuda_error(e);
     return BF_OK;
 }

@@ -54,3 +54,34 @@ def test_poly_order_from_sigma(cuda_lib):
     assert torch.equal(a, b)
     with pytest.raises(bf.BfError):
         bf.bf_poly_forward(f, 4, 0.0, 1.0, 9)
+
+
+@pytest.mark.parametrize("H,W,r,N,T", [(60, 80, 3, 3, 1.0), (70, 90, 5, 6, 1.0), (50, 140, 4, 8, 1.0),
+                                       (64, 64, 6, 5, 2.0)])
+def test_poly_adjoint_vs_central_differences(cuda_lib, H, W, r, N, T):
+    """dL/df of the p_N filter through the autograd wrapper against FP64
+    central differences of the oracle at sampled pixels (within 1e-3)."""
+    bf = cuda_lib
+    f = T * synth.rectangles(H, W, seed=H + N)
+    w = synth.weights((H, W), seed=1)
+    ft = torch.from_numpy(f.astype(np.float32)).cuda().requires_grad_(True)
+    out = bf.bilateral_poly(ft, r, 0.0, T, N)
+    assert rel_err(out.detach().cpu().numpy(), ref(f, r, N, T)).max() <= TOL
+    (torch.from_numpy(w).cuda() * out).sum().backward()
+    gg = ft.grad.cpu().numpy()
+    rng = np.random.default_rng(H * W + r)
+    f64 = f.astype(np.float32).astype(np.float64)
+    pts = [(0, 0), (H - 1, W - 1)] + [(int(rng.integers(0, H)), int(rng.integers(0, W)))
+                                      for _ in range(8)]
+    for y, x in pts:
+        y0, y1 = max(0, y - 2 * r), min(H, y + 2 * r + 1)
+        x0, x1 = max(0, x - 2 * r), min(W, x + 2 * r + 1)
+        sub = f64[y0:y1, x0:x1]
+        mask = np.zeros_like(sub)
+        mask[max(0, y - r) - y0:min(H, y + r + 1) - y0, max(0, x - r) - x0:min(W, x + r + 1) - x0] = 1
+        wsub = w[y0:y1, x0:x1].astype(np.float64) * mask
+        h = 1e-4 * T
+        sp = sub.copy(); sp[y - y0, x - x0] += h
+        sm = sub.copy(); sm[y - y0, x - x0] -= h
+        fd = (np.sum(wsub * ref(sp, r, N, T)) - np.sum(wsub * ref(sm, r, N, T))) / (2 * h)
+        assert abs(gg[y, x] - fd) <= 1e-3 * max(1.0, abs(fd)), (y, x, gg[y, x], fd)
