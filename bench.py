@@ -394,10 +394,19 @@ def extras(dev, flush, stream):
         "oracle_forward": o512t}
     img = torch.from_numpy(f_np).to(dev)
     out = torch.empty_like(img)
+    svq = torch.empty((H, W, 4), device=dev)
+    gq = torch.from_numpy(synth.weights((H, W), seed=1)).to(dev)
+    gi = torch.empty_like(img)
     for name, M, N_, kind in [("alg2_4096sq_r10_M2_N4", 2, 4, oracle.RANGE_COSN),
                               ("alg1_4096sq_r10_M2", 2, 0, oracle.RANGE_NONE)]:
         call = lambda M=M, N_=N_: bf.bf_spatial_forward(img, R, M, 0.0, 1.0, N_, out=out,
                                                         stream=stream)
+
+        def fwd_bwd(M=M, N_=N_):
+            bf.bf_spatial_forward(img, R, M, 0.0, 1.0, N_, out=out, saved=svq, stream=stream)
+            bf.bf_spatial_backward(gq, svq, R, M, 0.0, 1.0, N_, grad_img=gi, stream=stream)
+        fwd_bwd()
+        ms_fb = _time_ms(fwd_bwd, flush, stream)
         call()
         ms = _time_ms(call, flush, stream)
         o_np = out.cpu().numpy()
@@ -409,12 +418,19 @@ def extras(dev, flush, stream):
         nb = (M + 1) ** 2 * (N_ + 1)
         tf = basis_flops(nb) * H * W / (ms * 1e-3) / 1e12
         spatial[name] = {"ms": ms, "mpx_s": H * W / ms / 1e3, "basis_functions": nb,
+                         "fwd_bwd_ms": ms_fb, "fwd_bwd_mpx_s": H * W / ms_fb / 1e3,
                          "tflops_algorithmic": tf, "frac_of_fp32_peak": tf / FP32_PEAK_TFLOPS,
                          "err_vs_fp64": _err_stats(got, ref_s), "oracle_forward": o_s}
     res["spatial_kernel"] = spatial
 
     Np = bf.bf_poly_resolve_N(0.3, 1.0)
     call = lambda: bf.bf_poly_forward(img, R, 0.3, 1.0, 0, out=out, stream=stream)
+
+    def poly_fb():
+        bf.bf_poly_forward(img, R, 0.3, 1.0, 0, out=out, saved=svq, stream=stream)
+        bf.bf_poly_backward(gq, svq, R, 0.3, 1.0, 0, grad_img=gi, stream=stream)
+    poly_fb()
+    ms_pfb = _time_ms(poly_fb, flush, stream)
     call()
     ms = _time_ms(call, flush, stream)
     o_np = out.cpu().numpy()
@@ -425,6 +441,7 @@ def extras(dev, flush, stream):
     tf = basis_flops(2 * Np + 1) * H * W / (ms * 1e-3) / 1e12
     res[f"poly_range_4096sq_r10_sigma0.3_N{Np}"] = {
         "ms": ms, "mpx_s": H * W / ms / 1e3, "basis_functions": 2 * Np + 1,
+        "fwd_bwd_ms": ms_pfb, "fwd_bwd_mpx_s": H * W / ms_pfb / 1e3,
         "tflops_algorithmic": tf, "frac_of_fp32_peak": tf / FP32_PEAK_TFLOPS,
         "err_vs_fp64": _err_stats(got, ref_p), "oracle_forward": o_p}
     return res
