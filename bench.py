@@ -673,6 +673,32 @@ def main():
         rel = np.abs(got - ref) / np.maximum(np.abs(ref), 1e-2 * T_RANGE)
         err = {"max_rel": float(rel.max()), "mean_rel": float(rel.mean()),
                "max_abs": float(np.abs(got - ref).max()), "samples": int(idx.size)}
+        # the adjoint of the timed step: dL/df at sampled pixels against FP64
+        # central differences of the oracle on a crop around each pixel
+        bf.bf_forward(img, R, SIGMA, T_RANGE, N, out=out, opts=opts, saved=saved, stream=stream)
+        bf.bf_backward(img, out, g, saved, R, SIGMA, T_RANGE, N, grad_img=gimg, opts=opts,
+                       stream=stream)
+        torch.cuda.synchronize(dev)
+        gg = gimg.cpu().numpy()
+        gerr = 0.0
+        for _ in range(6):
+            y, x = int(rng.integers(0, H)), int(rng.integers(0, W))
+            y0, y1 = max(0, y - 2 * R), min(H, y + 2 * R + 1)
+            x0, x1 = max(0, x - 2 * R), min(W, x + 2 * R + 1)
+            sub = f_np[y0:y1, x0:x1].astype(np.float64)
+            mask = np.zeros_like(sub)
+            mask[max(0, y - R) - y0:min(H, y + R + 1) - y0,
+                 max(0, x - R) - x0:min(W, x + R + 1) - x0] = 1
+            wsub = w_np[y0:y1, x0:x1].astype(np.float64) * mask
+            hh = 1e-4
+            sp_, sm_ = sub.copy(), sub.copy()
+            sp_[y - y0, x - x0] += hh
+            sm_[y - y0, x - x0] -= hh
+            fd = (np.sum(wsub * oracle.bilateral(sp_, R, oracle.gamma_fixed(T_RANGE), N)) -
+                  np.sum(wsub * oracle.bilateral(sm_, R, oracle.gamma_fixed(T_RANGE), N))) / (2 * hh)
+            gerr = max(gerr, abs(float(gg[y, x]) - fd) / max(1.0, abs(fd)))
+        err["grad_max_rel_vs_fp64_fd"] = gerr
+        err["grad_samples"] = 6
 
     # roofline of the dominant kernel
     per_launch_fwd = t_fwd / args.steps

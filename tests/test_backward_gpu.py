@@ -175,3 +175,38 @@ def test_3d_launch_matches_per_image(cuda_lib, kahan_fallback):
         assert torch.max(torch.abs(gi1 - gi[b])).item() <= 1e-6 * max(1.0, gi1.abs().max().item())
         total += float(gs1)
     assert abs(float(gs) - total) <= 1e-4 * max(1.0, abs(total))
+
+
+def test_headline_adjoint_full_size_sampled(cuda_lib):
+    """The headline workload (4096^2, r=10, sigma_r=0.1 -> N=41) in the bench's
+    launch configuration: dL/df at 12 sampled pixels (corners included)
+    against FP64 central differences of the oracle on a crop around each."""
+    bf = cuda_lib
+    H = W = 4096
+    r, N = 10, 41
+    f = synth.rectangles(H, W, seed=0)
+    w = synth.weights((H, W), seed=1)
+    img = torch.from_numpy(f).cuda()
+    g = torch.from_numpy(w).cuda()
+    opts = bf._opts(save=True)
+    sv = torch.empty((H, W, 4), device="cuda")
+    out = bf.bf_forward(img, r, 0.1, 1.0, 0, opts=opts, saved=sv)
+    gi = torch.empty_like(img)
+    bf.bf_backward(img, out, g, sv, r, 0.1, 1.0, 0, grad_img=gi, opts=opts)
+    gg = gi.cpu().numpy()
+    rng = np.random.default_rng(17)
+    pts = [(0, 0), (H - 1, W - 1), (0, W - 1), (H - 1, 0)] + \
+        [(int(rng.integers(0, H)), int(rng.integers(0, W))) for _ in range(8)]
+    for y, x in pts:
+        y0, y1 = max(0, y - 2 * r), min(H, y + 2 * r + 1)
+        x0, x1 = max(0, x - 2 * r), min(W, x + 2 * r + 1)
+        sub = f[y0:y1, x0:x1].astype(np.float64)
+        mask = np.zeros_like(sub)
+        mask[max(0, y - r) - y0:min(H, y + r + 1) - y0, max(0, x - r) - x0:min(W, x + r + 1) - x0] = 1
+        wsub = w[y0:y1, x0:x1].astype(np.float64) * mask
+        h = 1e-4
+        sp = sub.copy(); sp[y - y0, x - x0] += h
+        sm = sub.copy(); sm[y - y0, x - x0] -= h
+        fd = (np.sum(wsub * oracle.bilateral(sp, r, math.pi / 2, N)) -
+              np.sum(wsub * oracle.bilateral(sm, r, math.pi / 2, N))) / (2 * h)
+        assert abs(gg[y, x] - fd) <= GTOL * max(1.0, abs(fd)), (y, x, gg[y, x], fd)
