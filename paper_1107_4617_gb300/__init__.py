@@ -174,6 +174,14 @@ def _dptr(t, name):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _check_bytes(t, need: int, name: str):
+    """Raise if tensor t holds fewer than `need` bytes (the library cannot
+    check the size of a raw device pointer)."""
+    have = t.numel() * t.element_size()
+    if have < need:
+        raise ValueError(f"{name} holds {have} bytes, needs {need}")
+
+
 def _in_dtype(t):
     import torch
     if t.dtype == torch.float32:
@@ -238,6 +246,9 @@ def bf_forward(img, r: int, sigma_r: float, T: float = 1.0, N: int = 0, out=None
         raise ValueError("opts.in_dtype does not match img.dtype")
     if out is None:
         out = torch.empty((H, W), dtype=torch.float32, device=img.device)
+    _check_bytes(out, 4 * H * W, "out")
+    if saved is not None:
+        _check_bytes(saved, bf_saved_bytes(H, W), "saved")
     st = load().bf_forward(_dptr(img, "img"), H, W, int(r), float(sigma_r), float(T), int(N),
                            _dptr(out, "out"), ctypes.byref(opts),
                            _dptr(saved, "saved") if saved is not None else None,
@@ -254,6 +265,10 @@ def bf_backward(img, out, grad_out, saved, r: int, sigma_r: float, T: float = 1.
     if opts is None:
         opts = _opts(in_dtype=_in_dtype(img))
     ws_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    _check_bytes(saved, bf_saved_bytes(H, W), "saved")
+    _check_bytes(grad_out, 4 * H * W, "grad_out")
+    if grad_img is not None:
+        _check_bytes(grad_img, 4 * H * W, "grad_img")
     st = load().bf_backward(_dptr(img, "img"), _dptr(out, "out"), _dptr(grad_out, "grad_out"),
                             _dptr(saved, "saved"), H, W, int(r), float(sigma_r), float(T), int(N),
                             _dptr(grad_img, "grad_img") if grad_img is not None else None,
@@ -275,6 +290,9 @@ def bf_spatial_forward(img, r: int, M: int, sigma_r: float = 0.0, T: float = 1.0
     H, W = img.shape
     if out is None:
         out = torch.empty((H, W), dtype=torch.float32, device=img.device)
+    _check_bytes(out, 4 * H * W, "out")
+    if saved is not None:
+        _check_bytes(saved, bf_saved_bytes(H, W), "saved")
     st = load().bf_spatial_forward(_dptr(img, "img"), H, W, int(r), int(M), float(sigma_r),
                                    float(T), int(N), _dptr(out, "out"),
                                    ctypes.byref(opts) if opts is not None else None,
@@ -291,6 +309,8 @@ def bf_spatial_backward(grad_out, saved, r: int, M: int, sigma_r: float = 0.0, T
     H, W = grad_out.shape
     if grad_img is None:
         grad_img = torch.empty((H, W), dtype=torch.float32, device=grad_out.device)
+    _check_bytes(saved, bf_saved_bytes(H, W), "saved")
+    _check_bytes(grad_img, 4 * H * W, "grad_img")
     st = load().bf_spatial_backward(_dptr(grad_out, "grad_out"), _dptr(saved, "saved"), H, W,
                                     int(r), int(M), float(sigma_r), float(T), int(N),
                                     _dptr(grad_img, "grad_img"),
@@ -314,6 +334,9 @@ def bf_poly_forward(img, r: int, sigma_r: float = 0.0, T: float = 1.0, N: int = 
     H, W = img.shape
     if out is None:
         out = torch.empty((H, W), dtype=torch.float32, device=img.device)
+    _check_bytes(out, 4 * H * W, "out")
+    if saved is not None:
+        _check_bytes(saved, bf_saved_bytes(H, W), "saved")
     st = load().bf_poly_forward(_dptr(img, "img"), H, W, int(r), float(sigma_r), float(T),
                                 int(N), _dptr(out, "out"),
                                 ctypes.byref(opts) if opts is not None else None,
@@ -330,6 +353,8 @@ def bf_poly_backward(grad_out, saved, r: int, sigma_r: float = 0.0, T: float = 1
     H, W = grad_out.shape
     if grad_img is None:
         grad_img = torch.empty((H, W), dtype=torch.float32, device=grad_out.device)
+    _check_bytes(saved, bf_saved_bytes(H, W), "saved")
+    _check_bytes(grad_img, 4 * H * W, "grad_img")
     st = load().bf_poly_backward(_dptr(grad_out, "grad_out"), _dptr(saved, "saved"), H, W,
                                  int(r), float(sigma_r), float(T), int(N),
                                  _dptr(grad_img, "grad_img"),
@@ -373,6 +398,9 @@ def bf_forward3d(img, r: int, sigma_r: float, T: float = 1.0, N: int = 0, out=No
         raise ValueError("opts.in_dtype does not match img.dtype")
     if out is None:
         out = torch.empty((B, H, W), dtype=torch.float32, device=img.device)
+    _check_bytes(out, 4 * B * H * W, "out")
+    if saved is not None:
+        _check_bytes(saved, B * bf_saved_bytes(H, W), "saved")
     st = load().bf_forward3d(_dptr(img, "img"), B, H, W, int(r), float(sigma_r), float(T), int(N),
                              _dptr(out, "out"), ctypes.byref(opts),
                              _dptr(saved, "saved") if saved is not None else None,
@@ -389,6 +417,10 @@ def bf_backward3d(img, out, grad_out, saved, r: int, sigma_r: float, T: float = 
     if opts is None:
         opts = _opts(in_dtype=_in_dtype(img))
     ws_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    _check_bytes(saved, B * bf_saved_bytes(H, W), "saved")
+    _check_bytes(grad_out, 4 * B * H * W, "grad_out")
+    if grad_img is not None:
+        _check_bytes(grad_img, 4 * B * H * W, "grad_img")
     st = load().bf_backward3d(_dptr(img, "img"), _dptr(out, "out"), _dptr(grad_out, "grad_out"),
                               _dptr(saved, "saved"), B, H, W, int(r), float(sigma_r), float(T),
                               int(N),
@@ -603,6 +635,7 @@ def bf_backward_noalloc(img, out, grad_out, saved, r: int, sigma_r: float, T: fl
     H, W = img.shape
     if opts is None:
         opts = _opts(in_dtype=_in_dtype(img))
+    _check_bytes(saved, bf_saved_bytes(H, W), "saved")
     st = f(_dptr(img, "img"), _dptr(out, "out"), _dptr(grad_out, "grad_out"),
            _dptr(saved, "saved"), H, W, int(r), float(sigma_r), float(T), int(N),
            _dptr(grad_img, "grad_img") if grad_img is not None else None,

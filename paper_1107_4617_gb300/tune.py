@@ -121,7 +121,7 @@ def _gpu_timer(H, W, r, sigma_r, T, N, dtype, adjoint, reps):
     img = torch.from_numpy(synth.rectangles(H, W, seed=0)).to(dev).to(dtype)
     g = torch.from_numpy(synth.weights((H, W), seed=1)).to(dev)
     out = torch.empty((H, W), device=dev)
-    sv = torch.empty((3, H, W), device=dev)
+    sv = torch.empty((H, W, 4), device=dev)  # bf_saved_bytes(H, W): one 16-byte quad per pixel
     gi = torch.empty((H, W), device=dev)
     flush = torch.empty((64 << 20,), device=dev)
     in_dtype = bf.BF16 if dtype == torch.bfloat16 else bf.F32

@@ -190,3 +190,15 @@ def test_poly_order_rule():
         assert bf.bf_poly_resolve_N(sigma, T) == N
         assert N == max(1, math.ceil(T * T / (2 * sigma * sigma) - 1e-9))
     assert bf.bf_poly_resolve_N(0.0, 1.0) == -1
+
+
+def test_binding_rejects_undersized_saved_buffer():
+    """The binding checks buffer sizes the C ABI cannot see (a raw pointer):
+    a saved buffer of the old three-plane size is refused before any call."""
+    import torch
+    img = torch.zeros((8, 9))
+    small = torch.zeros((3, 8, 9))
+    with pytest.raises(ValueError, match="saved"):
+        bf._check_bytes(small, bf.bf_saved_bytes(8, 9), "saved")
+    bf._check_bytes(torch.zeros((8, 9, 4)), bf.bf_saved_bytes(8, 9), "saved")
+    assert img.numel() * 16 == bf.bf_saved_bytes(8, 9)
