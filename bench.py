@@ -699,6 +699,16 @@ def main():
             gerr = max(gerr, abs(float(gg[y, x]) - fd) / max(1.0, abs(fd)))
         err["grad_max_rel_vs_fp64_fd"] = gerr
         err["grad_samples"] = 6
+        # how far the raised-cosine filter is from the exact-Gaussian bilateral
+        # filter it approximates (Eq. approx2): reported, not a parity metric.
+        # N = 41 by the order rule gives an effective width 1/(gamma sqrt N)
+        # slightly below sigma_r; both targets are reported.
+        gsig_eff = 1.0 / (oracle.gamma_fixed(T_RANGE) * math.sqrt(N))
+        for name, sg in (("approx_vs_gaussian_sigma_r", SIGMA), ("approx_vs_gaussian_sigma_eff",
+                                                                 gsig_eff)):
+            gref = oracle.bilateral_gauss_points(f_np.astype(np.float64), R, sg, idx)
+            d = np.abs(got - gref)
+            err[name] = {"sigma": sg, "max_abs": float(d.max()), "mean_abs": float(d.mean())}
 
     # roofline of the dominant kernel
     per_launch_fwd = t_fwd / args.steps

@@ -65,6 +65,11 @@ def _load():
             lib.oracle_bf_gauss.restype = ctypes.c_int
             lib.oracle_bf_gauss.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                             ctypes.c_double, _dp]
+            lib.oracle_bf_gauss_points.restype = ctypes.c_int
+            lib.oracle_bf_gauss_points.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                   ctypes.c_double,
+                                                   ctypes.POINTER(ctypes.c_longlong),
+                                                   ctypes.c_longlong, _dp]
             lib.oracle_bf_grad.restype = ctypes.c_int
             lib.oracle_bf_grad.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                            ctypes.c_double, ctypes.c_int, _dp, _dp]
@@ -167,6 +172,20 @@ def bilateral_gauss(f, r: int, sigma: float):
     rc = _load().oracle_bf_gauss(_ptr(f), H, W, int(r), float(sigma), _ptr(out))
     if rc != 0:
         raise ValueError(f"oracle_bf_gauss failed ({rc})")
+    return out
+
+
+def bilateral_gauss_points(f, r: int, sigma: float, idx):
+    """Exact-Gaussian bilateral filter at the flat pixel indices ``idx`` only."""
+    f = _as_f64(f)
+    H, W = f.shape
+    idx = np.ascontiguousarray(np.asarray(idx, dtype=np.int64))
+    out = np.empty(idx.shape[0], np.float64)
+    rc = _load().oracle_bf_gauss_points(_ptr(f), H, W, int(r), float(sigma),
+                                        idx.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)),
+                                        idx.shape[0], _ptr(out))
+    if rc != 0:
+        raise ValueError(f"oracle_bf_gauss_points failed ({rc})")
     return out
 
 

@@ -304,3 +304,28 @@ int oracle_bf_general_rows(const double* f, int H, int W, int r, int spatial, in
     free(sw);
     return 0;
 }
+
+/* Exact-Gaussian bilateral filter at a list of flat pixel indices only (for
+   the approximation error on large images). */
+int oracle_bf_gauss_points(const double* f, int H, int W, int r, double sigma,
+                           const long long* idx, long long n, double* out) {
+    if (!f || !idx || !out || H <= 0 || W <= 0 || r < 0 || !(sigma > 0) || n < 0) return -1;
+    const double inv = 1.0 / (2.0 * sigma * sigma);
+#pragma omp parallel for schedule(static)
+    for (long long i = 0; i < n; ++i) {
+        const long long p = idx[i];
+        const int y = (int)(p / W), x = (int)(p % W);
+        const double fx = f[p];
+        double num = 0.0, eta = 0.0;
+        for (int yy = imax(0, y - r); yy <= imin(H - 1, y + r); ++yy)
+            for (int xx = imax(0, x - r); xx <= imin(W - 1, x + r); ++xx) {
+                const double fy = f[(size_t)yy * W + xx];
+                const double t = fy - fx;
+                const double w = exp(-t * t * inv);
+                num += w * fy;
+                eta += w;
+            }
+        out[i] = num / eta;
+    }
+    return 0;
+}

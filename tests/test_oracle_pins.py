@@ -384,3 +384,11 @@ def test_poly_filter_brute_force_and_N0():
     # p_0 = 1: the box mean
     np.testing.assert_allclose(oracle.bilateral_general(f, r, range_kind=oracle.RANGE_POLY, N=0),
                                box_sum(f, r) / box_sum(np.ones_like(f), r), rtol=0, atol=1e-14)
+
+
+def test_gauss_points_match_full():
+    f = synth.rectangles(20, 23, seed=6).astype(np.float64)
+    full = oracle.bilateral_gauss(f, 3, 0.2)
+    idx = np.array([0, 5, 77, 199, 459])
+    np.testing.assert_allclose(oracle.bilateral_gauss_points(f, 3, 0.2, idx), full.ravel()[idx],
+                               rtol=0, atol=1e-15)
