@@ -392,3 +392,22 @@ def test_gauss_points_match_full():
     idx = np.array([0, 5, 77, 199, 459])
     np.testing.assert_allclose(oracle.bilateral_gauss_points(f, 3, 0.2, idx), full.ravel()[idx],
                                rtol=0, atol=1e-15)
+
+
+def test_gauss_filter_brute_force():
+    """The exact-Gaussian bilateral filter (the kernel q_N approximates, Eq.
+    approx2) against an independent Python quadruple loop with math.exp."""
+    f = np.random.default_rng(21).uniform(0, 1, (7, 8))
+    r, sig = 2, 0.15
+    H, W = f.shape
+    ref = np.zeros((H, W))
+    for y in range(H):
+        for x in range(W):
+            num = eta = 0.0
+            for yy in range(max(0, y - r), min(H, y + r + 1)):
+                for xx in range(max(0, x - r), min(W, x + r + 1)):
+                    wgt = math.exp(-(f[yy, xx] - f[y, x]) ** 2 / (2 * sig * sig))
+                    num += wgt * f[yy, xx]
+                    eta += wgt
+            ref[y, x] = num / eta
+    np.testing.assert_allclose(oracle.bilateral_gauss(f, r, sig), ref, rtol=0, atol=1e-13)
