@@ -212,7 +212,7 @@ def extras(dev, flush, stream):
 
     import oracle
     import paper_1107_4617_gb300 as bf
-    from paper_1107_4617_gb300 import synth
+    from paper_1107_4617_gb300 import synth, tune
     res = {}
     rng = np.random.default_rng(7)
 
@@ -264,6 +264,18 @@ def extras(dev, flush, stream):
             bf.bf_batch_launch(ws, opts, stream=bs)
         px = sum(sp["H"] * sp["W"] for sp in specs)
         ms_graph = _time_ms(lambda: g.replay(), flush, bs)
+    # the same launch with the autotuned band height / strip width for this batch
+    best = tune.tune_batch(descs, use_cache=False)
+    topts = bf._opts(tile_w=best["tile_w"], tile_h=best["tile_h"])
+    wst = torch.empty(((bf.bf_batch_workspace_bytes(descs, topts) + 3) // 4,), device=dev)
+    with torch.cuda.stream(bs):
+        bf.bf_batch_prepare(descs, wst, topts, stream=bs)
+        bf.bf_batch_launch(wst, topts, stream=bs)
+        torch.cuda.synchronize()
+        gt = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(gt, stream=bs):
+            bf.bf_batch_launch(wst, topts, stream=bs)
+        ms_tuned = _time_ms(lambda: gt.replay(), flush, bs)
 
     def separate():
         for sp, im, o in zip(specs, imgs, outs):
@@ -285,9 +297,11 @@ def extras(dev, flush, stream):
         "megapixels": px / 1e6, "persistent_graph_ms": ms_graph,
         "persistent_graph_mpx_s": px / ms_graph / 1e3, "separate_launches_ms": ms_sep,
         "separate_launches_mpx_s": px / ms_sep / 1e3,
+        "tuned_shape": {"tile_w": best["tile_w"], "tile_h": best["tile_h"]},
+        "persistent_graph_tuned_ms": ms_tuned, "persistent_graph_tuned_mpx_s": px / ms_tuned / 1e3,
         "err_vs_fp64": {"max_rel": max(e["max_rel"] for e in errs),
                         "max_abs": max(e["max_abs"] for e in errs), "images_checked": len(errs)}}
-    del imgs, outs, ws, g
+    del imgs, outs, ws, g, wst, gt
 
     # differentiation: 16 x 512^2, r=7, sigma_r=0.15 (N=19), L = sum(w * out)
     B, Hd, r = 16, 512, 7

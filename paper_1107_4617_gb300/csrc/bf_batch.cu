@@ -19,7 +19,7 @@ static const int kSysMagic = 0x42465359;  // "BFSY"
 // strip's skew (Wi steps) and the 2r warm-up rows stay a minor cost, small
 // enough that a few thousand tiles balance over the SMs.
 static int sys_batch_rows(int r, int H, const bf_opts* o) {
-    if (o && o->tile_h > 0) return o->tile_h;
+    if (o && o->tile_h > 0) return o->tile_h < H ? o->tile_h : H;
     int hb = 512;
     if (hb < 8 * r) hb = 8 * r;
     return hb < H ? hb : H;

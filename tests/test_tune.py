@@ -35,6 +35,74 @@ def test_tune_cache_roundtrip(tmp_path, monkeypatch):
     assert again == best and len(calls) == n
 
 
+def _descs(specs):
+    out = []
+    for sp in specs:
+        d = bf.BfDesc()
+        d.H, d.W, d.r, d.N, d.sigma_r, d.T = sp["H"], sp["W"], sp["r"], 0, sp["sigma_r"], 1.0
+        out.append(d)
+    return out
+
+
+def test_batch_signature_and_candidates():
+    specs = synth.batch_specs(6, seed=3)
+    a, b = _descs(specs), _descs(specs)
+    b[0].img = 12345  # addresses do not enter the key
+    assert tune.batch_signature(a) == tune.batch_signature(b)
+    b[2].r += 1
+    assert tune.batch_signature(a) != tune.batch_signature(b)
+    assert tune.batch_signature(a).startswith("batch6|")
+    c = tune.batch_candidates([3, 30])
+    assert {x["tile_w"] for x in c} == {0, 256} and {"tile_w": 0, "tile_h": 0} in c
+    # a half-width too wide for a 256-column strip leaves only the per-image rule
+    assert {x["tile_w"] for x in tune.batch_candidates([3, 121])} == {0}
+
+
+def test_tune_batch_cache_roundtrip(tmp_path, monkeypatch):
+    monkeypatch.setenv("BF_TUNE_CACHE", str(tmp_path / "t.json"))
+    descs = _descs(synth.batch_specs(5, seed=9))
+    calls = []
+
+    def fake(c):
+        calls.append(c)
+        return 2.0 - (c["tile_h"] == 768) + (c["tile_w"] == 256)
+
+    best = tune.tune_batch(descs, timer=fake)
+    assert best["tile_w"] == 0 and best["tile_h"] == 768 and best["ms"] == 1.0
+    n = len(calls)
+    assert tune.tune_batch(_descs(synth.batch_specs(5, seed=9)), timer=fake) == best
+    assert len(calls) == n  # served from the cache
+    other = tune.tune_batch(_descs(synth.batch_specs(5, seed=10)), timer=fake)
+    assert len(calls) == 2 * n and other["tile_h"] == 768
+
+
+@pytest.mark.gpu
+def test_tuned_batch_same_filter(cuda_lib, tmp_path, monkeypatch):
+    """Every tried batch launch shape gives the filter of the separate launches."""
+    monkeypatch.setenv("BF_TUNE_CACHE", str(tmp_path / "t.json"))
+    specs = synth.batch_specs(12, seed=5, side_lo=40, side_hi=700)
+    imgs = [torch.from_numpy(synth.rectangles(sp["H"], sp["W"], seed=sp["seed"])).cuda()
+            for sp in specs]
+    outs = [torch.empty_like(im) for im in imgs]
+    descs = bf.make_descs(imgs, outs, [sp["r"] for sp in specs], [sp["sigma_r"] for sp in specs])
+    refs = [bf.bf_forward(im, sp["r"], sp["sigma_r"]) for sp, im in zip(specs, imgs)]
+    for c in tune.batch_candidates([sp["r"] for sp in specs]):
+        for o in outs:
+            o.fill_(float("nan"))
+        o = bf._opts(tile_w=c["tile_w"], tile_h=c["tile_h"])
+        ws = torch.empty(((bf.bf_batch_workspace_bytes(descs, o) + 3) // 4,), device="cuda")
+        bf.bf_batch(descs, ws, o)
+        torch.cuda.synchronize()
+        # different band / strip splits round differently: each side is within
+        # the parity tolerance 1e-4 * max(|v|, 1e-2 T) of the exact filter
+        for a, b in zip(outs, refs):
+            tol = 2e-4 * torch.clamp(torch.abs(b), min=1e-2)
+            assert bool(torch.all(torch.abs(a - b) <= tol)), c
+    o = tune.tuned_batch_opts(descs)
+    assert (o.tile_w, o.tile_h) in {(c["tile_w"], c["tile_h"]) for c in
+                                    tune.batch_candidates([sp["r"] for sp in specs])}
+
+
 @pytest.mark.gpu
 def test_tuned_opts_same_filter(cuda_lib, tmp_path, monkeypatch):
     monkeypatch.setenv("BF_TUNE_CACHE", str(tmp_path / "t.json"))
