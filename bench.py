@@ -511,7 +511,8 @@ def main():
                     help="time the device step only (no e2e, N=40, CPU or accuracy legs); "
                          "used for profiler captures")
     ap.add_argument("--profile-workload", default=None,
-                    choices=["spatial_M2_N4", "alg1_M2", "poly_N6", "trunc_1e-3"],
+                    choices=["spatial_M2_N4", "spatial_M2_N4_fb", "alg1_M2", "poly_N6",
+                             "trunc_1e-3"],
                     help="launch only this 4096^2 r=10 workload's kernel, warmup + steps "
                          "times (profiler captures of the extra workloads)")
     args = ap.parse_args()
@@ -559,6 +560,11 @@ def main():
         pw = args.profile_workload
         if pw == "spatial_M2_N4":
             call = lambda: bf.bf_spatial_forward(img, R, 2, 0.0, 1.0, 4, out=out, stream=stream)
+        elif pw == "spatial_M2_N4_fb":
+            # forward with saved quads, then the adjoint
+            def call():
+                bf.bf_spatial_forward(img, R, 2, 0.0, 1.0, 4, out=out, saved=saved, stream=stream)
+                bf.bf_spatial_backward(g, saved, R, 2, 0.0, 1.0, 4, grad_img=gimg, stream=stream)
         elif pw == "alg1_M2":
             call = lambda: bf.bf_spatial_forward(img, R, 2, 0.0, 1.0, 0, out=out, stream=stream)
         elif pw == "poly_N6":

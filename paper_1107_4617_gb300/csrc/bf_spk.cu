@@ -47,9 +47,16 @@ struct Dims {
     static constexpr int NS = (M % 2 == 0) ? (NA - 1) * ND + (ND + 1) / 2 : NA * ND;
 };
 
-// Largest combo table any instantiation needs.
+// Largest combo count any instantiation has, and caps of the factor tables.
 constexpr int NS_CAP = 64;
+constexpr int FCAP = 8;
 
+// coef_c factors as fa[a] fb[|b|] fk[|k|] (halved for the one self-conjugate
+// combo a = b = k = 0): fa = beta_a (x2 for a = 0: one of each conjugate pair
+// is kept), fb = beta_|b| m_b / 4, fk = alpha_|k| m_k, with m = 2 for a zero
+// index (both sign choices of cos(A +- B +- C) give the same term). Indices
+// are half-indices: a = (M mod 2) + 2 ia, |b| = (M mod 2) + 2 ib, |k| = (N
+// mod 2) + 2 kk.
 struct Params {
     const float* img;      // forward input (forward modes)
     float* out;            // forward output
@@ -59,17 +66,33 @@ struct Params {
     float* gimg;           // adjoint: dL/dimg
     int H, W, r, Hb, Tw;
     float gamma;           // range kernel frequency (unused when N = 0)
-    float coef[NS_CAP];    // coef_c, in combo order
-    float ck[NS_CAP];      // coef_c k_c (k_c: signed range harmonic of combo c)
+    float fa[FCAP], fb[FCAP], fk[FCAP];
+    float coef[NS_CAP];    // plane-sum form: coef_c, in combo order
+    float ck[NS_CAP];      // plane-sum form: coef_c k_c (k_c: the combo's signed k)
 };
 
 // Launch modes: forward, forward that also saves the adjoint's quads, adjoint.
 enum Mode { FWD = 0, FWD_SAVE = 1, ADJ = 2 };
 
+__device__ __forceinline__ float2 dup(float v) { return make_float2(v, v); }
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
-__device__ __forceinline__ float2 conj2(float2 a) { return make_float2(a.x, -a.y); }
+
+// A complex number z as the register pairs used by the paired FP32 units:
+// v = (Re z, Im z) and iv = i z = (-Im z, Re z), so that w z = w.x v + w.y iv
+// for any complex w.
+struct Cx {
+    float2 v, iv;
+};
+
+// (c z) for a complex constant c given as dup(c.x), dup(c.y), dup(-c.y).
+__device__ __forceinline__ Cx crot(float2 cx, float2 cy, float2 cyn, const Cx& z) {
+    Cx o;
+    o.v = __ffma2_rn(cy, z.iv, __fmul2_rn(cx, z.v));
+    o.iv = __ffma2_rn(cyn, z.v, __fmul2_rn(cx, z.iv));
+    return o;
+}
 
 // e^{i m gs n} for integers m, n: the phase is reduced exactly on integers
 // (period 2 (2r + 1) in m n) before the sine and cosine.
@@ -82,9 +105,356 @@ __device__ __forceinline__ float2 phase(int m, int n, int r) {
     return make_float2(c, s);
 }
 
-// Range harmonics z_k = e^{i k theta} for signed k = -N, ..., N (step 2).
+// Non-negative range harmonics z_kk = e^{i k theta}, k = (N mod 2) + 2 kk,
+// theta = gamma f, from one sine and cosine of theta and complex products.
 template <int N>
-__device__ __forceinline__ void range_harmonics(float f, float gamma, float2 (&z)[N + 1]) {
+__device__ __forceinline__ void range_harmonics(float f, float gamma, float2 (&z)[N / 2 + 1]) {
+    if constexpr (N == 0) {
+        z[0] = make_float2(1.f, 0.f);
+    } else {
+        float s1, c1;
+        __sincosf(gamma * f, &s1, &c1);
+        const float2 w1 = make_float2(c1, s1);
+        const float2 w2 = cmul(w1, w1);
+        z[0] = (N & 1) ? w1 : make_float2(1.f, 0.f);
+#pragma unroll
+        for (int i = 1; i <= N / 2; ++i) z[i] = cmul(z[i - 1], w2);
+    }
+}
+
+// Longest phase table: 2 (2r + 1) entries for r <= 56, two float4 each.
+constexpr int PTAB_CAP = 2 * (2 * 56 + 1);
+
+__device__ __forceinline__ void prefetch_l2(const void* ptr) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(ptr));
+}
+
+// MODE = ADJ runs the same moving sums on the planes (alpha E_c, beta E_c),
+// alpha = g / den, beta = -alpha out (the window and the spatial kernel are
+// symmetric, so the adjoint's neighbour sums are again moving sums centred
+// on the pixel whose gradient is formed), and combines them into
+//   dL/df(p) = sum_c coef_c Re(conj E_c(p) A_c)
+//            + gamma [sum_c coef_c k_c Im(conj E_c(p) (f(p) A_c + B_c)) + alpha(p) X(p)],
+// A_c = Sum(alpha E_c), B_c = Sum(beta E_c), X = dnum_s - out dden_s saved by the
+// forward (dnum_s = sum_c coef_c k_c Im(conj E_c S_c(f E)), the derivative of
+// num through the centre value, divided by gamma).
+//
+// Per step and thread: the four entering / leaving pixels' range harmonics,
+// weighted and summed into Z_k (real weights, so Z_{-k} = conj Z_k); then per
+// combo the column-rotated vertical difference D'_c += e^{i a gs cw} e^{i b gs
+// e} Z_k, the horizontal hand-off S_c = S_c(left) + D'_c, and the centre's
+// coef_c conj(E_c) S_c, all on (re, im) register pairs.
+template <int M, int N, int MODE>
+__global__ void __launch_bounds__(WMAX, 2) spk_kernel(Params p) {
+    using D = Dims<M, N>;
+    constexpr int NA = D::NA, NB = D::NB, NK = D::NK;
+    constexpr int KH = N / 2 + 1;        // non-negative range harmonics
+    constexpr int BH = M / 2 + 1;        // non-negative spatial harmonics |b|
+    constexpr int LD = WMAX + 1;
+    constexpr int BUF = D::NS * LD;
+    extern __shared__ float4 smem[];  // [2][NS][LD]: (g.re, g.im, h.re, h.im), then the table
+    const int Wi = blockDim.x;
+    const int j = threadIdx.x;
+    const int w = j >> 5;
+    const int r = p.r;
+    const int W = p.W;
+    const int x0 = blockIdx.x * p.Tw;
+    const int cw = x0 - r + j;
+    const int c2 = cw - 2 * r - 1;
+    const int co = cw - r;
+    const bool own_in = cw >= 0 && cw < W;
+    const bool sec_in = (j >= 2 * r + 1) && c2 >= 0 && c2 < W;
+    const bool out_lane = (j >= 2 * r) && co < W;
+    const int y0 = blockIdx.y * p.Hb;
+    const int rows = min(p.Hb, p.H - y0);
+    const int span = rows + 2 * r;
+    const int steps = span + Wi - 1;
+    // -(-1)^M: weight of the second column; (-1)^M: the leaving row's phase
+    // relative to the entering row's, e^{-i b gs (2r+1)} for every b of M's parity
+    const float sgn2 = (M & 1) ? 1.f : -1.f;
+    const float lsg = (M & 1) ? -1.f : 1.f;
+
+    for (int i = j; i < 2 * BUF; i += Wi) smem[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int P = 2 * (2 * r + 1);  // period of e^{i gs n} in n
+    // tab[2q] = (z, i z), tab[2q + 1] = (conj z, i conj z) for z = e^{i pi q / (2r+1)}
+    float4* ptab = smem + 2 * BUF;
+    for (int q = j; q < P; q += Wi) {
+        float s, c;
+        sincospif((float)q / (float)(2 * r + 1), &s, &c);
+        ptab[2 * q] = make_float4(c, s, -s, c);
+        ptab[2 * q + 1] = make_float4(c, -s, s, c);
+    }
+    // phase indices b e mod P of the entering row e (b > 0, advanced by b per
+    // step) and their offsets b r to the centre row rho = e - r
+    int qe[BH], qoff[BH], qinc[BH];
+#pragma unroll
+    for (int hb = 0; hb < BH; ++hb) {
+        const int b = (M & 1) + 2 * hb;
+        int q0 = (int)(((long long)b * (long long)(y0 - r - j)) % P);
+        if (q0 < 0) q0 += P;
+        qe[hb] = q0;
+        qoff[hb] = (b * r) % P;
+        qinc[hb] = b % P;  // b may exceed the period when r is small
+    }
+
+    // column phases: e^{i a gs cw} of the own column, and coef's a-factor times
+    // e^{i a gs co} of the centre column, as dup pairs (x, y, -y)
+    float2 cx[NA], cy[NA], cyn[NA], ox[NA], oy[NA], oyn[NA];
+#pragma unroll
+    for (int ia = 0; ia < NA; ++ia) {
+        const int a = (M & 1) + 2 * ia;
+        const float2 c = phase(a, cw, r);
+        const float2 o = phase(a, co, r);
+        const float fa = p.fa[ia];
+        cx[ia] = dup(c.x); cy[ia] = dup(c.y); cyn[ia] = dup(-c.y);
+        ox[ia] = dup(fa * o.x); oy[ia] = dup(fa * o.y); oyn[ia] = dup(-fa * o.y);
+    }
+    float fbv[BH], fkv[KH];
+#pragma unroll
+    for (int hb = 0; hb < BH; ++hb) fbv[hb] = p.fb[hb];
+#pragma unroll
+    for (int kk = 0; kk < KH; ++kk) fkv[kk] = p.fk[kk];
+
+    // column-rotated vertical differences of the kept combos: (f-weighted,
+    // unweighted) in the forward, (alpha, beta)-weighted in the adjoint
+    float2 Dg[D::NS], Dh[D::NS];
+#pragma unroll
+    for (int c = 0; c < D::NS; ++c) { Dg[c] = make_float2(0.f, 0.f); Dh[c] = Dg[c]; }
+    // the five pixels of step tt (own / second column, entering / leaving row,
+    // centre), 0 where masked; the adjoint reads the saved quad (whose .x
+    // is f) and dL/dout instead
+    float4 nq[5];
+    float ng[5];
+    auto load_one = [&](int k, bool on, size_t q) {
+        if constexpr (MODE == ADJ) {
+            nq[k] = on ? __ldg(p.bsv + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+            ng[k] = on ? __ldg(p.gout + q) : 0.f;
+        } else {
+            nq[k].x = on ? __ldg(p.img + q) : 0.f;
+        }
+    };
+    auto load_step = [&](int tt) {
+        const int tau = tt - j;
+        const bool act = tau >= 0 && tau < span;
+        const int e = y0 - r + tau, l = e - 2 * r - 1, rho = e - r;
+        const bool in_e = act && e >= 0 && e < p.H;
+        const bool in_l = act && tau >= 2 * r + 1 && l >= 0 && l < p.H;
+        const bool out = act && tau >= 2 * r && out_lane;
+        load_one(0, in_e && own_in, (size_t)e * W + cw);
+        load_one(1, in_e && sec_in, (size_t)e * W + c2);
+        load_one(2, in_l && own_in, (size_t)l * W + cw);
+        load_one(3, in_l && sec_in, (size_t)l * W + c2);
+        load_one(4, out, (size_t)rho * W + co);
+    };
+    load_step(w * 32);  // a warp is first active at step 32 w
+    __syncthreads();
+
+    for (int t = 0; t < steps; ++t, [&] {
+#pragma unroll
+             for (int hb = 0; hb < BH; ++hb) {
+                 qe[hb] += qinc[hb];
+                 if (qe[hb] >= P) qe[hb] -= P;
+             }
+         }()) {
+        const int warp_first = t - (w * 32 + 31);
+        const int warp_last = t - w * 32;
+        if (warp_last >= 0 && warp_first < span) {
+            const int tau = t - j;
+            const bool act = tau >= 0 && tau < span;
+            const int e = y0 - r + tau;            // entering row
+            const int l = e - 2 * r - 1;           // leaving row
+            const int rho = e - r;                 // centre (output) row
+            const bool in_e = act && e >= 0 && e < p.H;
+            const bool in_l = act && tau >= 2 * r + 1 && l >= 0 && l < p.H;
+            const bool out = act && tau >= 2 * r && out_lane;
+            const bool m0 = in_e && own_in, m1 = in_e && sec_in;
+            const bool m2 = in_l && own_in, m3 = in_l && sec_in;
+            // this step's pixels were loaded during the previous step; start
+            // the loads of the next one so their latency hides under this step,
+            // and pull a later entering row into L2
+            float4 q[5];
+            float gq[5];
+#pragma unroll
+            for (int k = 0; k < 5; ++k) { q[k] = nq[k]; gq[k] = MODE == ADJ ? ng[k] : 0.f; }
+            const float fc = q[4].x;
+            load_step(t + 1);
+            {
+                const int ef = e + 8;
+                if (own_in && ef >= 0 && ef < p.H) {
+                    if constexpr (MODE == ADJ) {
+                        prefetch_l2(p.bsv + (size_t)ef * W + cw);
+                        prefetch_l2(p.gout + (size_t)ef * W + cw);
+                    } else {
+                        prefetch_l2(p.img + (size_t)ef * W + cw);
+                    }
+                }
+            }
+
+            // Z_k = sum_s u_s z_s(k) over the four streams with signs + own
+            // enter, -(-1)^M second enter, -(-1)^M own leave, + second leave
+            // (the leaving row's phase folded in): (u_g, u_h) = (f, 1) in the
+            // forward, (alpha, beta) in the adjoint
+            float zgx[KH], zgy[KH], zhx[KH], zhy[KH];
+#pragma unroll
+            for (int kk = 0; kk < KH; ++kk) { zgx[kk] = 0.f; zgy[kk] = 0.f; zhx[kk] = 0.f; zhy[kk] = 0.f; }
+            const float wsg[4] = {m0 ? 1.f : 0.f, m1 ? sgn2 : 0.f, m2 ? -lsg : 0.f,
+                                  m3 ? -sgn2 * lsg : 0.f};
+#pragma unroll
+            for (int s = 0; s < 4; ++s) {
+                float ug, uh;
+                if constexpr (MODE == ADJ) {
+                    const float al = gq[s] * q[s].y;
+                    ug = wsg[s] * al;
+                    uh = -ug * q[s].z;
+                } else {
+                    ug = wsg[s] * q[s].x;
+                    uh = wsg[s];
+                }
+                float2 z[KH];
+                range_harmonics<N>(q[s].x, p.gamma, z);
+#pragma unroll
+                for (int kk = 0; kk < KH; ++kk) {
+                    zgx[kk] = fmaf(ug, z[kk].x, zgx[kk]);
+                    zgy[kk] = fmaf(ug, z[kk].y, zgy[kk]);
+                    zhx[kk] = fmaf(uh, z[kk].x, zhx[kk]);
+                    zhy[kk] = fmaf(uh, z[kk].y, zhy[kk]);
+                }
+            }
+            // centre: f-side factors fk |k| z_c(k)
+            float2 zc[KH];
+            range_harmonics<N>(fc, p.gamma, zc);
+#pragma unroll
+            for (int kk = 0; kk < KH; ++kk) zc[kk] = make_float2(fkv[kk] * zc[kk].x, fkv[kk] * zc[kk].y);
+
+            // row phases of the entering row (vertical) and, times coef's
+            // b-factor, of the centre row (recombination), for signed b
+            Cx rp[NB], rc[NB];
+#pragma unroll
+            for (int hb = 0; hb < BH; ++hb) {
+                const int b = (M & 1) + 2 * hb;
+                const int ipos = (b + M) / 2, ineg = (M - b) / 2;
+                int qc = qe[hb] - qoff[hb];
+                if (qc < 0) qc += P;
+                const float2 sb = dup(fbv[hb]);
+                if (b == 0) {
+                    rp[ipos].v = make_float2(1.f, 0.f);
+                    rp[ipos].iv = make_float2(0.f, 1.f);
+                    rc[ipos].v = make_float2(fbv[hb], 0.f);
+                    rc[ipos].iv = make_float2(0.f, fbv[hb]);
+                } else {
+                    const float4 t1 = ptab[2 * qe[hb]], t2 = ptab[2 * qe[hb] + 1];
+                    const float4 u1 = ptab[2 * qc], u2 = ptab[2 * qc + 1];
+                    rp[ipos].v = make_float2(t1.x, t1.y); rp[ipos].iv = make_float2(t1.z, t1.w);
+                    rp[ineg].v = make_float2(t2.x, t2.y); rp[ineg].iv = make_float2(t2.z, t2.w);
+                    rc[ipos].v = __fmul2_rn(sb, make_float2(u1.x, u1.y));
+                    rc[ipos].iv = __fmul2_rn(sb, make_float2(u1.z, u1.w));
+                    rc[ineg].v = __fmul2_rn(sb, make_float2(u2.x, u2.y));
+                    rc[ineg].iv = __fmul2_rn(sb, make_float2(u2.z, u2.w));
+                }
+            }
+
+            const float4* rd = smem + ((t + 1) & 1) * BUF + j;
+            float4* wr = smem + (t & 1) * BUF + j + 1;
+            float2 NUM = make_float2(0.f, 0.f), DEN = NUM, DN = NUM, DD = NUM;
+            const float2 FC = dup(fc);
+            int c = 0;
+#pragma unroll
+            for (int ia = 0; ia < NA; ++ia) {
+                const int a = (M & 1) + 2 * ia;
+#pragma unroll
+                for (int ib = 0; ib < NB; ++ib) {
+                    // R = e^{i a gs cw} e^{i b gs e}, Q = coef's (a, b) factors times
+                    // e^{i a gs co} e^{i b gs rho}
+                    Cx R, Q;
+                    if (a == 0) {
+                        R = rp[ib];
+                        Q.v = __fmul2_rn(ox[ia], rc[ib].v);
+                        Q.iv = __fmul2_rn(ox[ia], rc[ib].iv);
+                    } else {
+                        R = crot(cx[ia], cy[ia], cyn[ia], rp[ib]);
+                        Q = crot(ox[ia], oy[ia], oyn[ia], rc[ib]);
+                    }
+#pragma unroll
+                    for (int ik = 0; ik < NK; ++ik) {
+                        const int d = ib * NK + ik;
+                        if (a == 0 && d < D::D0) continue;
+                        const int b = -M + 2 * ib;
+                        const int k = -N + 2 * ik;
+                        const int kk = (k < 0 ? -k : k) / 2;
+                        const bool neg = k < 0;
+                        // vertical: D'_c += R Z_k (Z_{-k} = conj Z_k)
+                        if (k == 0) {
+                            Dg[c] = __ffma2_rn(dup(zgx[kk]), R.v, Dg[c]);
+                            Dh[c] = __ffma2_rn(dup(zhx[kk]), R.v, Dh[c]);
+                        } else {
+                            Dg[c] = __ffma2_rn(dup(neg ? -zgy[kk] : zgy[kk]), R.iv,
+                                               __ffma2_rn(dup(zgx[kk]), R.v, Dg[c]));
+                            Dh[c] = __ffma2_rn(dup(neg ? -zhy[kk] : zhy[kk]), R.iv,
+                                               __ffma2_rn(dup(zhx[kk]), R.v, Dh[c]));
+                        }
+                        // horizontal hand-off
+                        const float4 A = rd[c * LD];
+                        const float2 hg = __fadd2_rn(make_float2(A.x, A.y), Dg[c]);
+                        const float2 hh = __fadd2_rn(make_float2(A.z, A.w), Dh[c]);
+                        wr[c * LD] = make_float4(hg.x, hg.y, hh.x, hh.y);
+                        // E = coef_c E_c(centre) = Q zc_k (conj for k < 0)
+                        float2 E;
+                        if (k == 0) {
+                            E = __fmul2_rn(dup(zc[kk].x), Q.v);
+                            if (a == 0 && b == 0) E = __fmul2_rn(dup(0.5f), E);  // self-conjugate
+                        } else {
+                            E = __ffma2_rn(dup(neg ? -zc[kk].y : zc[kk].y), Q.iv,
+                                           __fmul2_rn(dup(zc[kk].x), Q.v));
+                        }
+                        // Re(conj E h) = E . h; k Im(conj E h) = (-k E.y, k E.x) . h
+                        NUM = __ffma2_rn(E, hg, NUM);
+                        if constexpr (MODE != ADJ) {
+                            DEN = __ffma2_rn(E, hh, DEN);
+                            if constexpr (MODE == FWD_SAVE) {
+                                if (k != 0) {
+                                    const float2 Ek = make_float2(-(float)k * E.y, (float)k * E.x);
+                                    DN = __ffma2_rn(Ek, hg, DN);
+                                    DD = __ffma2_rn(Ek, hh, DD);
+                                }
+                            }
+                        } else {
+                            // hg = A_c = Sum(alpha E_c), hh = B_c = Sum(beta E_c)
+                            if (k != 0) {
+                                const float2 Ek = make_float2(-(float)k * E.y, (float)k * E.x);
+                                DEN = __ffma2_rn(Ek, __ffma2_rn(FC, hg, hh), DEN);
+                            }
+                        }
+                        ++c;
+                    }
+                }
+            }
+            if (out) {
+                const size_t o = (size_t)rho * W + co;
+                const float num = NUM.x + NUM.y, den = DEN.x + DEN.y;
+                if constexpr (MODE == ADJ) {
+                    // centre quad: (f, 1/den, out, X)
+                    const float al = gq[4] * q[4].y;
+                    p.gimg[o] = fmaf(p.gamma, fmaf(al, q[4].w, den), num);
+                } else {
+                    const float ov = num / den;
+                    p.out[o] = ov;
+                    if constexpr (MODE == FWD_SAVE) {
+                        const float dn = DN.x + DN.y, dd = DD.x + DD.y;
+                        p.sv[o] = make_float4(fc, 1.0f / den, ov, fmaf(-ov, dd, dn));
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+__device__ __forceinline__ float2 conj2(float2 a) { return make_float2(a.x, -a.y); }
+
+// Range harmonics z_k = e^{i k theta} for signed k = -N, ..., N (step 2), for
+// the plane-sum kernel.
+template <int N>
+__device__ __forceinline__ void range_harmonics_signed(float f, float gamma, float2 (&z)[N + 1]) {
     if constexpr (N == 0) {
         z[0] = make_float2(1.f, 0.f);
     } else {
@@ -107,9 +477,6 @@ __device__ __forceinline__ void range_harmonics(float f, float gamma, float2 (&z
     }
 }
 
-// Longest phase table: 2 (2r + 1) entries for r <= 56.
-constexpr int PTAB_CAP = 2 * (2 * 56 + 1);
-
 // Row phases e^{i b gs row} for signed b = -M, ..., M (step 2), from the
 // table tab[q] = e^{i pi q / (2r+1)} and the row's indices q[b] = b row mod
 // 2 (2r + 1) of the non-negative b (ib >= M / 2).
@@ -123,6 +490,10 @@ __device__ __forceinline__ void row_phases(const float2* tab, const int (&q)[M +
         if (-M + 2 * ib < 0) p[ib] = conj2(p[M - ib]);
 }
 
+// Plane-sum form: the vertical differences are kept per (b, k) plane
+// (e^{i b gs z2} e^{i k gamma f}, f-weighted and not) and rotated by each
+// combo's column phase e^{i a gs cw} in the horizontal hand-off. Cheaper than
+// the combo-sum form when many combos share a plane (no range kernel, M >= 2).
 // MODE = ADJ runs the same moving sums on the planes (alpha E_c, beta E_c),
 // alpha = g / den, beta = -alpha out (the window and the spatial kernel are
 // symmetric, so the adjoint's neighbour sums are again moving sums centred
@@ -133,7 +504,7 @@ __device__ __forceinline__ void row_phases(const float2* tab, const int (&q)[M +
 // forward (dnum_s = sum_c coef_c k_c Im(conj E_c S_c(f E)), the derivative of
 // num through the centre value, divided by gamma).
 template <int M, int N, int MODE>
-__global__ void __launch_bounds__(WMAX, 2) spk_kernel(Params p) {
+__global__ void __launch_bounds__(WMAX, 2) spk_plane_kernel(Params p) {
     using D = Dims<M, N>;
     constexpr int LD = WMAX + 1;
     constexpr int BUF = D::NS * LD;
@@ -166,7 +537,7 @@ __global__ void __launch_bounds__(WMAX, 2) spk_kernel(Params p) {
     }
     // phase indices b row mod P of the entering row (advanced by b per step)
     // and their offsets to the centre row rho = e - r
-    int qe[M + 1], qoff[M + 1];
+    int qe[M + 1], qoff[M + 1], qinc[M + 1];
 #pragma unroll
     for (int ib = 0; ib <= M; ++ib) {
         const int b = -M + 2 * ib;
@@ -175,6 +546,7 @@ __global__ void __launch_bounds__(WMAX, 2) spk_kernel(Params p) {
         if (q0 < 0) q0 += P;
         qe[ib] = q0;
         qoff[ib] = (bb * r) % P;
+        qinc[ib] = bb % P;  // b may exceed the period when r is small
     }
 
     // column phases e^{i a gs c} of the own and of the centre column
@@ -221,8 +593,10 @@ __global__ void __launch_bounds__(WMAX, 2) spk_kernel(Params p) {
     for (int t = 0; t < steps; ++t, [&] {
 #pragma unroll
              for (int ib = 0; ib <= M; ++ib) {
-                 const int b = -M + 2 * ib;
-                 if (b > 0) { qe[ib] += b; if (qe[ib] >= P) qe[ib] -= P; }
+                 if (-M + 2 * ib > 0) {
+                     qe[ib] += qinc[ib];
+                     if (qe[ib] >= P) qe[ib] -= P;
+                 }
              }
          }()) {
         const int warp_first = t - (w * 32 + 31);
@@ -255,7 +629,7 @@ __global__ void __launch_bounds__(WMAX, 2) spk_kernel(Params p) {
             // plane weights: (f, 1) in the forward, (alpha, beta) in the adjoint
             auto accumulate = [&](int k, float wgt, float rsg) {
                 float2 z[N + 1];
-                range_harmonics<N>(q[k].x, p.gamma, z);
+                range_harmonics_signed<N>(q[k].x, p.gamma, z);
                 float ug, uh;
                 if constexpr (MODE == ADJ) {
                     const float al = gq[k] * q[k].y;
@@ -298,7 +672,7 @@ __global__ void __launch_bounds__(WMAX, 2) spk_kernel(Params p) {
                 row_phases<M>(ptab, qc, rpc);
             }
             float2 zc[N + 1];
-            range_harmonics<N>(fc, p.gamma, zc);
+            range_harmonics_signed<N>(fc, p.gamma, zc);
             const float4* rd = smem + ((t + 1) & 1) * BUF + j;
             float4* wr = smem + (t & 1) * BUF + j + 1;
             float num = 0.f, den = 0.f, dn = 0.f, dd = 0.f;
@@ -352,27 +726,44 @@ __global__ void __launch_bounds__(WMAX, 2) spk_kernel(Params p) {
     }
 }
 
+
+// Combo-sum form (one complex FMA per combo and step) while the combos are
+// at most 1.6 times the (b, k) planes; the plane-sum form above otherwise,
+// whose per-step cost grows with the planes and whose hand-off rotations
+// replace the per-(a, b) phase products.
+template <int M, int N>
+constexpr bool use_combo_sum() {
+    return 5 * Dims<M, N>::NS <= 8 * Dims<M, N>::ND;
+}
+
 template <int M, int N>
 static cudaError_t launch(const Params& p, int mode, int gx, int gy, cudaStream_t s) {
     using D = Dims<M, N>;
     static_assert(D::NS <= NS_CAP, "combo table");
-    auto kern = mode == ADJ ? spk_kernel<M, N, ADJ>
-                            : (mode == FWD_SAVE ? spk_kernel<M, N, FWD_SAVE> : spk_kernel<M, N, FWD>);
-    const size_t smem = sizeof(float4) * 2 * (size_t)D::NS * (WMAX + 1) +
-                        sizeof(float2) * PTAB_CAP;
+    static_assert(D::NA <= FCAP && M / 2 + 1 <= FCAP && N / 2 + 1 <= FCAP, "factor tables");
+    void (*kern)(Params);
+    size_t smem;
+    if constexpr (use_combo_sum<M, N>()) {
+        kern = mode == ADJ ? spk_kernel<M, N, ADJ>
+                           : (mode == FWD_SAVE ? spk_kernel<M, N, FWD_SAVE> : spk_kernel<M, N, FWD>);
+        smem = sizeof(float4) * (2 * (size_t)D::NS * (WMAX + 1) + 2 * (size_t)PTAB_CAP);
+    } else {
+        kern = mode == ADJ ? spk_plane_kernel<M, N, ADJ>
+                           : (mode == FWD_SAVE ? spk_plane_kernel<M, N, FWD_SAVE>
+                                               : spk_plane_kernel<M, N, FWD>);
+        smem = sizeof(float4) * 2 * (size_t)D::NS * (WMAX + 1) + sizeof(float2) * PTAB_CAP;
+    }
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<dim3(gx, gy), WMAX, smem, s>>>(p);
     return cudaGetLastError();
 }
-
 // Combo order and coefficients, as the kernel enumerates them:
 // coef_c = 1/4 beta_a beta_|b| alpha_|k| m_b m_k (m = 2 for b = 0, k = 0:
 // both sign choices give the same term), doubled for a = 0 except the
-// self-conjugate (0, 0, 0); ck_c = coef_c k_c with the combo's signed k.
-static int combo_coefs(int M, int N, const double* beta, const double* alpha, float* coef,
-                       float* ck) {
+// self-conjugate (0, 0, 0). Returns the combo count, or -1.
+static int combo_coefs(int M, int N, const double* beta, const double* alpha, double* coef) {
     const int NB = M + 1, NK = N + 1, ND = NB * NK, D0 = ND - (ND + 1) / 2;
     int c = 0;
     for (int ia = 0; ia <= M / 2; ++ia) {
@@ -387,12 +778,45 @@ static int combo_coefs(int M, int N, const double* beta, const double* alpha, fl
             if (k == 0) v *= 2.0;
             if (a == 0 && !(b == 0 && k == 0)) v *= 2.0;
             if (c >= NS_CAP) return -1;
-            coef[c] = (float)v;
-            ck[c] = (float)(v * (double)k);
-            ++c;
+            coef[c++] = v;
         }
     }
     return c;
+}
+
+// The combo-sum kernel's factors fa, fb, fk of coef_c, checked against every
+// combo's coefficient (with the self-conjugate combo halved), and the
+// plane-sum kernel's per-combo coef_c and coef_c k_c.
+static bool combo_factors(int M, int N, const double* beta, const double* alpha, Params* p) {
+    if (M / 2 + 1 > FCAP || N / 2 + 1 > FCAP) return false;
+    for (int i = 0; i <= M / 2; ++i) {
+        const int a = (M & 1) + 2 * i;
+        p->fa[i] = (float)(beta[i] * (a == 0 ? 2.0 : 1.0));
+        p->fb[i] = (float)(0.25 * beta[i] * (a == 0 ? 2.0 : 1.0));
+    }
+    for (int i = 0; i <= N / 2; ++i) {
+        const int k = (N & 1) + 2 * i;
+        p->fk[i] = (float)(alpha[i] * (k == 0 ? 2.0 : 1.0));
+    }
+    double coef[NS_CAP];
+    if (combo_coefs(M, N, beta, alpha, coef) < 0) return false;
+    const int NB = M + 1, NK = N + 1, ND = NB * NK, D0 = ND - (ND + 1) / 2;
+    int c = 0;
+    for (int ia = 0; ia <= M / 2; ++ia) {
+        const int a = (M & 1) + 2 * ia;
+        for (int d = 0; d < ND; ++d) {
+            if (a == 0 && d < D0) continue;
+            const int b = -M + 2 * (d / NK), k = -N + 2 * (d % NK);
+            const int ab = b < 0 ? -b : b, ak = k < 0 ? -k : k;
+            double v = (double)p->fa[ia] * p->fb[(ab - (M & 1)) / 2] * p->fk[(ak - (N & 1)) / 2];
+            if (a == 0 && b == 0 && k == 0) v *= 0.5;
+            if (fabs(v - coef[c]) > 1e-6 * fabs(coef[c]) + 1e-30) return false;
+            p->coef[c] = (float)coef[c];
+            p->ck[c] = (float)(coef[c] * (double)k);
+            ++c;
+        }
+    }
+    return true;
 }
 
 static bool supported(int M, int N) {
@@ -442,7 +866,7 @@ static bf_status prepare(int H, int W, int r, int M, float sigma_r, float T, int
     if (bf_coeffs(M, beta, BF_N_MAX / 2 + 1) < 0 || bf_coeffs(*N, alpha, BF_N_MAX / 2 + 1) < 0)
         return BF_ERR_INTERNAL;
     memset(p, 0, sizeof(*p));
-    if (combo_coefs(M, *N, beta, alpha, p->coef, p->ck) < 0) return BF_ERR_INTERNAL;
+    if (!combo_factors(M, *N, beta, alpha, p)) return BF_ERR_INTERNAL;
     p->H = H; p->W = W; p->r = r;
     p->gamma = (float)gamma;
     p->Tw = WMAX - 2 * r;
@@ -476,6 +900,19 @@ static cudaError_t dispatch(const Params& p, int mode, int M, int N, int gx, int
     return cudaErrorInvalidValue;
 }
 
+// r = 0: a 1 x 1 window weighs the centre alone, so out = f, and the saved
+// quad is (f, 1/den = 1, out = f, X = 0): q_M(0) = q_N(0) = 1 and the range
+// kernel's slope at 0 is 0. (The strip engine's hand-off would telescope over
+// all lanes with signed terms here and lose digits to no purpose.)
+__global__ void r0_quads(const float* img, float* out, float4* sv, size_t n) {
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += stride) {
+        const float f = img[i];
+        out[i] = f;
+        sv[i] = make_float4(f, 1.f, f, 0.f);
+    }
+}
+
 }  // namespace spk
 }  // namespace bf
 
@@ -497,10 +934,19 @@ extern "C" bf_status bf_spatial_forward(const void* img, int H, int W, int r, in
     p.out = out;
     p.sv = static_cast<float4*>(saved);
     const int mode = saved ? spk::FWD_SAVE : spk::FWD;
-    if (r == 0 && !saved) {
+    if (r == 0) {
         // a 1 x 1 window: every kernel weighs the centre alone, out = f
-        cudaError_t e = cudaMemcpyAsync(out, img, sizeof(float) * (size_t)H * W,
-                                        cudaMemcpyDeviceToDevice, s);
+        cudaError_t e;
+        if (!saved) {
+            e = cudaMemcpyAsync(out, img, sizeof(float) * (size_t)H * W, cudaMemcpyDeviceToDevice,
+                                s);
+        } else {
+            const size_t n = (size_t)H * W;
+            const size_t want = (n + 255) / 256, cap = (size_t)8 * sm_count();
+            spk::r0_quads<<<(unsigned)(want < cap ? want : cap), 256, 0, s>>>(
+                static_cast<const float*>(img), out, static_cast<float4*>(saved), n);
+            e = cudaGetLastError();
+        }
         return e == cudaSuccess ? BF_OK : set_cuda_error(e);
     }
     cudaError_t e = spk::dispatch(p, mode, M, N, gx, gy, s);
@@ -517,6 +963,12 @@ extern "C" bf_status bf_spatial_backward(const float* grad_out, const void* save
     int gx = 0, gy = 0;
     bf_status st = spk::prepare(H, W, r, M, sigma_r, T, &N, opts, &p, &gx, &gy);
     if (st != BF_OK) return st;
+    if (r == 0) {
+        // 1 x 1 window: out = f, so dL/df = dL/dout
+        cudaError_t e = cudaMemcpyAsync(grad_img, grad_out, sizeof(float) * (size_t)H * W,
+                                        cudaMemcpyDeviceToDevice, (cudaStream_t)stream);
+        return e == cudaSuccess ? BF_OK : set_cuda_error(e);
+    }
     p.bsv = static_cast<const float4*>(saved);
     p.gout = grad_out;
     p.gimg = grad_img;

@@ -70,6 +70,31 @@ def test_edges_and_ragged_tiles(cuda_lib, H, W, r):
     assert rel_err(got, ref(f, r, 2, 4)).max() <= TOL
 
 
+@pytest.mark.parametrize("M,N,r", [(8, 0, 1), (6, 0, 1), (8, 0, 2), (4, 0, 0), (2, 4, 0),
+                                   (2, 4, 1), (1, 3, 1)])
+def test_short_phase_period(cuda_lib, M, N, r):
+    """Small windows, whose phase period 2 (2r + 1) can be shorter than the
+    spatial harmonic b. r = 0: a 1 x 1 window weighs the centre alone, so out =
+    f, the saved quad is (f, 1, f, 0) and the adjoint returns dL/dout."""
+    bf = cuda_lib
+    f = synth.sinusoids(70, 300, seed=M + r)
+    ft = torch.from_numpy(f).cuda()
+    sv = torch.empty((70, 300, 4), device="cuda")
+    got = bf.bf_spatial_forward(ft, r, M, 0.0, 1.0, N, saved=sv)
+    torch.cuda.synchronize()
+    want = ref(f, r, M, N)
+    assert rel_err(got.cpu().numpy(), want).max() <= TOL
+    s = sv.cpu().numpy()
+    assert np.array_equal(s[..., 0], f) and np.allclose(s[..., 2], got.cpu().numpy())
+    if r == 0:
+        assert np.array_equal(got.cpu().numpy(), f)
+        assert np.array_equal(s, np.stack([f, np.ones_like(f), f, np.zeros_like(f)], -1))
+        g = torch.from_numpy(synth.weights((70, 300), seed=3)).cuda()
+        gi = bf.bf_spatial_backward(g, sv, r, M, 0.0, 1.0, N)
+        torch.cuda.synchronize()
+        assert torch.equal(gi, g)
+
+
 def test_rejects_unbuilt_orders(cuda_lib):
     bf = cuda_lib
     f = torch.zeros((8, 8), device="cuda")
