@@ -144,14 +144,20 @@ __device__ __forceinline__ void prefetch_l2(const void* ptr) {
 // combo the column-rotated vertical difference D'_c += e^{i a gs cw} e^{i b gs
 // e} Z_k, the horizontal hand-off S_c = S_c(left) + D'_c, and the centre's
 // coef_c conj(E_c) S_c, all on (re, im) register pairs.
-template <int M, int N, int MODE>
+//
+// The adjoint is linear in the combo sums, so it may run as launches over
+// consecutive combo ranges [C0, C1) (fewer live sums per launch); a launch
+// with C0 > 0 adds its part to dL/df.
+template <int M, int N, int MODE, int C0 = 0, int C1 = Dims<M, N>::NS>
 __global__ void __launch_bounds__(WMAX, 2) spk_kernel(Params p) {
     using D = Dims<M, N>;
+    static_assert(0 <= C0 && C0 < C1 && C1 <= D::NS, "combo range");
+    static_assert(MODE == ADJ || (C0 == 0 && C1 == D::NS), "forward runs all combos");
     constexpr int NA = D::NA, NB = D::NB, NK = D::NK;
     constexpr int KH = N / 2 + 1;        // non-negative range harmonics
     constexpr int BH = M / 2 + 1;        // non-negative spatial harmonics |b|
     constexpr int LD = WMAX + 1;
-    constexpr int BUF = D::NS * LD;
+    constexpr int BUF = (C1 - C0) * LD;
     extern __shared__ float4 smem[];  // [2][NS][LD]: (g.re, g.im, h.re, h.im), then the table
     const int Wi = blockDim.x;
     const int j = threadIdx.x;
@@ -186,7 +192,7 @@ __global__ void __launch_bounds__(WMAX, 2) spk_kernel(Params p) {
     }
     // phase indices b e mod P of the entering row e (b > 0, advanced by b per
     // step) and their offsets b r to the centre row rho = e - r
-    int qe[BH], qoff[BH], qinc[BH];
+    int qe[BH], qoff[BH];
 #pragma unroll
     for (int hb = 0; hb < BH; ++hb) {
         const int b = (M & 1) + 2 * hb;
@@ -194,7 +200,6 @@ __global__ void __launch_bounds__(WMAX, 2) spk_kernel(Params p) {
         if (q0 < 0) q0 += P;
         qe[hb] = q0;
         qoff[hb] = (b * r) % P;
-        qinc[hb] = b % P;  // b may exceed the period when r is small
     }
 
     // column phases: e^{i a gs cw} of the own column, and coef's a-factor times
@@ -225,6 +230,7 @@ __global__ void __launch_bounds__(WMAX, 2) spk_kernel(Params p) {
     // is f) and dL/dout instead
     float4 nq[5];
     float ng[5];
+    float npart = 0.f;  // adjoint over a later combo range: the earlier ranges' dL/df
     auto load_one = [&](int k, bool on, size_t q) {
         if constexpr (MODE == ADJ) {
             nq[k] = on ? __ldg(p.bsv + q) : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -245,6 +251,7 @@ __global__ void __launch_bounds__(WMAX, 2) spk_kernel(Params p) {
         load_one(2, in_l && own_in, (size_t)l * W + cw);
         load_one(3, in_l && sec_in, (size_t)l * W + c2);
         load_one(4, out, (size_t)rho * W + co);
+        if constexpr (MODE == ADJ && C0 > 0) npart = out ? p.gimg[(size_t)rho * W + co] : 0.f;
     };
     load_step(w * 32);  // a warp is first active at step 32 w
     __syncthreads();
@@ -252,8 +259,12 @@ __global__ void __launch_bounds__(WMAX, 2) spk_kernel(Params p) {
     for (int t = 0; t < steps; ++t, [&] {
 #pragma unroll
              for (int hb = 0; hb < BH; ++hb) {
-                 qe[hb] += qinc[hb];
+                 // P >= 6 (r >= 1): one wrap, two when b = 8 > P
+                 qe[hb] += (M & 1) + 2 * hb;
                  if (qe[hb] >= P) qe[hb] -= P;
+                 if constexpr (M > 6) {
+                     if (qe[hb] >= P) qe[hb] -= P;
+                 }
              }
          }()) {
         const int warp_first = t - (w * 32 + 31);
@@ -276,6 +287,7 @@ __global__ void __launch_bounds__(WMAX, 2) spk_kernel(Params p) {
             float gq[5];
 #pragma unroll
             for (int k = 0; k < 5; ++k) { q[k] = nq[k]; gq[k] = MODE == ADJ ? ng[k] : 0.f; }
+            const float part = npart;
             const float fc = q[4].x;
             load_step(t + 1);
             {
@@ -357,7 +369,7 @@ __global__ void __launch_bounds__(WMAX, 2) spk_kernel(Params p) {
             float4* wr = smem + (t & 1) * BUF + j + 1;
             float2 NUM = make_float2(0.f, 0.f), DEN = NUM, DN = NUM, DD = NUM;
             const float2 FC = dup(fc);
-            int c = 0;
+            int cn = 0;  // combo index
 #pragma unroll
             for (int ia = 0; ia < NA; ++ia) {
                 const int a = (M & 1) + 2 * ia;
@@ -378,6 +390,8 @@ __global__ void __launch_bounds__(WMAX, 2) spk_kernel(Params p) {
                     for (int ik = 0; ik < NK; ++ik) {
                         const int d = ib * NK + ik;
                         if (a == 0 && d < D::D0) continue;
+                        const int c = cn++;
+                        if (c < C0 || c >= C1) continue;
                         const int b = -M + 2 * ib;
                         const int k = -N + 2 * ik;
                         const int kk = (k < 0 ? -k : k) / 2;
@@ -393,10 +407,10 @@ __global__ void __launch_bounds__(WMAX, 2) spk_kernel(Params p) {
                                                __ffma2_rn(dup(zhx[kk]), R.v, Dh[c]));
                         }
                         // horizontal hand-off
-                        const float4 A = rd[c * LD];
+                        const float4 A = rd[(c - C0) * LD];
                         const float2 hg = __fadd2_rn(make_float2(A.x, A.y), Dg[c]);
                         const float2 hh = __fadd2_rn(make_float2(A.z, A.w), Dh[c]);
-                        wr[c * LD] = make_float4(hg.x, hg.y, hh.x, hh.y);
+                        wr[(c - C0) * LD] = make_float4(hg.x, hg.y, hh.x, hh.y);
                         // E = coef_c E_c(centre) = Q zc_k (conj for k < 0)
                         float2 E;
                         if (k == 0) {
@@ -424,7 +438,6 @@ __global__ void __launch_bounds__(WMAX, 2) spk_kernel(Params p) {
                                 DEN = __ffma2_rn(Ek, __ffma2_rn(FC, hg, hh), DEN);
                             }
                         }
-                        ++c;
                     }
                 }
             }
@@ -433,8 +446,12 @@ __global__ void __launch_bounds__(WMAX, 2) spk_kernel(Params p) {
                 const float num = NUM.x + NUM.y, den = DEN.x + DEN.y;
                 if constexpr (MODE == ADJ) {
                     // centre quad: (f, 1/den, out, X)
-                    const float al = gq[4] * q[4].y;
-                    p.gimg[o] = fmaf(p.gamma, fmaf(al, q[4].w, den), num);
+                    if constexpr (C0 == 0) {
+                        const float al = gq[4] * q[4].y;
+                        p.gimg[o] = fmaf(p.gamma, fmaf(al, q[4].w, den), num);
+                    } else {
+                        p.gimg[o] = part + fmaf(p.gamma, den, num);
+                    }
                 } else {
                     const float ov = num / den;
                     p.out[o] = ov;
@@ -537,7 +554,7 @@ __global__ void __launch_bounds__(WMAX, 2) spk_plane_kernel(Params p) {
     }
     // phase indices b row mod P of the entering row (advanced by b per step)
     // and their offsets to the centre row rho = e - r
-    int qe[M + 1], qoff[M + 1], qinc[M + 1];
+    int qe[M + 1], qoff[M + 1];
 #pragma unroll
     for (int ib = 0; ib <= M; ++ib) {
         const int b = -M + 2 * ib;
@@ -546,7 +563,6 @@ __global__ void __launch_bounds__(WMAX, 2) spk_plane_kernel(Params p) {
         if (q0 < 0) q0 += P;
         qe[ib] = q0;
         qoff[ib] = (bb * r) % P;
-        qinc[ib] = bb % P;  // b may exceed the period when r is small
     }
 
     // column phases e^{i a gs c} of the own and of the centre column
@@ -593,9 +609,14 @@ __global__ void __launch_bounds__(WMAX, 2) spk_plane_kernel(Params p) {
     for (int t = 0; t < steps; ++t, [&] {
 #pragma unroll
              for (int ib = 0; ib <= M; ++ib) {
-                 if (-M + 2 * ib > 0) {
-                     qe[ib] += qinc[ib];
+                 const int b = -M + 2 * ib;
+                 if (b > 0) {
+                     // P >= 6 (r >= 1): one wrap, two when b = 8 > P
+                     qe[ib] += b;
                      if (qe[ib] >= P) qe[ib] -= P;
+                     if constexpr (M > 6) {
+                         if (qe[ib] >= P) qe[ib] -= P;
+                     }
                  }
              }
          }()) {
@@ -736,29 +757,56 @@ constexpr bool use_combo_sum() {
     return 5 * Dims<M, N>::NS <= 8 * Dims<M, N>::ND;
 }
 
-template <int M, int N>
-static cudaError_t launch(const Params& p, int mode, int gx, int gy, cudaStream_t s) {
-    using D = Dims<M, N>;
-    static_assert(D::NS <= NS_CAP, "combo table");
-    static_assert(D::NA <= FCAP && M / 2 + 1 <= FCAP && N / 2 + 1 <= FCAP, "factor tables");
-    void (*kern)(Params);
-    size_t smem;
-    if constexpr (use_combo_sum<M, N>()) {
-        kern = mode == ADJ ? spk_kernel<M, N, ADJ>
-                           : (mode == FWD_SAVE ? spk_kernel<M, N, FWD_SAVE> : spk_kernel<M, N, FWD>);
-        smem = sizeof(float4) * (2 * (size_t)D::NS * (WMAX + 1) + 2 * (size_t)PTAB_CAP);
-    } else {
-        kern = mode == ADJ ? spk_plane_kernel<M, N, ADJ>
-                           : (mode == FWD_SAVE ? spk_plane_kernel<M, N, FWD_SAVE>
-                                               : spk_plane_kernel<M, N, FWD>);
-        smem = sizeof(float4) * 2 * (size_t)D::NS * (WMAX + 1) + sizeof(float2) * PTAB_CAP;
-    }
+template <typename K>
+static cudaError_t launch_one(K kern, size_t smem, const Params& p, int gx, int gy, cudaStream_t s) {
+    if (p.r < 1) return cudaErrorInvalidValue;  // r = 0 has its closed form
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<dim3(gx, gy), WMAX, smem, s>>>(p);
     return cudaGetLastError();
 }
+
+// Combo-sum adjoints with 18 or more combos run as two launches over halves of
+// the combos: half the live sums and hand-off rows per launch leave the
+// registers to keep the next step's pixel loads in flight.
+template <int M, int N>
+constexpr int adjoint_split() {
+    return Dims<M, N>::NS >= 18 ? (Dims<M, N>::NS + 1) / 2 : Dims<M, N>::NS;
+}
+
+template <int M, int N>
+static cudaError_t launch(const Params& p, int mode, int gx, int gy, cudaStream_t s) {
+    using D = Dims<M, N>;
+    static_assert(D::NS <= NS_CAP, "combo table");
+    static_assert(D::NA <= FCAP && M / 2 + 1 <= FCAP && N / 2 + 1 <= FCAP, "factor tables");
+    const size_t tab = sizeof(float4) * 2 * (size_t)PTAB_CAP;
+    if constexpr (use_combo_sum<M, N>()) {
+        if (mode == FWD || mode == FWD_SAVE) {
+            const size_t smem = sizeof(float4) * 2 * (size_t)D::NS * (WMAX + 1) + tab;
+            return mode == FWD_SAVE ? launch_one(spk_kernel<M, N, FWD_SAVE>, smem, p, gx, gy, s)
+                                    : launch_one(spk_kernel<M, N, FWD>, smem, p, gx, gy, s);
+        }
+        constexpr int H = adjoint_split<M, N>();
+        cudaError_t e = launch_one(spk_kernel<M, N, ADJ, 0, H>,
+                                   sizeof(float4) * 2 * (size_t)H * (WMAX + 1) + tab, p, gx, gy, s);
+        if constexpr (H < D::NS) {
+            if (e == cudaSuccess)
+                e = launch_one(spk_kernel<M, N, ADJ, H, D::NS>,
+                               sizeof(float4) * 2 * (size_t)(D::NS - H) * (WMAX + 1) + tab, p, gx,
+                               gy, s);
+        }
+        return e;
+    } else {
+        const size_t smem =
+            sizeof(float4) * 2 * (size_t)D::NS * (WMAX + 1) + sizeof(float2) * PTAB_CAP;
+        auto kern = mode == ADJ ? spk_plane_kernel<M, N, ADJ>
+                                : (mode == FWD_SAVE ? spk_plane_kernel<M, N, FWD_SAVE>
+                                                    : spk_plane_kernel<M, N, FWD>);
+        return launch_one(kern, smem, p, gx, gy, s);
+    }
+}
+
 // Combo order and coefficients, as the kernel enumerates them:
 // coef_c = 1/4 beta_a beta_|b| alpha_|k| m_b m_k (m = 2 for b = 0, k = 0:
 // both sign choices give the same term), doubled for a = 0 except the
