@@ -19,6 +19,7 @@
 #include <string.h>
 
 #include "bf_internal.cuh"
+#include "bf_launch.cuh"
 
 namespace bf {
 namespace poly {
@@ -228,7 +229,12 @@ static cudaError_t launch(const Params& p, int mode, int gx, int gy, cudaStream_
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<dim3(gx, gy), WMAX, smem, s>>>(p);
+    Params q = p;
+    // the adjoint (five saved quads per step) runs best at two CTAs per SM
+    if (q.Hb <= 0)
+        q.Hb = wave_band_rows((const void*)kern, WMAX, smem, q.H, gx, mode == ADJ ? 2 : 0);
+    gy = (q.H + q.Hb - 1) / q.Hb;
+    kern<<<dim3(gx, gy), WMAX, smem, s>>>(q);
     return cudaGetLastError();
 }
 
@@ -281,18 +287,10 @@ static bf_status prepare(int H, int W, int r, float sigma_r, float T, int* N,
     p->invT = 1.0f / T;
     p->Tw = WMAX - 2 * r;
     *gx = (W + p->Tw - 1) / p->Tw;
-    int hb;
-    if (opts && opts->tile_h > 0) {
-        hb = opts->tile_h;
-    } else {
-        // one wave of resident CTAs (two per SM)
-        int nb = 2 * sm_count() / *gx;
-        if (nb < 1) nb = 1;
-        hb = (H + nb - 1) / nb;
-        if (hb < 32) hb = 32;
-    }
-    p->Hb = hb;
-    *gy = (H + hb - 1) / hb;
+    // band height: the caller's, else (0) one wave of the launched kernel's
+    // resident CTAs, chosen at launch
+    p->Hb = (opts && opts->tile_h > 0) ? opts->tile_h : 0;
+    *gy = 0;
     return BF_OK;
 }
 

@@ -30,6 +30,7 @@
 #include <string.h>
 
 #include "bf_internal.cuh"
+#include "bf_launch.cuh"
 
 namespace bf {
 namespace spk {
@@ -758,12 +759,17 @@ constexpr bool use_combo_sum() {
 }
 
 template <typename K>
-static cudaError_t launch_one(K kern, size_t smem, const Params& p, int gx, int gy, cudaStream_t s) {
+static cudaError_t launch_one(K kern, size_t smem, const Params& p, int gx, bool adj,
+                              cudaStream_t s) {
     if (p.r < 1) return cudaErrorInvalidValue;  // r = 0 has its closed form
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<dim3(gx, gy), WMAX, smem, s>>>(p);
+    Params q = p;
+    // the adjoint (five saved quads per step) runs best at two CTAs per SM
+    if (q.Hb <= 0) q.Hb = wave_band_rows((const void*)kern, WMAX, smem, q.H, gx, adj ? 2 : 0);
+    const int gy = (q.H + q.Hb - 1) / q.Hb;
+    kern<<<dim3(gx, gy), WMAX, smem, s>>>(q);
     return cudaGetLastError();
 }
 
@@ -784,17 +790,19 @@ static cudaError_t launch(const Params& p, int mode, int gx, int gy, cudaStream_
     if constexpr (use_combo_sum<M, N>()) {
         if (mode == FWD || mode == FWD_SAVE) {
             const size_t smem = sizeof(float4) * 2 * (size_t)D::NS * (WMAX + 1) + tab;
-            return mode == FWD_SAVE ? launch_one(spk_kernel<M, N, FWD_SAVE>, smem, p, gx, gy, s)
-                                    : launch_one(spk_kernel<M, N, FWD>, smem, p, gx, gy, s);
+            return mode == FWD_SAVE
+                       ? launch_one(spk_kernel<M, N, FWD_SAVE>, smem, p, gx, false, s)
+                       : launch_one(spk_kernel<M, N, FWD>, smem, p, gx, false, s);
         }
         constexpr int H = adjoint_split<M, N>();
         cudaError_t e = launch_one(spk_kernel<M, N, ADJ, 0, H>,
-                                   sizeof(float4) * 2 * (size_t)H * (WMAX + 1) + tab, p, gx, gy, s);
+                                   sizeof(float4) * 2 * (size_t)H * (WMAX + 1) + tab, p, gx, true,
+                                   s);
         if constexpr (H < D::NS) {
             if (e == cudaSuccess)
                 e = launch_one(spk_kernel<M, N, ADJ, H, D::NS>,
                                sizeof(float4) * 2 * (size_t)(D::NS - H) * (WMAX + 1) + tab, p, gx,
-                               gy, s);
+                               true, s);
         }
         return e;
     } else {
@@ -803,7 +811,7 @@ static cudaError_t launch(const Params& p, int mode, int gx, int gy, cudaStream_
         auto kern = mode == ADJ ? spk_plane_kernel<M, N, ADJ>
                                 : (mode == FWD_SAVE ? spk_plane_kernel<M, N, FWD_SAVE>
                                                     : spk_plane_kernel<M, N, FWD>);
-        return launch_one(kern, smem, p, gx, gy, s);
+        return launch_one(kern, smem, p, gx, mode == ADJ, s);
     }
 }
 
@@ -919,19 +927,10 @@ static bf_status prepare(int H, int W, int r, int M, float sigma_r, float T, int
     p->gamma = (float)gamma;
     p->Tw = WMAX - 2 * r;
     *gx = (W + p->Tw - 1) / p->Tw;
-    int hb;
-    if (opts && opts->tile_h > 0) {
-        hb = opts->tile_h;
-    } else {
-        // one wave of resident CTAs: at most 2 per SM (rounding the band count
-        // up would start a second, nearly empty wave)
-        int nb = 2 * sm_count() / *gx;
-        if (nb < 1) nb = 1;
-        hb = (H + nb - 1) / nb;
-        if (hb < 32) hb = 32;
-    }
-    p->Hb = hb;
-    *gy = (H + hb - 1) / hb;
+    // band height: the caller's, else (0) one wave of the launched kernel's
+    // resident CTAs, chosen at launch
+    p->Hb = (opts && opts->tile_h > 0) ? opts->tile_h : 0;
+    *gy = 0;
     return BF_OK;
 }
 

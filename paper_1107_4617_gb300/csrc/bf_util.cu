@@ -1,9 +1,11 @@
 // bf_check_range: min and max of an image, so a caller can check the filter's
 // precondition that all values lie in an interval of length T (Sec. 3: the
-// range kernel is a valid kernel on [-T, T] only).
+// range kernel is a valid kernel on [-T, T] only). Also the variants' band
+// height rule.
 #include <math.h>
 
 #include "bf_internal.cuh"
+#include "bf_launch.cuh"
 
 namespace bf {
 namespace util {
@@ -67,6 +69,19 @@ __global__ void finish_kernel(int* keys) {
 }
 
 }  // namespace util
+
+int wave_band_rows(const void* kern, int threads, size_t smem, int H, int gx, int max_per_sm) {
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem) != cudaSuccess ||
+        occ < 1)
+        occ = 1;
+    if (max_per_sm > 0 && occ > max_per_sm) occ = max_per_sm;
+    int nb = occ * sm_count() / (gx > 0 ? gx : 1);  // rounding up would start a second wave
+    if (nb < 1) nb = 1;
+    int hb = (H + nb - 1) / nb;
+    return hb < 32 ? 32 : hb;
+}
+
 }  // namespace bf
 
 using namespace bf;
