@@ -259,11 +259,14 @@ bf_status bf_backward_noalloc(const void* img, const float* out, const float* gr
  *   img, out  device H x W FP32 (out must not alias img).
  *   M         1..4, 6 or 8 when N = 0; 1 or 2 when 1 <= N <= 4.
  *   r         0..56.
- *   opts      NULL or defaults; tile_h is honoured; BF16 input, Kahan,
- *             trunc_tol and BF_GAMMA_FROM_SIGMA give BF_ERR_UNSUPPORTED.
+ *   opts      NULL or defaults; tile_h (rows per band) is honoured, else the
+ *             band height fills one wave of the launched kernel's resident
+ *             CTAs; BF16 input, Kahan, trunc_tol and BF_GAMMA_FROM_SIGMA give
+ *             BF_ERR_UNSUPPORTED.
  *   saved     NULL, or device buffer of bf_saved_bytes(H, W) (16-byte aligned)
  *             receiving the quads (f, 1/den, out, dnum_s - out dden_s) for
  *             bf_spatial_backward.
+ * r = 0 (a 1 x 1 window) is exact: out = img, saved quads (f, 1, f, 0).
  * Errors: BF_ERR_INVALID_ARG, BF_ERR_UNSUPPORTED (other M, N, r), BF_ERR_CUDA.
  */
 bf_status bf_spatial_forward(const void* img, int H, int W, int r, int M, float sigma_r, float T,
@@ -279,7 +282,9 @@ bf_status bf_spatial_forward(const void* img, int H, int W, int r, int M, float 
  *   saved     the quads bf_spatial_forward wrote (device, bf_saved_bytes(H, W)).
  *   grad_img  device H x W FP32 output.
  * Same H, W, r, M, sigma_r, T, N, opts as the forward. The range frequency is
- * fixed (gamma = pi / (2T)), so dL/dsigma_r is 0 and not computed.
+ * fixed (gamma = pi / (2T)), so dL/dsigma_r is 0 and not computed. Runs as one
+ * or (with 18 or more combos) two launches on `stream`; grad_img must not
+ * alias grad_out or saved. r = 0: grad_img = grad_out.
  * Errors: as bf_spatial_forward.
  */
 bf_status bf_spatial_backward(const float* grad_out, const void* saved, int H, int W, int r, int M,

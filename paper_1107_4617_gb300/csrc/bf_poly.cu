@@ -354,6 +354,9 @@ extern "C" bf_status bf_poly_backward(const float* grad_out, const void* saved, 
                                       const bf_opts* opts, void* stream) {
     if (!grad_out || !saved || !grad_img) return BF_ERR_INVALID_ARG;
     if ((uintptr_t)saved & 15) return BF_ERR_INVALID_ARG;
+    // neighbours' dL/dout and quads are read while dL/dimg is written
+    if ((const void*)grad_img == (const void*)grad_out || (const void*)grad_img == saved)
+        return BF_ERR_INVALID_ARG;
     poly::Params p;
     int gx = 0, gy = 0;
     bf_status st = poly::prepare(H, W, r, sigma_r, T, &N, opts, &p, &gx, &gy);

@@ -1006,6 +1006,9 @@ extern "C" bf_status bf_spatial_backward(const float* grad_out, const void* save
                                          float* grad_img, const bf_opts* opts, void* stream) {
     if (!grad_out || !saved || !grad_img) return BF_ERR_INVALID_ARG;
     if ((uintptr_t)saved & 15) return BF_ERR_INVALID_ARG;
+    // neighbours' dL/dout and quads are read while dL/dimg is written
+    if ((const void*)grad_img == (const void*)grad_out || (const void*)grad_img == saved)
+        return BF_ERR_INVALID_ARG;
     spk::Params p;
     int gx = 0, gy = 0;
     bf_status st = spk::prepare(H, W, r, M, sigma_r, T, &N, opts, &p, &gx, &gy);

@@ -125,6 +125,11 @@ def test_argument_checks_return_before_any_launch():
     o.gamma_mode = bf.GAMMA_FROM_SIGMA
     assert lib.bf_backward(p, q, q, q, 4, 4, 1, 0.2, 1.0, 0, None, q, None, 0,
                            ctypes.byref(o), None) == 6
+    # variant adjoints: dL/dimg aliasing dL/dout or the saved quads
+    s16 = ctypes.c_void_p(0x3000)
+    for gi in (p, s16):
+        assert lib.bf_spatial_backward(p, s16, 4, 4, 1, 2, 0.0, 1.0, 4, gi, None, None) == 1
+        assert lib.bf_poly_backward(p, s16, 4, 4, 1, 0.0, 1.0, 3, gi, None, None) == 1
     # batch: empty list
     assert lib.bf_batch(None, 0, None, p, 64, None) == 1
     # truncation tolerance outside [0, 1)
