@@ -331,6 +331,10 @@ static bf_status backward_impl(const void* img, const float* out, const float* g
     if (!img || !out || !grad_out || !saved || B < 1 || H < 1 || W < 1) return BF_ERR_INVALID_ARG;
     if (!grad_img && !grad_sigma) return BF_ERR_INVALID_ARG;
     if ((uintptr_t)saved & 15) return BF_ERR_INVALID_ARG;  // quads: 16-byte aligned
+    // neighbours' pixels, dL/dout and quads are read while dL/dimg is written
+    if (grad_img && ((const void*)grad_img == img || grad_img == out ||
+                     grad_img == grad_out || (const void*)grad_img == saved))
+        return BF_ERR_INVALID_ARG;
     bf_status st = check_opts(opts);
     if (st != BF_OK) return st;
     const int gm = opts ? opts->gamma_mode : BF_GAMMA_FIXED;

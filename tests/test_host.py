@@ -125,8 +125,12 @@ def test_argument_checks_return_before_any_launch():
     o.gamma_mode = bf.GAMMA_FROM_SIGMA
     assert lib.bf_backward(p, q, q, q, 4, 4, 1, 0.2, 1.0, 0, None, q, None, 0,
                            ctypes.byref(o), None) == 6
-    # variant adjoints: dL/dimg aliasing dL/dout or the saved quads
+    # adjoint: dL/dimg aliasing an input
     s16 = ctypes.c_void_p(0x3000)
+    for gi in (p, q, s16):
+        assert lib.bf_backward(p, q, q, s16, 4, 4, 1, 0.2, 1.0, 0, gi, None, None, 0, None,
+                               None) == 1
+    # variant adjoints: dL/dimg aliasing dL/dout or the saved quads
     for gi in (p, s16):
         assert lib.bf_spatial_backward(p, s16, 4, 4, 1, 2, 0.0, 1.0, 4, gi, None, None) == 1
         assert lib.bf_poly_backward(p, s16, 4, 4, 1, 0.0, 1.0, 3, gi, None, None) == 1
