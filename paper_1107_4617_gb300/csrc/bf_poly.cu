@@ -37,11 +37,25 @@ struct Params {
     float* gimg;           // adjoint: dL/dimg
     int H, W, r, Hb, Tw;
     float invT, T;
-    // psi_m(v) = sum_n c[m][n] v^n, m, n = 0..2N; dc[m][n] = (n + 1) c[m][n + 1]
-    // (psi_m'(v) = sum_n dc[m][n] v^n)
-    float c[PCAP][PCAP];
-    float dc[PCAP][PCAP];
+    // psi_m(v) = sum_n c_m[n] v^n (degree 2N - m: the terms u^m v^n of the
+    // expansion have m + n <= 2N), kept in pairs for the paired FP32 units:
+    // c2[i][n] = (c_{2i}[n], c_{2i+1}[n]) (psi_{2N+1} = 0), and likewise dc2 for
+    // psi_m'(v) = sum_n (n + 1) c_m[n + 1] v^n.
+    float2 c2[NMAX + 1][PCAP];
+    float2 dc2[NMAX + 1][PCAP];
 };
+
+__device__ __forceinline__ float2 dup(float v) { return make_float2(v, v); }
+
+// sum_n c[n] v^n on both lanes by Horner from degree deg (a constant once the
+// caller's loop is unrolled).
+__device__ __forceinline__ float2 horner2(const float2* c, int deg, float2 V) {
+    float2 s = c[deg];
+#pragma unroll
+    for (int n = PCAP - 2; n >= 0; --n)
+        if (n < deg) s = __ffma2_rn(s, V, c[n]);
+    return s;
+}
 
 // Launch modes: forward, forward that also saves the adjoint's quads, adjoint.
 enum Mode { FWD = 0, FWD_SAVE = 1, ADJ = 2 };
@@ -56,10 +70,10 @@ enum Mode { FWD = 0, FWD_SAVE = 1, ADJ = 2 };
 // through the centre value).
 template <int N, int MODE>
 __global__ void __launch_bounds__(WMAX, 2) poly_kernel(Params p) {
-    // forward: power planes u^0 .. u^{2N+1}; adjoint: alpha u^m and beta u^m, m <= 2N
-    constexpr int NP = MODE == ADJ ? 2 * (2 * N + 1) : 2 * N + 2;
-    constexpr int NA = 2 * N + 1;        // adjoint: first beta plane
-    constexpr int NQ = (NP + 3) / 4;     // float4 slots per lane
+    // forward: power planes u^0 .. u^{2N+1} as pairs (u^{2i}, u^{2i+1});
+    // adjoint: pairs (alpha u^m, beta u^m), m <= 2N
+    constexpr int NP2 = MODE == ADJ ? 2 * N + 1 : N + 1;  // plane pairs
+    constexpr int NQ = (NP2 + 1) / 2;    // float4 slots per lane
     constexpr int LD = WMAX + 1;
     constexpr int BUF = NQ * LD;
     extern __shared__ float4 smem[];     // [2][NQ][LD]
@@ -81,9 +95,9 @@ __global__ void __launch_bounds__(WMAX, 2) poly_kernel(Params p) {
     const int steps = span + Wi - 1;
 
     for (int i = j; i < 2 * BUF; i += Wi) smem[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    float D[NQ * 4];
+    float2 D[2 * NQ];
 #pragma unroll
-    for (int m = 0; m < NQ * 4; ++m) D[m] = 0.f;
+    for (int m = 0; m < 2 * NQ; ++m) D[m] = make_float2(0.f, 0.f);
     // the five pixels of step tt (own / second column, entering / leaving row,
     // centre), 0 where masked; the adjoint reads the saved quad (whose .x is f)
     // and dL/dout instead
@@ -140,20 +154,20 @@ __global__ void __launch_bounds__(WMAX, 2) poly_kernel(Params p) {
                 const float u = fmaf(q[k].x, p.invT, -0.5f);
                 if constexpr (MODE == ADJ) {
                     const float al = gq[k] * q[k].y;
-                    float pa = wgt * al, pb = -wgt * al * q[k].z;
+                    float2 pab = make_float2(wgt * al, -wgt * al * q[k].z);
+                    const float2 U = dup(u);
 #pragma unroll
-                    for (int m = 0; m < NA; ++m) {
-                        D[m] += pa;
-                        D[NA + m] += pb;
-                        pa *= u;
-                        pb *= u;
+                    for (int m = 0; m < NP2; ++m) {
+                        D[m] = __fadd2_rn(D[m], pab);
+                        pab = __fmul2_rn(pab, U);
                     }
                 } else {
-                    float pw = wgt;
+                    float2 pw = make_float2(wgt, wgt * u);
+                    const float2 U2 = dup(u * u);
 #pragma unroll
-                    for (int m = 0; m < NP; ++m) {
-                        D[m] += pw;
-                        pw *= u;
+                    for (int i = 0; i < NP2; ++i) {
+                        D[i] = __fadd2_rn(D[i], pw);
+                        pw = __fmul2_rn(pw, U2);
                     }
                 }
             };
@@ -164,54 +178,62 @@ __global__ void __launch_bounds__(WMAX, 2) poly_kernel(Params p) {
 
             const float4* rd = smem + ((t + 1) & 1) * BUF + j;
             float4* wr = smem + (t & 1) * BUF + j + 1;
-            float B[NQ * 4];
+            float2 B[2 * NQ];
 #pragma unroll
-            for (int q = 0; q < NQ; ++q) {
-                const float4 A = rd[q * LD];
-                B[4 * q + 0] = A.x + D[4 * q + 0];
-                B[4 * q + 1] = A.y + D[4 * q + 1];
-                B[4 * q + 2] = A.z + D[4 * q + 2];
-                B[4 * q + 3] = A.w + D[4 * q + 3];
-                wr[q * LD] = make_float4(B[4 * q], B[4 * q + 1], B[4 * q + 2], B[4 * q + 3]);
+            for (int qq = 0; qq < NQ; ++qq) {
+                const float4 A = rd[qq * LD];
+                B[2 * qq] = __fadd2_rn(make_float2(A.x, A.y), D[2 * qq]);
+                B[2 * qq + 1] = __fadd2_rn(make_float2(A.z, A.w), D[2 * qq + 1]);
+                wr[qq * LD] = make_float4(B[2 * qq].x, B[2 * qq].y, B[2 * qq + 1].x,
+                                          B[2 * qq + 1].y);
             }
             if (out) {
-                const float v = fmaf(fc, p.invT, -0.5f);
+                const float2 V = dup(fmaf(fc, p.invT, -0.5f));
                 const size_t o = (size_t)rho * W + co;
-                float num = 0.f, den = 0.f, dn = 0.f, dd = 0.f;
+                float2 NUM = make_float2(0.f, 0.f), DEN = NUM, DN = NUM, DD = NUM;
 #pragma unroll
-                for (int m = 0; m <= 2 * N; ++m) {
-                    // psi_m(v) (and psi_m'(v)) by Horner
-                    float psi = p.c[m][2 * N];
-#pragma unroll
-                    for (int n = 2 * N - 1; n >= 0; --n) psi = fmaf(psi, v, p.c[m][n]);
-                    float dpsi = 0.f;
+                for (int i = 0; i <= N; ++i) {
+                    // (psi_{2i}, psi_{2i+1}) at v: degree 2N - 2i (psi_{2N+1} = 0)
+                    const int deg = 2 * N - 2 * i;
+                    const float2 ps = horner2(p.c2[i], deg, V);
+                    float2 dps = make_float2(0.f, 0.f);
                     if constexpr (MODE != FWD) {
-                        dpsi = p.dc[m][2 * N - 1];
-#pragma unroll
-                        for (int n = 2 * N - 2; n >= 0; --n) dpsi = fmaf(dpsi, v, p.dc[m][n]);
+                        if (deg >= 1) dps = horner2(p.dc2[i], deg - 1, V);
                     }
                     if constexpr (MODE == ADJ) {
-                        // B[m] = A_m, B[NA + m] = B_m
-                        num = fmaf(psi, B[m], num);
-                        den = fmaf(dpsi, fmaf(fc, B[m], B[NA + m]), den);
+                        // B[m] = (A_m, B_m) = (Sum(alpha u^m), Sum(beta u^m))
+                        const float2 b0 = B[2 * i];
+                        NUM.x = fmaf(ps.x, b0.x, NUM.x);
+                        DEN.x = fmaf(dps.x, fmaf(fc, b0.x, b0.y), DEN.x);
+                        if (i < N) {
+                            const float2 b1 = B[2 * i + 1];
+                            NUM.y = fmaf(ps.y, b1.x, NUM.y);
+                            DEN.y = fmaf(dps.y, fmaf(fc, b1.x, b1.y), DEN.y);
+                        }
                     } else {
-                        const float g = fmaf(0.5f, B[m], B[m + 1]);
-                        num = fmaf(psi, g, num);
-                        den = fmaf(psi, B[m], den);
+                        // B[i] = (Sum u^{2i}, Sum u^{2i+1}); g_m = Sum u^m / 2 + Sum u^{m+1}
+                        const float2 bm = B[i];
+                        const float2 bm1 = make_float2(bm.y, i < N ? B[i + 1].x : 0.f);
+                        const float2 g = __ffma2_rn(dup(0.5f), bm, bm1);
+                        NUM = __ffma2_rn(ps, g, NUM);
+                        DEN = __ffma2_rn(ps, bm, DEN);
                         if constexpr (MODE == FWD_SAVE) {
-                            dn = fmaf(dpsi, g, dn);
-                            dd = fmaf(dpsi, B[m], dd);
+                            DN = __ffma2_rn(dps, g, DN);
+                            DD = __ffma2_rn(dps, bm, DD);
                         }
                     }
                 }
+                const float num = NUM.x + NUM.y, den = DEN.x + DEN.y;
                 if constexpr (MODE == ADJ) {
                     const float al = gq[4] * q[4].y;  // centre quad: (f, 1/den, out, X)
                     p.gimg[o] = num + fmaf(den, p.invT, al * q[4].w);
                 } else {
                     const float ov = p.T * num / den;
                     p.out[o] = ov;
-                    if constexpr (MODE == FWD_SAVE)
+                    if constexpr (MODE == FWD_SAVE) {
+                        const float dn = DN.x + DN.y, dd = DD.x + DD.y;
                         p.sv[o] = make_float4(fc, 1.0f / den, ov, fmaf(-ov * p.invT, dd, dn));
+                    }
                 }
             }
         }
@@ -277,10 +299,16 @@ static bf_status prepare(int H, int W, int r, float sigma_r, float T, int* N,
     memset(p, 0, sizeof(*p));
     double c[PCAP][PCAP];
     expansion(*N, c);
+    // psi_m has degree 2N - m: the kernel's Horner starts there
     for (int m = 0; m < PCAP; ++m)
+        for (int n = 0; n < PCAP; ++n)
+            if (m + n > 2 * *N && c[m][n] != 0.0) return BF_ERR_INTERNAL;
+    auto cf = [&](int m, int n) { return m < PCAP && n < PCAP ? c[m][n] : 0.0; };
+    for (int i = 0; i <= NMAX; ++i)
         for (int n = 0; n < PCAP; ++n) {
-            p->c[m][n] = (float)c[m][n];
-            p->dc[m][n] = n + 1 < PCAP ? (float)((double)(n + 1) * c[m][n + 1]) : 0.f;
+            p->c2[i][n] = make_float2((float)cf(2 * i, n), (float)cf(2 * i + 1, n));
+            p->dc2[i][n] = make_float2((float)((n + 1) * cf(2 * i, n + 1)),
+                                       (float)((n + 1) * cf(2 * i + 1, n + 1)));
         }
     p->H = H; p->W = W; p->r = r;
     p->T = T;
