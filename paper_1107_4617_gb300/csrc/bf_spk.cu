@@ -676,10 +676,36 @@ __global__ void __launch_bounds__(WMAX, 2) spk_plane_kernel(Params p) {
                 }
             };
             // + own enter, -(-1)^M second enter, - own leave, +(-1)^M second leave
-            accumulate(0, m0 ? 1.f : 0.f, 1.f);
-            accumulate(1, m1 ? sgn2 : 0.f, 1.f);
-            accumulate(2, m2 ? -1.f : 0.f, lsg);
-            accumulate(3, m3 ? -sgn2 : 0.f, lsg);
+            if constexpr (N == 0) {
+                // no range kernel: each stream's E is its row phase, so the four
+                // streams reduce to one real weight per sum before the phases
+                const float wsg[4] = {m0 ? 1.f : 0.f, m1 ? sgn2 : 0.f, m2 ? -lsg : 0.f,
+                                      m3 ? -sgn2 * lsg : 0.f};
+                float zg = 0.f, zh = 0.f;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    if constexpr (MODE == ADJ) {
+                        const float al = wsg[k] * (gq[k] * q[k].y);
+                        zg += al;
+                        zh = fmaf(-al, q[k].z, zh);
+                    } else {
+                        zg = fmaf(wsg[k], q[k].x, zg);
+                        zh += wsg[k];
+                    }
+                }
+#pragma unroll
+                for (int ib = 0; ib <= M; ++ib) {
+                    Dg[ib].x = fmaf(zg, rp[ib].x, Dg[ib].x);
+                    Dg[ib].y = fmaf(zg, rp[ib].y, Dg[ib].y);
+                    Dh[ib].x = fmaf(zh, rp[ib].x, Dh[ib].x);
+                    Dh[ib].y = fmaf(zh, rp[ib].y, Dh[ib].y);
+                }
+            } else {
+                accumulate(0, m0 ? 1.f : 0.f, 1.f);
+                accumulate(1, m1 ? sgn2 : 0.f, 1.f);
+                accumulate(2, m2 ? -1.f : 0.f, lsg);
+                accumulate(3, m3 ? -sgn2 : 0.f, lsg);
+            }
             (void)f0; (void)f1; (void)f2; (void)f3;
 
             // horizontal and recombination with the centre's conj(E_c)
