@@ -311,6 +311,8 @@ int bf_poly_resolve_N(float sigma_r, float T);
  *   saved     NULL, or device buffer of bf_saved_bytes(H, W) (16-byte aligned)
  *             receiving the quads (f, 1/den, out, dnum_s - out dden_s) for
  *             bf_poly_backward.
+ * r = 0 (a 1 x 1 window) is exact: out = img, saved quads (f, 1, f, 0), and
+ * bf_poly_backward returns grad_out.
  * Errors: BF_ERR_INVALID_ARG, BF_ERR_UNSUPPORTED (N > 8, r > 56),
  * BF_ERR_CUDA.
  */

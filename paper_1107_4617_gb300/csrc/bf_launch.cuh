@@ -2,6 +2,7 @@
 // kernel): band height from the launched kernel's occupancy.
 #pragma once
 
+#include <cuda_runtime.h>
 #include <stddef.h>
 
 namespace bf {
@@ -10,5 +11,10 @@ namespace bf {
 // (threads per CTA, dynamic shared bytes) resident per SM, at most max_per_sm
 // of them (0: no cap); at least 32 rows.
 int wave_band_rows(const void* kern, int threads, size_t smem, int H, int gx, int max_per_sm);
+
+// r = 0 (a 1 x 1 window) for the variant filters, whose kernels are 1 with
+// slope 0 at the origin: out = img (n FP32 values) and, if sv is given, the
+// saved quads (f, 1/den = 1, out = f, X = 0). Enqueued on s.
+cudaError_t unit_window(const float* img, float* out, float4* sv, size_t n, cudaStream_t s);
 
 }  // namespace bf

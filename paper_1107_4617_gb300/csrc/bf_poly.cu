@@ -364,9 +364,11 @@ extern "C" bf_status bf_poly_forward(const void* img, int H, int W, int r, float
     bf_status st = poly::prepare(H, W, r, sigma_r, T, &N, opts, &p, &gx, &gy);
     if (st != BF_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    if (r == 0 && !saved) {  // 1 x 1 window: out = f
-        cudaError_t e = cudaMemcpyAsync(out, img, sizeof(float) * (size_t)H * W,
-                                        cudaMemcpyDeviceToDevice, s);
+    if (r == 0) {
+        // a 1 x 1 window: p_N(0) = 1 with slope 0, so out = f and the quads
+        // are (f, 1, f, 0)
+        cudaError_t e = unit_window(static_cast<const float*>(img), out,
+                                    static_cast<float4*>(saved), (size_t)H * W, s);
         return e == cudaSuccess ? BF_OK : set_cuda_error(e);
     }
     p.img = static_cast<const float*>(img);
@@ -389,6 +391,12 @@ extern "C" bf_status bf_poly_backward(const float* grad_out, const void* saved, 
     int gx = 0, gy = 0;
     bf_status st = poly::prepare(H, W, r, sigma_r, T, &N, opts, &p, &gx, &gy);
     if (st != BF_OK) return st;
+    if (r == 0) {
+        // 1 x 1 window: out = f, so dL/df = dL/dout
+        cudaError_t e = cudaMemcpyAsync(grad_img, grad_out, sizeof(float) * (size_t)H * W,
+                                        cudaMemcpyDeviceToDevice, (cudaStream_t)stream);
+        return e == cudaSuccess ? BF_OK : set_cuda_error(e);
+    }
     p.bsv = static_cast<const float4*>(saved);
     p.gout = grad_out;
     p.gimg = grad_img;

@@ -973,19 +973,6 @@ static cudaError_t dispatch(const Params& p, int mode, int M, int N, int gx, int
     return cudaErrorInvalidValue;
 }
 
-// r = 0: a 1 x 1 window weighs the centre alone, so out = f, and the saved
-// quad is (f, 1/den = 1, out = f, X = 0): q_M(0) = q_N(0) = 1 and the range
-// kernel's slope at 0 is 0. (The strip engine's hand-off would telescope over
-// all lanes with signed terms here and lose digits to no purpose.)
-__global__ void r0_quads(const float* img, float* out, float4* sv, size_t n) {
-    const size_t stride = (size_t)gridDim.x * blockDim.x;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += stride) {
-        const float f = img[i];
-        out[i] = f;
-        sv[i] = make_float4(f, 1.f, f, 0.f);
-    }
-}
-
 }  // namespace spk
 }  // namespace bf
 
@@ -1008,18 +995,11 @@ extern "C" bf_status bf_spatial_forward(const void* img, int H, int W, int r, in
     p.sv = static_cast<float4*>(saved);
     const int mode = saved ? spk::FWD_SAVE : spk::FWD;
     if (r == 0) {
-        // a 1 x 1 window: every kernel weighs the centre alone, out = f
-        cudaError_t e;
-        if (!saved) {
-            e = cudaMemcpyAsync(out, img, sizeof(float) * (size_t)H * W, cudaMemcpyDeviceToDevice,
-                                s);
-        } else {
-            const size_t n = (size_t)H * W;
-            const size_t want = (n + 255) / 256, cap = (size_t)8 * sm_count();
-            spk::r0_quads<<<(unsigned)(want < cap ? want : cap), 256, 0, s>>>(
-                static_cast<const float*>(img), out, static_cast<float4*>(saved), n);
-            e = cudaGetLastError();
-        }
+        // a 1 x 1 window weighs the centre alone (q_M(0) = q_N(0) = 1, slope 0):
+        // out = f. The strip's hand-off would telescope over all lanes with
+        // signed terms here and lose digits to no purpose.
+        cudaError_t e = unit_window(static_cast<const float*>(img), out,
+                                    static_cast<float4*>(saved), (size_t)H * W, s);
         return e == cudaSuccess ? BF_OK : set_cuda_error(e);
     }
     cudaError_t e = spk::dispatch(p, mode, M, N, gx, gy, s);

@@ -70,6 +70,22 @@ __global__ void finish_kernel(int* keys) {
 
 }  // namespace util
 
+__global__ void unit_window_quads(const float* img, float* out, float4* sv, size_t n) {
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += stride) {
+        const float f = img[i];
+        out[i] = f;
+        sv[i] = make_float4(f, 1.f, f, 0.f);
+    }
+}
+
+cudaError_t unit_window(const float* img, float* out, float4* sv, size_t n, cudaStream_t s) {
+    if (!sv) return cudaMemcpyAsync(out, img, sizeof(float) * n, cudaMemcpyDeviceToDevice, s);
+    const size_t want = (n + 255) / 256, cap = (size_t)8 * sm_count();
+    unit_window_quads<<<(unsigned)(want < cap ? want : cap), 256, 0, s>>>(img, out, sv, n);
+    return cudaGetLastError();
+}
+
 int wave_band_rows(const void* kern, int threads, size_t smem, int H, int gx, int max_per_sm) {
     int occ = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem) != cudaSuccess ||

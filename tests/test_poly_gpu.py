@@ -85,3 +85,19 @@ def test_poly_adjoint_vs_central_differences(cuda_lib, H, W, r, N, T):
         sm = sub.copy(); sm[y - y0, x - x0] -= h
         fd = (np.sum(wsub * ref(sp, r, N, T)) - np.sum(wsub * ref(sm, r, N, T))) / (2 * h)
         assert abs(gg[y, x] - fd) <= 1e-3 * max(1.0, abs(fd)), (y, x, gg[y, x], fd)
+
+
+def test_unit_window_closed_form(cuda_lib):
+    """r = 0 (a 1 x 1 window): out = f, saved quads (f, 1, f, 0), dL/df = dL/dout,
+    on an image wider than one strip."""
+    bf = cuda_lib
+    f = synth.sinusoids(70, 300, seed=11)
+    ft = torch.from_numpy(f).cuda()
+    sv = torch.empty((70, 300, 4), device="cuda")
+    out = bf.bf_poly_forward(ft, 0, 0.0, 1.0, 6, saved=sv)
+    g = torch.from_numpy(synth.weights((70, 300), seed=2)).cuda()
+    gi = bf.bf_poly_backward(g, sv, 0, 0.0, 1.0, 6)
+    torch.cuda.synchronize()
+    assert np.array_equal(out.cpu().numpy(), f)
+    assert np.array_equal(sv.cpu().numpy(), np.stack([f, np.ones_like(f), f, np.zeros_like(f)], -1))
+    assert torch.equal(gi, g)
