@@ -19,13 +19,18 @@
 //
 // The skewed strip of the box engine carries over because the window width
 // 2r + 1 is half a period of every spatial harmonic of the same parity as M:
-// e^{i a gs (2r+1)} = (-1)^a = (-1)^M. Thread j keeps, per (b, k), the
-// vertical running sums of e^{i b gs z2} e^{i k gamma f} (times f, and not)
+// e^{i a gs (2r+1)} = (-1)^a = (-1)^M. Thread j keeps vertical running sums
 // over its own column minus (-1)^M times those of the column 2r + 1 to the
-// left; the horizontal sum of combo (a, b, k) then obeys
-//   S(j) = S(j - 1) + e^{i a gs cw(j)} D_{b,k}(j),
-// passed one lane per step through a shared row double-buffered by step
-// parity, one CTA barrier per step.
+// left; horizontal sums pass one lane per step through a shared row
+// double-buffered by step parity, one CTA barrier per step. Two forms:
+//   combo-sum (spk_kernel): per combo c, the column-rotated difference
+//     D'_c += e^{i a gs cw} e^{i b gs e} Z_k, Z_k the four streams' weighted
+//     range harmonics, and S_c(j) = S_c(j - 1) + D'_c(j);
+//   plane-sum (spk_plane_kernel): per (b, k) plane the difference D_{b,k} of
+//     e^{i b gs z2} e^{i k gamma f} (times f, and not), rotated in the
+//     hand-off, S(j) = S(j - 1) + e^{i a gs cw(j)} D_{b,k}(j);
+// the first where the combos are few against the planes (every N > 0), the
+// second where many combos share a plane (no range kernel, M >= 2).
 #include <math.h>
 #include <string.h>
 
