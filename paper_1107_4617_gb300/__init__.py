@@ -526,6 +526,15 @@ _fn = None
 _spatial_fn = None
 
 
+def _as_batch(x):
+    """[H, W] or [B, H, W] -> contiguous [B, H, W] (a view when possible)."""
+    if x.dim() == 2:
+        x = x.unsqueeze(0)
+    if x.dim() != 3:
+        raise ValueError("expected an [H, W] or [B, H, W] tensor")
+    return x.contiguous()
+
+
 def _make_spatial_function():
     import torch
 
@@ -535,20 +544,25 @@ def _make_spatial_function():
 
         @staticmethod
         def forward(ctx, f, r, M, sigma_r, T, N):
-            f = f.contiguous()
-            H, W = f.shape
-            saved = torch.empty((H, W, 4), dtype=torch.float32, device=f.device)
-            out = bf_spatial_forward(f, r, M, sigma_r, T, N, saved=saved)
+            fb = _as_batch(f)
+            B, H, W = fb.shape
+            saved = torch.empty((B, H, W, 4), dtype=torch.float32, device=f.device)
+            out = torch.empty((B, H, W), dtype=torch.float32, device=f.device)
+            for b in range(B):  # one launch per image, in order on the current stream
+                bf_spatial_forward(fb[b], r, M, sigma_r, T, N, out=out[b], saved=saved[b])
             ctx.save_for_backward(saved)
-            ctx.cfg = (r, M, sigma_r, T, N)
-            return out
+            ctx.cfg = (r, M, sigma_r, T, N, f.dim())
+            return out[0] if f.dim() == 2 else out
 
         @staticmethod
         def backward(ctx, g):
             (saved,) = ctx.saved_tensors
-            r, M, sigma_r, T, N = ctx.cfg
-            gi = bf_spatial_backward(g.contiguous().float(), saved, r, M, sigma_r, T, N)
-            return gi, None, None, None, None, None
+            r, M, sigma_r, T, N, dim = ctx.cfg
+            gb = _as_batch(g.float())
+            gi = torch.empty_like(gb)
+            for b in range(gb.shape[0]):
+                bf_spatial_backward(gb[b], saved[b], r, M, sigma_r, T, N, grad_img=gi[b])
+            return (gi[0] if dim == 2 else gi), None, None, None, None, None
 
     return BilateralSpatial
 
@@ -565,28 +579,33 @@ def _make_poly_function():
 
         @staticmethod
         def forward(ctx, f, r, sigma_r, T, N):
-            f = f.contiguous()
-            H, W = f.shape
-            saved = torch.empty((H, W, 4), dtype=torch.float32, device=f.device)
-            out = bf_poly_forward(f, r, sigma_r, T, N, saved=saved)
+            fb = _as_batch(f)
+            B, H, W = fb.shape
+            saved = torch.empty((B, H, W, 4), dtype=torch.float32, device=f.device)
+            out = torch.empty((B, H, W), dtype=torch.float32, device=f.device)
+            for b in range(B):  # one launch per image, in order on the current stream
+                bf_poly_forward(fb[b], r, sigma_r, T, N, out=out[b], saved=saved[b])
             ctx.save_for_backward(saved)
-            ctx.cfg = (r, sigma_r, T, N)
-            return out
+            ctx.cfg = (r, sigma_r, T, N, f.dim())
+            return out[0] if f.dim() == 2 else out
 
         @staticmethod
         def backward(ctx, g):
             (saved,) = ctx.saved_tensors
-            r, sigma_r, T, N = ctx.cfg
-            return (bf_poly_backward(g.contiguous().float(), saved, r, sigma_r, T, N),
-                    None, None, None, None)
+            r, sigma_r, T, N, dim = ctx.cfg
+            gb = _as_batch(g.float())
+            gi = torch.empty_like(gb)
+            for b in range(gb.shape[0]):
+                bf_poly_backward(gb[b], saved[b], r, sigma_r, T, N, grad_img=gi[b])
+            return (gi[0] if dim == 2 else gi), None, None, None, None
 
     return BilateralPoly
 
 
 def bilateral_poly(f, r: int, sigma_r: float = 0.0, T: float = 1.0, N: int = 0):
     """Bilateral filter with range kernel p_N(t) = (1 - t^2/T^2)^N (N <= 0:
-    from sigma_r) and the box window, of a 2-D float32 CUDA tensor,
-    differentiable in f."""
+    from sigma_r) and the box window, of an [H, W] or [B, H, W] float32 CUDA
+    tensor, differentiable in f."""
     global _poly_fn
     if _poly_fn is None:
         _poly_fn = _make_poly_function()
@@ -596,7 +615,7 @@ def bilateral_poly(f, r: int, sigma_r: float = 0.0, T: float = 1.0, N: int = 0):
 def bilateral_spatial(f, r: int, M: int, sigma_r: float = 0.0, T: float = 1.0, N: int = 0):
     """Neighbourhood filter with the separable spatial kernel q_M x q_M and
     range kernel q_N (N = 0: the linear filter of Algorithm 1; N < 0: from
-    sigma_r) of a 2-D float32 CUDA tensor, differentiable in f."""
+    sigma_r) of an [H, W] or [B, H, W] float32 CUDA tensor, differentiable in f."""
     global _spatial_fn
     if _spatial_fn is None:
         _spatial_fn = _make_spatial_function()

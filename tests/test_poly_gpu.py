@@ -101,3 +101,20 @@ def test_unit_window_closed_form(cuda_lib):
     assert np.array_equal(out.cpu().numpy(), f)
     assert np.array_equal(sv.cpu().numpy(), np.stack([f, np.ones_like(f), f, np.zeros_like(f)], -1))
     assert torch.equal(gi, g)
+
+
+def test_batched_autograd_matches_per_image(cuda_lib):
+    """bilateral_poly on [B, H, W]: each image's output and dL/df equal those of
+    the image on its own."""
+    bf = cuda_lib
+    fs = np.stack([synth.rectangles(90, 140, seed=40 + b) for b in range(3)])
+    w = torch.from_numpy(synth.weights((3, 90, 140), seed=5)).cuda()
+    ft = torch.from_numpy(fs).cuda().requires_grad_(True)
+    out = bf.bilateral_poly(ft, 4, 0.0, 1.0, 5)
+    (w * out).sum().backward()
+    for b in range(3):
+        fb = torch.from_numpy(fs[b]).cuda().requires_grad_(True)
+        ob = bf.bilateral_poly(fb, 4, 0.0, 1.0, 5)
+        (w[b] * ob).sum().backward()
+        assert torch.equal(out[b].detach(), ob.detach())
+        assert torch.equal(ft.grad[b], fb.grad)

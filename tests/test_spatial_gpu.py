@@ -158,3 +158,20 @@ def test_spatial_saved_quads(cuda_lib):
     np.testing.assert_array_equal(q[..., 0], f)
     np.testing.assert_array_equal(q[..., 2], got)
     np.testing.assert_allclose(1.0 / q[..., 1], den, rtol=2e-5, atol=0)
+
+
+def test_batched_autograd_matches_per_image(cuda_lib):
+    """bilateral_spatial on [B, H, W]: each image's output and dL/df equal those
+    of the image on its own (the same kernels on the same data)."""
+    bf = cuda_lib
+    fs = np.stack([synth.rectangles(90, 140, seed=30 + b) for b in range(3)])
+    w = torch.from_numpy(synth.weights((3, 90, 140), seed=4)).cuda()
+    ft = torch.from_numpy(fs).cuda().requires_grad_(True)
+    out = bf.bilateral_spatial(ft, 4, 2, 0.0, 1.0, 4)
+    (w * out).sum().backward()
+    for b in range(3):
+        fb = torch.from_numpy(fs[b]).cuda().requires_grad_(True)
+        ob = bf.bilateral_spatial(fb, 4, 2, 0.0, 1.0, 4)
+        (w[b] * ob).sum().backward()
+        assert torch.equal(out[b].detach(), ob.detach())
+        assert torch.equal(ft.grad[b], fb.grad)
