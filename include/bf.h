@@ -353,7 +353,9 @@ bf_status bf_batch_prepare(const bf_desc* descs, int n, const bf_opts* opts, voi
 /* Launches the persistent batch kernel over a table bf_batch_prepare wrote
    into workspace: a memset of the work counter and one kernel, nothing
    else, so it can be captured into a CUDA graph and replayed. opts must
-   carry the same kahan / in_dtype as the prepare call. */
+   carry the same kahan / in_dtype as the prepare call. On the plain (non-
+   Kahan) path a table without the tag bf_batch_prepare writes (a workspace
+   never prepared, or overwritten) launches no work: outputs stay untouched. */
 bf_status bf_batch_launch(void* workspace, size_t ws_bytes, const bf_opts* opts, void* stream);
 
 /* Minimum and maximum of an H x W device image (dtype BF_F32 or BF_BF16), for

@@ -10,10 +10,9 @@
 #include <vector>
 
 #include "bf_internal.cuh"
+#include "bf_launch.cuh"
 
 namespace bf {
-
-static const int kSysMagic = 0x42465359;  // "BFSY"
 
 // Rows per band in a batch on the skewed-strip engine: tall enough that the
 // strip's skew (Wi steps) and the 2r warm-up rows stay a minor cost, small
@@ -183,7 +182,7 @@ bf_status bf_batch_prepare(const bf_desc* descs, int n, const bf_opts* opts, voi
     const size_t tbytes = sys_table_bytes(n);
     std::vector<char> host(tbytes, 0);
     SysBatchTable* tab = reinterpret_cast<SysBatchTable*>(host.data());
-    tab->magic = kSysMagic;
+    tab->magic = SYS_BATCH_MAGIC;
     tab->in_dtype = opts ? opts->in_dtype : BF_F32;
     char* acc_base = static_cast<char*>(workspace) + align256(tbytes);
     size_t acc_off = 0;

@@ -17,4 +17,9 @@ int wave_band_rows(const void* kern, int threads, size_t smem, int H, int gx, in
 // saved quads (f, 1/den = 1, out = f, X = 0). Enqueued on s.
 cudaError_t unit_window(const float* img, float* out, float4* sv, size_t n, cudaStream_t s);
 
+// Tag bf_batch_prepare writes into a strip-engine batch table; the persistent
+// batch kernels do no work on a table without it (a workspace that was never
+// prepared, or was overwritten).
+constexpr int SYS_BATCH_MAGIC = 0x42465359;  // "BFSY"
+
 }  // namespace bf

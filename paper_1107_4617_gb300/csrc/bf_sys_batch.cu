@@ -3,6 +3,7 @@
 // every harmonic chunk of that tile in turn. Images are stored in decreasing
 // order of per-tile cost, so the longest tiles start first. No CTA waits on
 // another; the only device loop is over the finite tile list.
+#include "bf_launch.cuh"
 #include "bf_sys_engine.cuh"
 
 namespace bf {
@@ -28,6 +29,7 @@ __global__ void __launch_bounds__(WMAX, 256 / WMAX) bf_sys_batch_kernel(SysBatch
     extern __shared__ float4 smem[];
     __shared__ SysParams sp;
     __shared__ int s_tile, s_img;
+    if (tab->magic != SYS_BATCH_MAGIC) return;  // not a prepared table: no work
     const SysBatchGroup& G = tab->g[group];
     const int n_tiles = G.n_tiles;
     for (;;) {

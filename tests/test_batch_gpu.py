@@ -97,3 +97,27 @@ def test_batch_kahan_and_bf16(cuda_lib):
             ref = oracle.bilateral(im.float().cpu().numpy().astype(np.float64), s["r"], math.pi / 2, N)
             e = np.abs(o.cpu().numpy() - ref) / np.maximum(np.abs(ref), 1e-2)
             assert e.max() <= 1e-4, (s, e.max())
+
+
+def test_batch_launch_needs_a_prepared_table(cuda_lib):
+    """A table whose tag was overwritten launches no work (outputs keep their
+    sentinel); preparing it again restores the filter."""
+    bf = cuda_lib
+    specs = synth.batch_specs(6, seed=13, side_lo=40, side_hi=300)
+    imgs = [torch.from_numpy(synth.rectangles(s["H"], s["W"], seed=s["seed"])).cuda()
+            for s in specs]
+    outs = [torch.full_like(im, -7.0) for im in imgs]
+    descs = bf.make_descs(imgs, outs, [s["r"] for s in specs], [s["sigma_r"] for s in specs])
+    opts = bf._opts()
+    ws = torch.empty(((bf.bf_batch_workspace_bytes(descs, opts) + 3) // 4,), device="cuda")
+    bf.bf_batch_prepare(descs, ws, opts)
+    ws.view(torch.int32)[4] = 0  # the tag follows the four work counters
+    bf.bf_batch_launch(ws, opts)
+    torch.cuda.synchronize()
+    assert all(bool(torch.all(o == -7.0)) for o in outs)
+    bf.bf_batch_prepare(descs, ws, opts)
+    bf.bf_batch_launch(ws, opts)
+    torch.cuda.synchronize()
+    for s, im, o in zip(specs, imgs, outs):
+        ref = bf.bf_forward(im, s["r"], s["sigma_r"])
+        assert torch.max(torch.abs(o - ref)).item() <= 2e-4
