@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include "bf_internal.cuh"
+#include "bf_trace.cuh"
 
 namespace bf {
 
@@ -424,11 +425,13 @@ size_t bf_backward3d_workspace_bytes(int B, int H, int W, int r, float sigma_r, 
 
 bf_status bf_forward(const void* img, int H, int W, int r, float sigma_r, float T, int N,
                      float* out, const bf_opts* opts, void* saved, void* stream) {
+    BF_TRACE("bf_forward");
     return forward_impl(img, 1, H, W, r, sigma_r, T, N, out, opts, saved, stream);
 }
 
 bf_status bf_forward3d(const void* img, int B, int H, int W, int r, float sigma_r, float T, int N,
                        float* out, const bf_opts* opts, void* saved, void* stream) {
+    BF_TRACE("bf_forward3d");
     return forward_impl(img, B, H, W, r, sigma_r, T, N, out, opts, saved, stream);
 }
 
@@ -436,6 +439,7 @@ bf_status bf_backward(const void* img, const float* out, const float* grad_out,
                       const void* saved, int H, int W, int r, float sigma_r, float T, int N,
                       float* grad_img, float* grad_sigma, void* workspace, size_t ws_bytes,
                       const bf_opts* opts, void* stream) {
+    BF_TRACE("bf_backward");
     return backward_impl(img, out, grad_out, saved, 1, H, W, r, sigma_r, T, N, grad_img,
                          grad_sigma, workspace, ws_bytes, opts, stream);
 }
@@ -444,6 +448,7 @@ bf_status bf_backward3d(const void* img, const float* out, const float* grad_out
                         const void* saved, int B, int H, int W, int r, float sigma_r, float T,
                         int N, float* grad_img, float* grad_sigma, void* workspace,
                         size_t ws_bytes, const bf_opts* opts, void* stream) {
+    BF_TRACE("bf_backward3d");
     return backward_impl(img, out, grad_out, saved, B, H, W, r, sigma_r, T, N, grad_img,
                          grad_sigma, workspace, ws_bytes, opts, stream);
 }

@@ -11,6 +11,7 @@
 
 #include "bf_internal.cuh"
 #include "bf_launch.cuh"
+#include "bf_trace.cuh"
 
 namespace bf {
 
@@ -158,6 +159,7 @@ size_t bf_batch_workspace_bytes(const bf_desc* descs, int n, const bf_opts* opts
 
 bf_status bf_batch_prepare(const bf_desc* descs, int n, const bf_opts* opts, void* workspace,
                            size_t ws_bytes, void* stream) {
+    BF_TRACE("bf_batch_prepare");
     if (!descs || n < 1 || !workspace) return BF_ERR_INVALID_ARG;
     bf_status st = check_opts(opts);
     if (st != BF_OK) return st;
@@ -244,6 +246,7 @@ bf_status bf_batch_prepare(const bf_desc* descs, int n, const bf_opts* opts, voi
 }
 
 bf_status bf_batch_launch(void* workspace, size_t ws_bytes, const bf_opts* opts, void* stream) {
+    BF_TRACE("bf_batch_launch");
     if (!workspace) return BF_ERR_INVALID_ARG;
     bf_status st = check_opts(opts);
     if (st != BF_OK) return st;

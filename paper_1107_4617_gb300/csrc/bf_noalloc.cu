@@ -18,6 +18,7 @@
 #include <mutex>
 
 #include "bf_internal.cuh"
+#include "bf_trace.cuh"
 
 namespace {
 
@@ -53,6 +54,7 @@ extern "C" bf_status bf_backward_noalloc(const void* img, const float* out,
                                          const float* grad_out, const void* saved, int H, int W,
                                          int r, float sigma_r, float T, int N, float* grad_img,
                                          float* grad_sigma, const bf_opts* opts, void* stream) {
+    BF_TRACE("bf_backward_noalloc");
     const size_t cap = sizeof(float) * (size_t)BF_NOALLOC_MAX_PARTIALS;
     const size_t need = bf_backward_workspace_bytes(H, W, r, sigma_r, T, N, opts);
     if (need > cap) return BF_ERR_UNSUPPORTED;  // call needs more scratch than the array holds

@@ -20,6 +20,7 @@
 
 #include "bf_internal.cuh"
 #include "bf_launch.cuh"
+#include "bf_trace.cuh"
 
 namespace bf {
 namespace poly {
@@ -355,6 +356,7 @@ extern "C" int bf_poly_resolve_N(float sigma_r, float T) {
 extern "C" bf_status bf_poly_forward(const void* img, int H, int W, int r, float sigma_r,
                                      float T, int N, float* out, const bf_opts* opts, void* saved,
                                      void* stream) {
+    BF_TRACE("bf_poly_forward");
     if (!img || !out) return BF_ERR_INVALID_ARG;
     if ((const void*)out == img) return BF_ERR_INVALID_ARG;
     if (saved && ((uintptr_t)saved & 15)) return BF_ERR_INVALID_ARG;
@@ -382,6 +384,7 @@ extern "C" bf_status bf_poly_forward(const void* img, int H, int W, int r, float
 extern "C" bf_status bf_poly_backward(const float* grad_out, const void* saved, int H, int W,
                                       int r, float sigma_r, float T, int N, float* grad_img,
                                       const bf_opts* opts, void* stream) {
+    BF_TRACE("bf_poly_backward");
     if (!grad_out || !saved || !grad_img) return BF_ERR_INVALID_ARG;
     if ((uintptr_t)saved & 15) return BF_ERR_INVALID_ARG;
     // neighbours' dL/dout and quads are read while dL/dimg is written

@@ -36,6 +36,7 @@
 
 #include "bf_internal.cuh"
 #include "bf_launch.cuh"
+#include "bf_trace.cuh"
 
 namespace bf {
 namespace spk {
@@ -986,6 +987,7 @@ using namespace bf;
 extern "C" bf_status bf_spatial_forward(const void* img, int H, int W, int r, int M,
                                         float sigma_r, float T, int N, float* out,
                                         const bf_opts* opts, void* saved, void* stream) {
+    BF_TRACE("bf_spatial_forward");
     if (!img || !out) return BF_ERR_INVALID_ARG;
     if ((const void*)out == img) return BF_ERR_INVALID_ARG;
     if (saved && ((uintptr_t)saved & 15)) return BF_ERR_INVALID_ARG;
@@ -1015,6 +1017,7 @@ extern "C" bf_status bf_spatial_forward(const void* img, int H, int W, int r, in
 extern "C" bf_status bf_spatial_backward(const float* grad_out, const void* saved, int H, int W,
                                          int r, int M, float sigma_r, float T, int N,
                                          float* grad_img, const bf_opts* opts, void* stream) {
+    BF_TRACE("bf_spatial_backward");
     if (!grad_out || !saved || !grad_img) return BF_ERR_INVALID_ARG;
     if ((uintptr_t)saved & 15) return BF_ERR_INVALID_ARG;
     // neighbours' dL/dout and quads are read while dL/dimg is written

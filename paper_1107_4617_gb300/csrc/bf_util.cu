@@ -6,6 +6,7 @@
 
 #include "bf_internal.cuh"
 #include "bf_launch.cuh"
+#include "bf_trace.cuh"
 
 namespace bf {
 namespace util {
@@ -104,6 +105,7 @@ using namespace bf;
 
 extern "C" bf_status bf_check_range(const void* img, int H, int W, int in_dtype, float* minmax,
                                     void* stream) {
+    BF_TRACE("bf_check_range");
     if (!img || !minmax || H < 1 || W < 1) return BF_ERR_INVALID_ARG;
     if (in_dtype != BF_F32 && in_dtype != BF_BF16) return BF_ERR_INVALID_ARG;
     if ((uintptr_t)minmax & 7) return BF_ERR_INVALID_ARG;
