@@ -1,5 +1,5 @@
 // Host dispatch of the skewed-strip engine (bf_sys_engine.cuh): picks the
-// instantiation (strip width, harmonic pairs, Kahan) and splits the harmonics
+// instantiation (strip width, harmonic pairs, seed, Kahan) and splits the harmonics
 // of q_N's expansion into chunks when they exceed the register budget of one
 // launch; chunks accumulate num/den (or the adjoint's two parts) in the
 // output buffers and the last chunk finishes the ratio.
@@ -16,6 +16,30 @@ static int sys_kp(int K) {
     for (int kp : kps)
         if (2 * kp >= K) return kp;
     return -1;
+}
+
+// First-chunk kernels of FP32 images on 128-thread strips: odd N (seed 1) runs
+// kc harmonics in (kc + 1) / 2 pairs, even N (seed 2) the constant harmonic
+// apart and kc - 1 harmonics in pairs; the last pair is half when the paired
+// count is odd.
+static cudaError_t launch_first(const SysParams& p, int mode, int kc, int seed, int wi, int gx,
+                                int gy, cudaStream_t s) {
+    const int np = seed == 2 ? kc - 1 : kc;
+    const bool half = np & 1;
+    switch ((np + 1) / 2) {
+        case 1: return sys_first_kp<1>(p, mode, half, seed, wi, gx, gy, s);
+        case 2: return sys_first_kp<2>(p, mode, half, seed, wi, gx, gy, s);
+        case 3: return sys_first_kp<3>(p, mode, half, seed, wi, gx, gy, s);
+        case 4: return sys_first_kp<4>(p, mode, half, seed, wi, gx, gy, s);
+        case 5: return sys_first_kp<5>(p, mode, half, seed, wi, gx, gy, s);
+        case 6: return sys_first_kp<6>(p, mode, half, seed, wi, gx, gy, s);
+        case 7: return sys_first_kp<7>(p, mode, half, seed, wi, gx, gy, s);
+        case 8: return sys_first_kp<8>(p, mode, half, seed, wi, gx, gy, s);
+        case 9: return sys_first_kp<9>(p, mode, half, seed, wi, gx, gy, s);
+        case 10: return sys_first_kp<10>(p, mode, half, seed, wi, gx, gy, s);
+        case 11: return sys_first_kp<11>(p, mode, half, seed, wi, gx, gy, s);
+    }
+    return cudaErrorInvalidValue;
 }
 
 int sys_chunks(int K, bool kahan, int kp_max) {
@@ -51,6 +75,8 @@ cudaError_t launch_sys(const SysParams& base, int mode, bool kahan, int in_dtype
         if (mode == 2 && c + 1 < nch) p.partial = nullptr;  // reduce only on the last chunk
         cudaError_t e;
         if (kahan) e = launch_sys_kahan(p, mode, in_dtype, kp, wi, gx, gy, s);
+        else if (wi <= 128 && in_dtype == BF_F32 && (p.k0 == 1 || (p.k0 == 0 && kc > 1)))
+            e = launch_first(p, mode, kc, p.k0 == 1 ? 1 : 2, wi, gx, gy, s);
         else if (wi <= 128) e = launch_sys_w128(p, mode, in_dtype, kp, wi, gx, gy, s);
         else e = launch_sys_w256(p, mode, in_dtype, kp, wi, gx, gy, s);
         if (e != cudaSuccess) return e;

@@ -29,7 +29,15 @@
 // Every stream stores pair i multiplied by s_i = (-1)^(i/2), which turns the
 // recurrence into d_{i+1} = (+-m) d_i + d_{i-1}, m = 2 cos 4 theta, with no
 // negation; since all planes of pair i carry the same s_i and the
-// recombination multiplies two of them, the sign cancels there.
+// recombination multiplies two of them, the sign cancels there. An odd
+// number of harmonics ends in a half pair (HALF): its one harmonic runs on
+// scalar FP32 and passes one float4 per lane through shared memory.
+//
+// The first two pairs of every stream (the seed) come from one MUFU sincos
+// of theta. For the first harmonic chunk the seed is specialised at compile
+// time (SEED 1: odd N, harmonics 1, 3, 5, 7; SEED 2: even N, harmonics 2, 4,
+// 6, 8, with the constant harmonic k = 0 kept apart as scalar planes); later
+// chunks (SEED 0) start from a reduced sincos of k0 theta.
 #pragma once
 #include "bf_internal.cuh"
 
@@ -64,9 +72,9 @@ struct Strm {
     float2 c, s, nc, ns, m, nm;
 };
 
-// k0 = frequency of the first harmonic (k0 <= 1 for an unchunked filter; a
-// later harmonic chunk starts at k0 = kstart + 2 i0 and seeds from k0 theta).
-__device__ __forceinline__ Strm seed(float f, float gamma, int k0) {
+// k0 = frequency of the first harmonic of the launch (a later harmonic chunk
+// starts at k0 = kstart + 2 i0 and seeds from a reduced sincos of k0 theta).
+__device__ __forceinline__ Strm seed_general(float f, float gamma, int k0) {
     float sn, cs;
     __sincosf(gamma * f, &sn, &cs);
     const float wc = (cs - sn) * (cs + sn);   // e^{2 i theta}
@@ -90,13 +98,72 @@ __device__ __forceinline__ Strm seed(float f, float gamma, int k0) {
     return q;
 }
 
+// Odd N, first chunk: harmonics 2, 3 theta from theta by the Chebyshev
+// three-term recurrence in theta, m = 2 cos 4 theta = 4 cos^2 2theta - 2, and
+// pair 1 (5, 7 theta) from pair 0 and its mirror (-3, -1 theta) by the
+// recurrence in 4 theta.
+__device__ __forceinline__ Strm seed_odd(float f, float gamma) {
+    float s1, c1;
+    __sincosf(gamma * f, &s1, &c1);
+    const float cc = c1 + c1;
+    const float c2 = fmaf(cc, c1, -1.0f);
+    const float s2 = cc * s1;
+    const float c3 = fmaf(cc, c2, -c1);
+    const float s3 = fmaf(cc, s2, -s1);
+    const float m = fmaf(4.0f * c2, c2, -2.0f);
+    Strm q;
+    q.c = make_float2(c1, c3);
+    q.s = make_float2(s1, s3);
+    q.nc = make_float2(fmaf(m, c1, -c3), fmaf(m, c3, -c1));
+    q.ns = make_float2(fmaf(m, s1, s3), fmaf(m, s3, s1));
+    q.m = dup(m);
+    q.nm = dup(-m);
+    return q;
+}
+
+// Even N, first chunk, the constant harmonic apart: pairs from harmonics
+// 2, 4 theta; cos 4 theta = m / 2, and pair 1 (6, 8 theta) by the recurrence in
+// 4 theta with the mirrors -2 theta and 0.
+__device__ __forceinline__ Strm seed_even(float f, float gamma) {
+    float s1, c1;
+    __sincosf(gamma * f, &s1, &c1);
+    const float cc = c1 + c1;
+    const float c2 = fmaf(cc, c1, -1.0f);
+    const float s2 = cc * s1;
+    const float m = fmaf(4.0f * c2, c2, -2.0f);
+    const float c4 = 0.5f * m;
+    const float s4 = 2.0f * s2 * c2;
+    Strm q;
+    q.c = make_float2(c2, c4);
+    q.s = make_float2(s2, s4);
+    q.nc = make_float2(fmaf(m, c2, -c2), fmaf(m, c4, -1.0f));
+    q.ns = make_float2(fmaf(m, s2, s2), m * s4);
+    q.m = dup(m);
+    q.nm = dup(-m);
+    return q;
+}
+
+template <int SEED>
+__device__ __forceinline__ Strm seed(float f, float gamma, int k0) {
+    if constexpr (SEED == 1) return seed_odd(f, gamma);
+    else if constexpr (SEED == 2) return seed_even(f, gamma);
+    else return seed_general(f, gamma, k0);
+}
+
 // Step from pair i to pair i+1 and form pair i+2 when it is needed:
-// d_{i+2} = (i+1 even ? m : -m) d_{i+1} + d_i.
-__device__ __forceinline__ void advance(Strm& q, int i, bool need) {
+// d_{i+2} = (i+1 even ? m : -m) d_{i+1} + d_i. half: pair i+2 is the half
+// pair (only its first component is formed).
+__device__ __forceinline__ void advance(Strm& q, int i, bool need, bool half = false) {
     if (need) {
         const float2 mm = ((i + 1) & 1) ? q.nm : q.m;
-        const float2 c2 = __ffma2_rn(mm, q.nc, q.c);
-        const float2 s2 = __ffma2_rn(mm, q.ns, q.s);
+        float2 c2, s2;
+        if (half) {
+            c2 = make_float2(fmaf(mm.x, q.nc.x, q.c.x), 0.f);
+            s2 = make_float2(fmaf(mm.x, q.ns.x, q.s.x), 0.f);
+        } else {
+            c2 = __ffma2_rn(mm, q.nc, q.c);
+            s2 = __ffma2_rn(mm, q.ns, q.s);
+        }
         q.c = q.nc; q.s = q.ns; q.nc = c2; q.ns = s2;
     } else {
         q.c = q.nc; q.s = q.ns;
@@ -165,9 +232,10 @@ struct Geo {
 
 // Float4 slots of shared memory one tile needs: two step-parity buffers of
 // 2 KP planes x (WMAX + 1) columns (column 0 stays zero: the first lane's
-// carry-in).
-__host__ __device__ constexpr int sys_smem_slots(int KP, int WMAX) {
-    return 2 * 2 * KP * (WMAX + 1);
+// carry-in), plus one row for the constant (DC) harmonic of even N when it
+// runs apart from the pairs.
+__host__ __device__ constexpr int sys_smem_slots(int KP, int WMAX, bool dc = false) {
+    return 2 * (2 * KP + (dc ? 1 : 0)) * (WMAX + 1);
 }
 
 // One strip x band tile (bx, by) of one image, for one chunk of harmonics.
@@ -175,11 +243,17 @@ __host__ __device__ constexpr int sys_smem_slots(int KP, int WMAX) {
 // (adjoint, last chunk only). KAHAN compensates the vertical running sums.
 // zo: element offset of this image in the image-sized buffers (and quad
 // offset in the saved buffer).
-template <int KP, bool BWD, bool SAVE, bool KAHAN, int WMAX, typename Tin>
+template <int KP, bool BWD, bool SAVE, bool KAHAN, int WMAX, typename Tin, bool HALF = false,
+          int SEED = 0>
 __device__ __forceinline__ void sys_tile(const SysParams& p, int bx, int by, size_t zo,
                                          float4* smem, float& gsum) {
+    // SEED 2 (even N): the constant harmonic k = 0 runs apart from the pairs
+    // (planes f and 1, or alpha in the adjoint: its k = 0 phase terms vanish),
+    // and pair i holds harmonics 4i + 2, 4i + 4, i.e. coefficients CO + 2i.
+    constexpr bool DC = SEED == 2;
+    constexpr int CO = DC ? 1 : 0;
     constexpr int LD = WMAX + 1;          // row of one plane in shared memory
-    constexpr int BUF = 2 * KP * LD;      // one step-parity buffer
+    constexpr int BUF = (2 * KP + (DC ? 1 : 0)) * LD;  // one step-parity buffer
     const int Wi = blockDim.x;
     const int j = threadIdx.x;
     const int w = j >> 5;
@@ -207,10 +281,11 @@ __device__ __forceinline__ void sys_tile(const SysParams& p, int bx, int by, siz
         b.bsv = p.bsv + zo;
     }
 
-    for (int i = threadIdx.x; i < sys_smem_slots(KP, WMAX); i += Wi)
+    for (int i = threadIdx.x; i < sys_smem_slots(KP, WMAX, DC); i += Wi)
         smem[i] = make_float4(0.f, 0.f, 0.f, 0.f);
 
     float2 Dx[KP], Dy[KP], Dz[KP], Dw[KP];
+    float Dfa = 0.f, Dfz = 0.f;  // DC planes (f or alpha, and 1)
     float2 Ex[KAHAN ? KP : 1], Ey[KAHAN ? KP : 1], Ez[KAHAN ? KP : 1], Ew[KAHAN ? KP : 1];
 #pragma unroll
     for (int i = 0; i < KP; ++i) {
@@ -259,11 +334,13 @@ __device__ __forceinline__ void sys_tile(const SysParams& p, int bx, int by, siz
         if (warp_last >= 0 && warp_first < span) {
             const Geo gc = g;  // geometry of this step
             const Px<BWD> c0 = v0, c1 = v1, c2v = v2, c3 = v3, cc = vc;
-            // pull the entering row of a later step into L2 (no registers held):
-            // the other four streams re-read pixels the strip touched recently
+            // pull the entering row of a later step into L2 (no registers held;
+            // only rows that enter this band's window, so nothing past the
+            // band is fetched): the other four streams re-read pixels the
+            // strip touched recently
             {
                 const int ef = e0 + t + PREFETCH_ROWS;
-                if (own_in && ef >= 0 && ef < p.H) {
+                if (own_in && (unsigned)(ef - elo) < (unsigned)ne) {
                     if constexpr (!BWD) {
                         prefetch_l2(b.img + ef * W + cw);
                     } else {
@@ -309,8 +386,8 @@ __device__ __forceinline__ void sys_tile(const SysParams& p, int bx, int by, siz
             // the centre pixel's recombination of pair i with its box sums h
             auto combine = [&](const Strm& sc, int i, float2 hx, float2 hy, float2 hz,
                                float2 hw) {
-                const float2 A2 = make_float2(p.a[2 * i], p.a[2 * i + 1]);
-                const float2 AK2 = make_float2(p.ak[2 * i], p.ak[2 * i + 1]);
+                const float2 A2 = make_float2(p.a[CO + 2 * i], p.a[CO + 2 * i + 1]);
+                const float2 AK2 = make_float2(p.ak[CO + 2 * i], p.ak[CO + 2 * i + 1]);
                 const float2 nzs = __fmul2_rn(sc.s, dup(-1.f));
                 if constexpr (!BWD) {
                     NUM = __ffma2_rn(A2, __ffma2_rn(sc.c, hx, __fmul2_rn(sc.s, hy)), NUM);
@@ -327,93 +404,141 @@ __device__ __forceinline__ void sys_tile(const SysParams& p, int bx, int by, siz
                     DEN = __ffma2_rn(AK2, __ffma2_rn(FC, pp, qq), DEN);
                 }
             };
-            if constexpr (!BWD && !KAHAN) {
-                // forward: the vertical running sums one stream at a time (only
-                // that stream's recurrence is live, and its harmonic pairs update
+            // the same for the one harmonic of the half pair (first components)
+            auto combine1 = [&](const Strm& sc, int i, float hx, float hy, float hz, float hw) {
+                const float a = p.a[CO + 2 * i], ak = p.ak[CO + 2 * i];
+                const float c = sc.c.x, sn = sc.s.x;
+                if constexpr (!BWD) {
+                    NUM.x = fmaf(a, fmaf(c, hx, sn * hy), NUM.x);
+                    DEN.x = fmaf(a, fmaf(c, hz, sn * hw), DEN.x);
+                    if constexpr (SAVE) {
+                        DNUM.x = fmaf(ak, fmaf(c, hy, -sn * hx), DNUM.x);
+                        DDEN.x = fmaf(ak, fmaf(c, hw, -sn * hz), DDEN.x);
+                    }
+                } else {
+                    NUM.x = fmaf(a, fmaf(hx, c, hy * sn), NUM.x);
+                    const float pp = fmaf(hy, c, -hx * sn);
+                    const float qq = fmaf(hw, c, -hz * sn);
+                    DEN.x = fmaf(ak, fmaf(FC.x, pp, qq), DEN.x);
+                }
+            };
+            if constexpr (!KAHAN) {
+                // the vertical running sums one stream at a time (only that
+                // stream's recurrence is live, and its harmonic pairs update
                 // independent sums), then the horizontal step and the centre
                 auto accumulate = [&](float f, float2 U, float2 V) {
-                    Strm q = seed(f, p.gamma, p.k0);
+                    if constexpr (DC) {
+                        Dfa += U.x;
+                        if constexpr (!BWD) Dfz += V.x;
+                    }
+                    Strm q = seed<SEED>(f, p.gamma, p.k0);
 #pragma unroll
                     for (int i = 0; i < KP; ++i) {
-                        Dx[i] = __ffma2_rn(q.c, U, Dx[i]);
-                        Dy[i] = __ffma2_rn(q.s, U, Dy[i]);
-                        Dz[i] = __ffma2_rn(q.c, V, Dz[i]);
-                        Dw[i] = __ffma2_rn(q.s, V, Dw[i]);
-                        if (i + 1 < KP) advance(q, i, i + 2 < KP);
+                        if (HALF && i == KP - 1) {
+                            Dx[i].x = fmaf(q.c.x, U.x, Dx[i].x);
+                            Dy[i].x = fmaf(q.s.x, U.x, Dy[i].x);
+                            Dz[i].x = fmaf(q.c.x, V.x, Dz[i].x);
+                            Dw[i].x = fmaf(q.s.x, V.x, Dw[i].x);
+                        } else {
+                            Dx[i] = __ffma2_rn(q.c, U, Dx[i]);
+                            Dy[i] = __ffma2_rn(q.s, U, Dy[i]);
+                            Dz[i] = __ffma2_rn(q.c, V, Dz[i]);
+                            Dw[i] = __ffma2_rn(q.s, V, Dw[i]);
+                        }
+                        if (i + 1 < KP) advance(q, i, i + 2 < KP, HALF && i + 2 == KP - 1);
                     }
                 };
                 accumulate(pix_f(c0), U0, V0);
                 accumulate(pix_f(c1), U1, V1);
                 accumulate(pix_f(c2v), U2, V2);
                 accumulate(pix_f(c3), U3, V3);
-                Strm sc = seed(pix_f(cc), p.gamma, p.k0);
+                Strm sc = seed<SEED>(pix_f(cc), p.gamma, p.k0);
+                if constexpr (DC) {
+                    // box sums of the constant harmonic: C_0 = 1, S_0 = 0
+                    const float4 A = rd[(2 * KP) * LD];
+                    const float hf = A.x + Dfa;
+                    const float h1 = BWD ? 0.f : A.z + Dfz;
+                    wr[(2 * KP) * LD] = make_float4(hf, 0.f, h1, 0.f);
+                    NUM.x = fmaf(p.a[0], hf, NUM.x);
+                    if constexpr (!BWD) DEN.x = fmaf(p.a[0], h1, DEN.x);
+                }
+                // adjoint: the left neighbour's sums of pair i + PF are loaded
+                // before this lane stores pair i (the two step-parity buffers
+                // never overlap), so the loads stay in flight across the stores
+                constexpr int PF = BWD ? 2 : 0;
+                float4 PA[KP], PB[KP];
+#pragma unroll
+                for (int i = 0; i < PF && i < KP; ++i) {
+                    PA[i] = rd[(2 * i) * LD];
+                    if (!(HALF && i == KP - 1)) PB[i] = rd[(2 * i + 1) * LD];
+                }
+#pragma unroll
+                for (int i = 0; i < KP; ++i) {
+                    if (PF > 0 && i + PF < KP) {
+                        PA[i + PF] = rd[(2 * (i + PF)) * LD];
+                        if (!(HALF && i + PF == KP - 1)) PB[i + PF] = rd[(2 * (i + PF) + 1) * LD];
+                    }
+                    if (HALF && i == KP - 1) {
+                        // one float4 per lane: (P, Q, U, V) of the single harmonic
+                        const float4 A = PF > 0 ? PA[i] : rd[(2 * i) * LD];
+                        const float hx = A.x + Dx[i].x, hy = A.y + Dy[i].x;
+                        const float hz = A.z + Dz[i].x, hw = A.w + Dw[i].x;
+                        wr[(2 * i) * LD] = make_float4(hx, hy, hz, hw);
+                        combine1(sc, i, hx, hy, hz, hw);
+                    } else {
+                        const float4 A = PF > 0 ? PA[i] : rd[(2 * i) * LD];
+                        const float4 B = PF > 0 ? PB[i] : rd[(2 * i + 1) * LD];
+                        const float2 hx = __fadd2_rn(make_float2(A.x, A.y), Dx[i]);
+                        const float2 hy = __fadd2_rn(make_float2(A.z, A.w), Dy[i]);
+                        const float2 hz = __fadd2_rn(make_float2(B.x, B.y), Dz[i]);
+                        const float2 hw = __fadd2_rn(make_float2(B.z, B.w), Dw[i]);
+                        wr[(2 * i) * LD] = make_float4(hx.x, hx.y, hy.x, hy.y);
+                        wr[(2 * i + 1) * LD] = make_float4(hz.x, hz.y, hw.x, hw.y);
+                        combine(sc, i, hx, hy, hz, hw);
+                    }
+                    if (i + 1 < KP) advance(sc, i, i + 2 < KP, HALF && i + 2 == KP - 1);
+                }
+            } else {
+                // Kahan (forward): all five streams advance together, pair by
+                // pair, so the four streams' increments of a row are formed
+                // together and added once with compensation
+                static_assert(!HALF && !BWD && !DC,
+                              "the Kahan form runs whole pairs from k0, forward only");
+                Strm s0 = seed<SEED>(pix_f(c0), p.gamma, p.k0);
+                Strm s1 = seed<SEED>(pix_f(c1), p.gamma, p.k0);
+                Strm s2 = seed<SEED>(pix_f(c2v), p.gamma, p.k0);
+                Strm s3 = seed<SEED>(pix_f(c3), p.gamma, p.k0);
+                Strm sc = seed<SEED>(pix_f(cc), p.gamma, p.k0);
 #pragma unroll
                 for (int i = 0; i < KP; ++i) {
                     const float4 A = rd[(2 * i) * LD];
                     const float4 B = rd[(2 * i + 1) * LD];
+                    // this row's increment of each running sum, then a
+                    // Kahan-compensated add (Kahan 1965): y = inc - e,
+                    // t = D + y, e = (t - D) - y, D = t
+                    const float2 m1 = dup(-1.f);
+                    float2 ix = __fmul2_rn(s0.c, U0), iy = __fmul2_rn(s0.s, U0);
+                    float2 iz = __fmul2_rn(s0.c, V0), iw = __fmul2_rn(s0.s, V0);
+                    ix = __ffma2_rn(s1.c, U1, ix); ix = __ffma2_rn(s2.c, U2, ix);
+                    ix = __ffma2_rn(s3.c, U3, ix);
+                    iy = __ffma2_rn(s1.s, U1, iy); iy = __ffma2_rn(s2.s, U2, iy);
+                    iy = __ffma2_rn(s3.s, U3, iy);
+                    iz = __ffma2_rn(s1.c, V1, iz); iz = __ffma2_rn(s2.c, V2, iz);
+                    iz = __ffma2_rn(s3.c, V3, iz);
+                    iw = __ffma2_rn(s1.s, V1, iw); iw = __ffma2_rn(s2.s, V2, iw);
+                    iw = __ffma2_rn(s3.s, V3, iw);
+                    auto kadd = [&](float2& D, float2& E, float2 inc) {
+                        const float2 y = __ffma2_rn(E, m1, inc);
+                        const float2 t2 = __fadd2_rn(D, y);
+                        E = __ffma2_rn(y, m1, __ffma2_rn(D, m1, t2));
+                        D = t2;
+                    };
+                    kadd(Dx[i], Ex[i], ix); kadd(Dy[i], Ey[i], iy);
+                    kadd(Dz[i], Ez[i], iz); kadd(Dw[i], Ew[i], iw);
                     const float2 hx = __fadd2_rn(make_float2(A.x, A.y), Dx[i]);
                     const float2 hy = __fadd2_rn(make_float2(A.z, A.w), Dy[i]);
                     const float2 hz = __fadd2_rn(make_float2(B.x, B.y), Dz[i]);
                     const float2 hw = __fadd2_rn(make_float2(B.z, B.w), Dw[i]);
-                    wr[(2 * i) * LD] = make_float4(hx.x, hx.y, hy.x, hy.y);
-                    wr[(2 * i + 1) * LD] = make_float4(hz.x, hz.y, hw.x, hw.y);
-                    combine(sc, i, hx, hy, hz, hw);
-                    if (i + 1 < KP) advance(sc, i, i + 2 < KP);
-                }
-            } else {
-                // adjoint and Kahan: all five streams advance together, pair by
-                // pair (Kahan compensates one add per row and sum, so the four
-                // streams' increments are formed together)
-                Strm s0 = seed(pix_f(c0), p.gamma, p.k0);
-                Strm s1 = seed(pix_f(c1), p.gamma, p.k0);
-                Strm s2 = seed(pix_f(c2v), p.gamma, p.k0);
-                Strm s3 = seed(pix_f(c3), p.gamma, p.k0);
-                Strm sc = seed(pix_f(cc), p.gamma, p.k0);
-#pragma unroll
-                for (int i = 0; i < KP; ++i) {
-                    const float4 A = rd[(2 * i) * LD];
-                    const float4 B = rd[(2 * i + 1) * LD];
-                    float2 dx, dy, dz, dw;
-                    if constexpr (!KAHAN) {
-                        dx = Dx[i]; dy = Dy[i]; dz = Dz[i]; dw = Dw[i];
-                        dx = __ffma2_rn(s0.c, U0, dx); dx = __ffma2_rn(s1.c, U1, dx);
-                        dx = __ffma2_rn(s2.c, U2, dx); dx = __ffma2_rn(s3.c, U3, dx);
-                        dy = __ffma2_rn(s0.s, U0, dy); dy = __ffma2_rn(s1.s, U1, dy);
-                        dy = __ffma2_rn(s2.s, U2, dy); dy = __ffma2_rn(s3.s, U3, dy);
-                        dz = __ffma2_rn(s0.c, V0, dz); dz = __ffma2_rn(s1.c, V1, dz);
-                        dz = __ffma2_rn(s2.c, V2, dz); dz = __ffma2_rn(s3.c, V3, dz);
-                        dw = __ffma2_rn(s0.s, V0, dw); dw = __ffma2_rn(s1.s, V1, dw);
-                        dw = __ffma2_rn(s2.s, V2, dw); dw = __ffma2_rn(s3.s, V3, dw);
-                    } else {
-                        // this row's increment of each running sum, then a
-                        // Kahan-compensated add (Kahan 1965): y = inc - e,
-                        // t = D + y, e = (t - D) - y, D = t
-                        const float2 m1 = dup(-1.f);
-                        float2 ix = __fmul2_rn(s0.c, U0), iy = __fmul2_rn(s0.s, U0);
-                        float2 iz = __fmul2_rn(s0.c, V0), iw = __fmul2_rn(s0.s, V0);
-                        ix = __ffma2_rn(s1.c, U1, ix); ix = __ffma2_rn(s2.c, U2, ix);
-                        ix = __ffma2_rn(s3.c, U3, ix);
-                        iy = __ffma2_rn(s1.s, U1, iy); iy = __ffma2_rn(s2.s, U2, iy);
-                        iy = __ffma2_rn(s3.s, U3, iy);
-                        iz = __ffma2_rn(s1.c, V1, iz); iz = __ffma2_rn(s2.c, V2, iz);
-                        iz = __ffma2_rn(s3.c, V3, iz);
-                        iw = __ffma2_rn(s1.s, V1, iw); iw = __ffma2_rn(s2.s, V2, iw);
-                        iw = __ffma2_rn(s3.s, V3, iw);
-                        auto kadd = [&](float2& D, float2& E, float2 inc) {
-                            const float2 y = __ffma2_rn(E, m1, inc);
-                            const float2 t2 = __fadd2_rn(D, y);
-                            E = __ffma2_rn(y, m1, __ffma2_rn(D, m1, t2));
-                            D = t2;
-                        };
-                        kadd(Dx[i], Ex[i], ix); kadd(Dy[i], Ey[i], iy);
-                        kadd(Dz[i], Ez[i], iz); kadd(Dw[i], Ew[i], iw);
-                        dx = Dx[i]; dy = Dy[i]; dz = Dz[i]; dw = Dw[i];
-                    }
-                    Dx[i] = dx; Dy[i] = dy; Dz[i] = dz; Dw[i] = dw;
-                    const float2 hx = __fadd2_rn(make_float2(A.x, A.y), dx);
-                    const float2 hy = __fadd2_rn(make_float2(A.z, A.w), dy);
-                    const float2 hz = __fadd2_rn(make_float2(B.x, B.y), dz);
-                    const float2 hw = __fadd2_rn(make_float2(B.z, B.w), dw);
                     wr[(2 * i) * LD] = make_float4(hx.x, hx.y, hy.x, hy.y);
                     wr[(2 * i + 1) * LD] = make_float4(hz.x, hz.y, hw.x, hw.y);
                     combine(sc, i, hx, hy, hz, hw);
@@ -490,23 +615,25 @@ __device__ __forceinline__ void cta_sum_to(float gsum, float* partial, int slot)
 
 // One CTA per tile. WMAX = largest strip width (threads) of the instantiation:
 // 128-thread strips run two CTAs per SM, 256-thread strips one.
-template <int KP, bool BWD, bool SAVE, bool KAHAN, int WMAX, typename Tin>
+template <int KP, bool BWD, bool SAVE, bool KAHAN, int WMAX, typename Tin, bool HALF = false,
+          int SEED = 0>
 __global__ void __launch_bounds__(WMAX, 256 / WMAX) bf_sys_kernel(SysParams p) {
     extern __shared__ float4 smem[];
     float gsum = 0.f;
     const size_t z = blockIdx.z;  // image of a [B, H, W] launch
     const size_t hw = (size_t)p.H * p.W;
-    sysd::sys_tile<KP, BWD, SAVE, KAHAN, WMAX, Tin>(p, blockIdx.x, blockIdx.y, z * hw, smem,
-                                                    gsum);
+    sysd::sys_tile<KP, BWD, SAVE, KAHAN, WMAX, Tin, HALF, SEED>(p, blockIdx.x, blockIdx.y,
+                                                                z * hw, smem, gsum);
     if (BWD && p.partial)
         sysd::cta_sum_to(gsum, p.partial, (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x);
 }
 
-template <int KP, bool BWD, bool SAVE, bool KAHAN, int WMAX, typename Tin>
+template <int KP, bool BWD, bool SAVE, bool KAHAN, int WMAX, typename Tin, bool HALF = false,
+          int SEED = 0>
 cudaError_t sys_launch_one(const SysParams& p, int wi, int gx, int gy, cudaStream_t s) {
     const int gz = p.B > 0 ? p.B : 1;
-    auto kern = bf_sys_kernel<KP, BWD, SAVE, KAHAN, WMAX, Tin>;
-    const size_t smem = sizeof(float4) * (size_t)sysd::sys_smem_slots(KP, WMAX);
+    auto kern = bf_sys_kernel<KP, BWD, SAVE, KAHAN, WMAX, Tin, HALF, SEED>;
+    const size_t smem = sizeof(float4) * (size_t)sysd::sys_smem_slots(KP, WMAX, SEED == 2);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
