@@ -244,7 +244,7 @@ __host__ __device__ constexpr int sys_smem_slots(int KP, int WMAX, bool dc = fal
 // zo: element offset of this image in the image-sized buffers (and quad
 // offset in the saved buffer).
 template <int KP, bool BWD, bool SAVE, bool KAHAN, int WMAX, typename Tin, bool HALF = false,
-          int SEED = 0>
+          int SEED = 0, int FORM = 0>
 __device__ __forceinline__ void sys_tile(const SysParams& p, int bx, int by, size_t zo,
                                          float4* smem, float& gsum) {
     // SEED 2 (even N): the constant harmonic k = 0 runs apart from the pairs
@@ -422,7 +422,7 @@ __device__ __forceinline__ void sys_tile(const SysParams& p, int bx, int by, siz
                     DEN.x = fmaf(ak, fmaf(FC.x, pp, qq), DEN.x);
                 }
             };
-            if constexpr (!KAHAN) {
+            if constexpr (!KAHAN && FORM != 1) {
                 // the vertical running sums one stream at a time (only that
                 // stream's recurrence is live, and its harmonic pairs update
                 // independent sums), then the horizontal step and the centre
@@ -462,10 +462,10 @@ __device__ __forceinline__ void sys_tile(const SysParams& p, int bx, int by, siz
                     NUM.x = fmaf(p.a[0], hf, NUM.x);
                     if constexpr (!BWD) DEN.x = fmaf(p.a[0], h1, DEN.x);
                 }
-                // adjoint: the left neighbour's sums of pair i + PF are loaded
+                // FORM 2 / 3: the left neighbour's sums of pair i + PF are loaded
                 // before this lane stores pair i (the two step-parity buffers
                 // never overlap), so the loads stay in flight across the stores
-                constexpr int PF = BWD ? 2 : 0;
+                constexpr int PF = FORM == 2 ? 2 : (FORM == 3 ? 1 : 0);
                 float4 PA[KP], PB[KP];
 #pragma unroll
                 for (int i = 0; i < PF && i < KP; ++i) {
@@ -497,6 +497,74 @@ __device__ __forceinline__ void sys_tile(const SysParams& p, int bx, int by, siz
                         combine(sc, i, hx, hy, hz, hw);
                     }
                     if (i + 1 < KP) advance(sc, i, i + 2 < KP, HALF && i + 2 == KP - 1);
+                }
+            } else if constexpr (FORM == 1) {
+                // all five streams advance together, pair by pair: the four
+                // streams' updates of pair i sit between the load of the left
+                // neighbour's sums of pair i and their use
+                Strm s0 = seed<SEED>(pix_f(c0), p.gamma, p.k0);
+                Strm s1 = seed<SEED>(pix_f(c1), p.gamma, p.k0);
+                Strm s2 = seed<SEED>(pix_f(c2v), p.gamma, p.k0);
+                Strm s3 = seed<SEED>(pix_f(c3), p.gamma, p.k0);
+                Strm sc = seed<SEED>(pix_f(cc), p.gamma, p.k0);
+                if constexpr (DC) {
+                    const float4 A = rd[(2 * KP) * LD];
+                    // the same order of adds as the sequential form
+                    Dfa += U0.x; Dfa += U1.x; Dfa += U2.x; Dfa += U3.x;
+                    const float hf = A.x + Dfa;
+                    float h1 = 0.f;
+                    if constexpr (!BWD) {
+                        Dfz += V0.x; Dfz += V1.x; Dfz += V2.x; Dfz += V3.x;
+                        h1 = A.z + Dfz;
+                    }
+                    wr[(2 * KP) * LD] = make_float4(hf, 0.f, h1, 0.f);
+                    NUM.x = fmaf(p.a[0], hf, NUM.x);
+                    if constexpr (!BWD) DEN.x = fmaf(p.a[0], h1, DEN.x);
+                }
+#pragma unroll
+                for (int i = 0; i < KP; ++i) {
+                    if (HALF && i == KP - 1) {
+                        const float4 A = rd[(2 * i) * LD];
+                        float dx = Dx[i].x, dy = Dy[i].x, dz = Dz[i].x, dw = Dw[i].x;
+                        dx = fmaf(s0.c.x, U0.x, dx); dx = fmaf(s1.c.x, U1.x, dx);
+                        dx = fmaf(s2.c.x, U2.x, dx); dx = fmaf(s3.c.x, U3.x, dx);
+                        dy = fmaf(s0.s.x, U0.x, dy); dy = fmaf(s1.s.x, U1.x, dy);
+                        dy = fmaf(s2.s.x, U2.x, dy); dy = fmaf(s3.s.x, U3.x, dy);
+                        dz = fmaf(s0.c.x, V0.x, dz); dz = fmaf(s1.c.x, V1.x, dz);
+                        dz = fmaf(s2.c.x, V2.x, dz); dz = fmaf(s3.c.x, V3.x, dz);
+                        dw = fmaf(s0.s.x, V0.x, dw); dw = fmaf(s1.s.x, V1.x, dw);
+                        dw = fmaf(s2.s.x, V2.x, dw); dw = fmaf(s3.s.x, V3.x, dw);
+                        Dx[i].x = dx; Dy[i].x = dy; Dz[i].x = dz; Dw[i].x = dw;
+                        const float hx = A.x + dx, hy = A.y + dy, hz = A.z + dz, hw = A.w + dw;
+                        wr[(2 * i) * LD] = make_float4(hx, hy, hz, hw);
+                        combine1(sc, i, hx, hy, hz, hw);
+                    } else {
+                        const float4 A = rd[(2 * i) * LD];
+                        const float4 B = rd[(2 * i + 1) * LD];
+                        float2 dx = Dx[i], dy = Dy[i], dz = Dz[i], dw = Dw[i];
+                        dx = __ffma2_rn(s0.c, U0, dx); dx = __ffma2_rn(s1.c, U1, dx);
+                        dx = __ffma2_rn(s2.c, U2, dx); dx = __ffma2_rn(s3.c, U3, dx);
+                        dy = __ffma2_rn(s0.s, U0, dy); dy = __ffma2_rn(s1.s, U1, dy);
+                        dy = __ffma2_rn(s2.s, U2, dy); dy = __ffma2_rn(s3.s, U3, dy);
+                        dz = __ffma2_rn(s0.c, V0, dz); dz = __ffma2_rn(s1.c, V1, dz);
+                        dz = __ffma2_rn(s2.c, V2, dz); dz = __ffma2_rn(s3.c, V3, dz);
+                        dw = __ffma2_rn(s0.s, V0, dw); dw = __ffma2_rn(s1.s, V1, dw);
+                        dw = __ffma2_rn(s2.s, V2, dw); dw = __ffma2_rn(s3.s, V3, dw);
+                        Dx[i] = dx; Dy[i] = dy; Dz[i] = dz; Dw[i] = dw;
+                        const float2 hx = __fadd2_rn(make_float2(A.x, A.y), dx);
+                        const float2 hy = __fadd2_rn(make_float2(A.z, A.w), dy);
+                        const float2 hz = __fadd2_rn(make_float2(B.x, B.y), dz);
+                        const float2 hw = __fadd2_rn(make_float2(B.z, B.w), dw);
+                        wr[(2 * i) * LD] = make_float4(hx.x, hx.y, hy.x, hy.y);
+                        wr[(2 * i + 1) * LD] = make_float4(hz.x, hz.y, hw.x, hw.y);
+                        combine(sc, i, hx, hy, hz, hw);
+                    }
+                    if (i + 1 < KP) {
+                        const bool need = i + 2 < KP, hn = HALF && i + 2 == KP - 1;
+                        advance(s0, i, need, hn); advance(s1, i, need, hn);
+                        advance(s2, i, need, hn); advance(s3, i, need, hn);
+                        advance(sc, i, need, hn);
+                    }
                 }
             } else {
                 // Kahan (forward): all five streams advance together, pair by
@@ -616,23 +684,23 @@ __device__ __forceinline__ void cta_sum_to(float gsum, float* partial, int slot)
 // One CTA per tile. WMAX = largest strip width (threads) of the instantiation:
 // 128-thread strips run two CTAs per SM, 256-thread strips one.
 template <int KP, bool BWD, bool SAVE, bool KAHAN, int WMAX, typename Tin, bool HALF = false,
-          int SEED = 0>
+          int SEED = 0, int FORM = 0>
 __global__ void __launch_bounds__(WMAX, 256 / WMAX) bf_sys_kernel(SysParams p) {
     extern __shared__ float4 smem[];
     float gsum = 0.f;
     const size_t z = blockIdx.z;  // image of a [B, H, W] launch
     const size_t hw = (size_t)p.H * p.W;
-    sysd::sys_tile<KP, BWD, SAVE, KAHAN, WMAX, Tin, HALF, SEED>(p, blockIdx.x, blockIdx.y,
-                                                                z * hw, smem, gsum);
+    sysd::sys_tile<KP, BWD, SAVE, KAHAN, WMAX, Tin, HALF, SEED, FORM>(p, blockIdx.x, blockIdx.y,
+                                                                      z * hw, smem, gsum);
     if (BWD && p.partial)
         sysd::cta_sum_to(gsum, p.partial, (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x);
 }
 
 template <int KP, bool BWD, bool SAVE, bool KAHAN, int WMAX, typename Tin, bool HALF = false,
-          int SEED = 0>
+          int SEED = 0, int FORM = 0>
 cudaError_t sys_launch_one(const SysParams& p, int wi, int gx, int gy, cudaStream_t s) {
     const int gz = p.B > 0 ? p.B : 1;
-    auto kern = bf_sys_kernel<KP, BWD, SAVE, KAHAN, WMAX, Tin, HALF, SEED>;
+    auto kern = bf_sys_kernel<KP, BWD, SAVE, KAHAN, WMAX, Tin, HALF, SEED, FORM>;
     const size_t smem = sizeof(float4) * (size_t)sysd::sys_smem_slots(KP, WMAX, SEED == 2);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);

@@ -9,14 +9,44 @@
 
 namespace bf {
 
+// Form of the step body per launch mode, seed (odd / even N), pair count and
+// half pair: 0 = the four vertical streams one after another, then the
+// centre; 1 = all five streams pair by pair; 2 / 3 = form 0 with the left
+// neighbour's sums loaded two / one pair ahead of this lane's stores. The
+// forms compute the same sums in the same order; they differ only in
+// instruction schedule, and the fastest one differs between instantiations
+// by up to 1.9x. Each entry is the fastest of the four on a GB300 at
+// 4096^2, r = 10 (median of 12 launches with L2 flushed, every N = 2..43;
+// form 0 is kept unless another is at least 2 % faster).
+constexpr unsigned char kFirstForm[3][2][11][2] = {
+    // plain forward
+    {
+        {{0, 0}, {0, 2}, {0, 2}, {0, 0}, {0, 0}, {2, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}},
+        {{0, 0}, {2, 0}, {0, 0}, {0, 1}, {1, 3}, {0, 0}, {0, 0}, {0, 0}, {0, 1}, {0, 0}, {0, 0}},
+    },
+    // forward with saved quads
+    {
+        {{3, 0}, {3, 3}, {0, 3}, {0, 3}, {0, 3}, {1, 1}, {0, 0}, {0, 0}, {0, 0}, {1, 0}, {0, 0}},
+        {{3, 3}, {0, 3}, {1, 0}, {3, 1}, {0, 3}, {1, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}},
+    },
+    // adjoint
+    {
+        {{0, 0}, {3, 0}, {0, 2}, {2, 2}, {2, 2}, {2, 2}, {0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}},
+        {{0, 0}, {0, 0}, {2, 0}, {3, 0}, {2, 2}, {0, 0}, {0, 0}, {1, 0}, {0, 0}, {0, 0}, {0, 1}},
+    },
+};
+
 template <int KP, bool HALF, int SEED>
 cudaError_t sys_first_modes(const SysParams& p, int mode, int wi, int gx, int gy,
                             cudaStream_t s) {
+    constexpr int F0 = kFirstForm[0][SEED - 1][KP - 1][HALF];
+    constexpr int F1 = kFirstForm[1][SEED - 1][KP - 1][HALF];
+    constexpr int F2 = kFirstForm[2][SEED - 1][KP - 1][HALF];
     if (mode == 2)
-        return sys_launch_one<KP, true, false, false, 128, float, HALF, SEED>(p, wi, gx, gy, s);
+        return sys_launch_one<KP, true, false, false, 128, float, HALF, SEED, F2>(p, wi, gx, gy, s);
     if (mode == 1)
-        return sys_launch_one<KP, false, true, false, 128, float, HALF, SEED>(p, wi, gx, gy, s);
-    return sys_launch_one<KP, false, false, false, 128, float, HALF, SEED>(p, wi, gx, gy, s);
+        return sys_launch_one<KP, false, true, false, 128, float, HALF, SEED, F1>(p, wi, gx, gy, s);
+    return sys_launch_one<KP, false, false, false, 128, float, HALF, SEED, F0>(p, wi, gx, gy, s);
 }
 
 template <int KP>

@@ -4,7 +4,7 @@
 namespace bf {
 
 #define BF_SYS_MODES(KP, T)                                                               \
-    if (mode == 2) return sys_launch_one<KP, true, false, false, 128, T>(p, wi, gx, gy, s); \
+    if (mode == 2) return sys_launch_one<KP, true, false, false, 128, T, false, 0, 1>(p, wi, gx, gy, s); \
     if (mode == 1) return sys_launch_one<KP, false, true, false, 128, T>(p, wi, gx, gy, s); \
     return sys_launch_one<KP, false, false, false, 128, T>(p, wi, gx, gy, s);
 #define BF_SYS_CASE(KP)                              \
