@@ -21,9 +21,18 @@
  * pixels only).
  *
  * Conventions shared by every call below:
- *  - Image pointers are DEVICE pointers to row-major H x W arrays with row
- *    pitch W elements, unless the name says _host. The caller owns every
- *    buffer; no call allocates device memory.
+ *  - Image pointers are DEVICE pointers to row-major H x W arrays, unless the
+ *    name says _host. Rows of the image buffers (img, out, grad_out, grad_img,
+ *    den) lie `pitch` elements apart: bf_opts.pitch for bf_forward /
+ *    bf_backward and their [B, H, W] forms (image b then starts b * H * pitch
+ *    elements in), bf_desc.pitch for bf_batch; 0 means W (a compact image),
+ *    and a pitch below W is BF_ERR_INVALID_ARG. A pitch lets a caller filter a
+ *    region of a larger image, or a strided tensor view, without a copy:
+ *    elements between W and pitch in each row are neither read nor written.
+ *    The saved quads, workspaces and the variant filters (bf_spatial_*,
+ *    bf_poly_*, which reject a pitch other than 0 or W with
+ *    BF_ERR_UNSUPPORTED) are always compact. The caller owns every buffer; no
+ *    call allocates device memory.
  *  - `stream` is a cudaStream_t (NULL = the legacy default stream). Calls are
  *    asynchronous on it and never synchronise the host.
  *  - Argument checks run before any launch; on a failed check nothing is
@@ -92,13 +101,18 @@ typedef struct {
                              anywhere on [-T, T], may dip below 0 by as much, and
                              den >= 1/2 still holds. Forward and backward calls
                              must pass the same value. See bf_trunc_harmonics. */
+    int pitch;            /* row pitch of the image buffers in elements; 0 = W */
 } bf_opts;
 
 /* One image of a batch (bf_batch). img/out/den are device pointers. */
 typedef struct {
     const void* img;      /* H x W, dtype opts->in_dtype */
     float* out;           /* H x W */
+    float* den;           /* NULL, or H x W receiving den(x), the normaliser eta(x) of
+                             Eq. filter2 (sum of the window's weights; >= 1 inside the
+                             precondition); must not alias img or out */
     int H, W;
+    int pitch;            /* row pitch of img, out and den in elements; 0 = W */
     int r;                /* spatial half-width, 0..BF_R_MAX */
     int N;                /* order; <= 0 derives it from sigma_r (bf_resolve_N) */
     float sigma_r;
@@ -224,16 +238,19 @@ bf_status bf_backward3d(const void* img, const float* out, const float* grad_out
  * holds until the process exits.
  *
  * Arguments and results are those of bf_backward without workspace/ws_bytes.
- * Errors: as bf_backward, plus BF_ERR_UNSUPPORTED when the call needs more
- * scratch than the array holds (bf_backward_workspace_bytes(H, W, r, sigma_r,
- * T, N, opts) > BF_NOALLOC_MAX_PARTIALS * sizeof(float); this includes every
- * N > 43, whose harmonic chunks need image-sized accumulators), checked
- * before any launch.
+ * Errors: as bf_backward, plus BF_ERR_UNSUPPORTED, checked before any launch,
+ * when the call needs more scratch than the array holds, i.e. when
+ * bf_backward_workspace_bytes(H, W, r, sigma_r, T, N, opts) exceeds
+ * BF_NOALLOC_MAX_PARTIALS * sizeof(float) (64 KiB): one float per CTA of the
+ * launch grid, plus, when the harmonics run in chunks (N > 43), two H x W
+ * float accumulators at a 256-byte aligned offset; so chunked calls are
+ * accepted only for small images (about 90 x 90 and below).
  *
- * Set-up: the first call on each device looks up the array's device address
- * (cudaGetSymbolAddress, with that device current) and keeps it; make that
- * first call before any stream capture. It allocates nothing: no cudaMalloc,
- * cudaFree or allocating library routine.
+ * Set-up: every call looks up the array's device address on the current
+ * device (cudaGetSymbolAddress, a host-side lookup), so a cudaDeviceReset
+ * does not leave it stale. The first call on a device may load the library's
+ * device code there; make it before any stream capture. The entry point
+ * allocates nothing: no cudaMalloc, cudaFree or allocating library routine.
  *
  * Sharing: every call on a device uses the same array, which keeps the last
  * call's contents. No slot needs to start at zero (each call writes every

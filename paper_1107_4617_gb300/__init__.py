@@ -51,12 +51,13 @@ class BfOpts(ctypes.Structure):
     _fields_ = [("kahan", ctypes.c_int), ("gamma_mode", ctypes.c_int),
                 ("in_dtype", ctypes.c_int), ("save_for_backward", ctypes.c_int),
                 ("tile_h", ctypes.c_int), ("tile_w", ctypes.c_int), ("kp_max", ctypes.c_int),
-                ("trunc_tol", ctypes.c_float)]
+                ("trunc_tol", ctypes.c_float), ("pitch", ctypes.c_int)]
 
 
 class BfDesc(ctypes.Structure):
-    _fields_ = [("img", ctypes.c_void_p), ("out", ctypes.c_void_p), ("H", ctypes.c_int),
-                ("W", ctypes.c_int), ("r", ctypes.c_int), ("N", ctypes.c_int),
+    _fields_ = [("img", ctypes.c_void_p), ("out", ctypes.c_void_p), ("den", ctypes.c_void_p),
+                ("H", ctypes.c_int), ("W", ctypes.c_int), ("pitch", ctypes.c_int),
+                ("r", ctypes.c_int), ("N", ctypes.c_int),
                 ("sigma_r", ctypes.c_float), ("T", ctypes.c_float)]
 
 
@@ -149,12 +150,13 @@ def _check(fn: str, status: int):
 
 
 def _opts(kahan=False, gamma_mode=GAMMA_FIXED, in_dtype=F32, save=False, tile_h=0, tile_w=0,
-          kp_max=0, trunc_tol=0.0):
+          kp_max=0, trunc_tol=0.0, pitch=0):
     o = BfOpts()
     o.kahan, o.gamma_mode, o.in_dtype = int(bool(kahan)), int(gamma_mode), int(in_dtype)
     o.save_for_backward, o.tile_h, o.tile_w = int(bool(save)), int(tile_h), int(tile_w)
     o.kp_max = int(kp_max)
     o.trunc_tol = float(trunc_tol)
+    o.pitch = int(pitch)
     return o
 
 
@@ -172,6 +174,42 @@ def _dptr(t, name):
     if not t.is_contiguous():
         raise ValueError(f"{name} must be contiguous")
     return ctypes.c_void_p(t.data_ptr())
+
+
+def _rows(t, name):
+    """Device pointer and row pitch (elements) of a CUDA tensor whose rows are
+    contiguous: [H, W] with strides (pitch, 1), or [B, H, W] with strides
+    (H * pitch, pitch, 1); pitch >= W. A compact tensor has pitch W."""
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dim() not in (2, 3) or t.stride(-1) != 1:
+        raise ValueError(f"{name} must be 2-D or 3-D with contiguous rows")
+    H, W = t.shape[-2], t.shape[-1]
+    pitch = t.stride(-2) if H > 1 else W
+    if pitch < W:
+        raise ValueError(f"{name}: rows overlap (pitch {pitch} < W {W})")
+    if t.dim() == 3 and t.shape[0] > 1 and t.stride(0) != H * pitch:
+        raise ValueError(f"{name}: images must be H * pitch elements apart")
+    return ctypes.c_void_p(t.data_ptr()), int(pitch)
+
+
+def _pitch_opts(opts, pitch):
+    """A copy of opts with its row pitch set."""
+    o = BfOpts()
+    ctypes.pointer(o)[0] = opts
+    o.pitch = int(pitch)
+    return o
+
+
+def _like_rows(t, pitch, dtype=None):
+    """An uninitialised tensor shaped like t whose rows lie pitch elements apart."""
+    import torch
+    dtype = dtype or torch.float32
+    if t.dim() == 2:
+        return torch.empty((t.shape[0], pitch), dtype=dtype, device=t.device)[:, :t.shape[1]]
+    B, H, W = t.shape
+    return torch.empty((B, H, pitch), dtype=dtype, device=t.device)[:, :, :W]
 
 
 def _check_bytes(t, need: int, name: str):
@@ -235,8 +273,10 @@ def bf_batch_workspace_bytes(descs, opts: BfOpts | None = None) -> int:
 
 def bf_forward(img, r: int, sigma_r: float, T: float = 1.0, N: int = 0, out=None,
                opts: BfOpts | None = None, saved=None, stream=None):
-    """Forward filter of a 2-D CUDA tensor (float32 or bfloat16) -> float32."""
-    import torch
+    """Forward filter of a 2-D CUDA tensor (float32 or bfloat16) -> float32.
+    img and out may be row-pitched views (e.g. a column slice of a wider
+    tensor); they must share one row pitch, which goes to the C ABI as
+    bf_opts.pitch."""
     if img.dim() != 2:
         raise ValueError("img must be 2-D (H, W)")
     H, W = img.shape
@@ -244,13 +284,17 @@ def bf_forward(img, r: int, sigma_r: float, T: float = 1.0, N: int = 0, out=None
         opts = _opts(in_dtype=_in_dtype(img))
     elif opts.in_dtype != _in_dtype(img):
         raise ValueError("opts.in_dtype does not match img.dtype")
+    pimg, pitch = _rows(img, "img")
     if out is None:
-        out = torch.empty((H, W), dtype=torch.float32, device=img.device)
-    _check_bytes(out, 4 * H * W, "out")
+        out = _like_rows(img, pitch)
+    pout, opitch = _rows(out, "out")
+    if tuple(out.shape) != (H, W) or opitch != pitch:
+        raise ValueError("out must be (H, W) with the row pitch of img")
     if saved is not None:
         _check_bytes(saved, bf_saved_bytes(H, W), "saved")
-    st = load().bf_forward(_dptr(img, "img"), H, W, int(r), float(sigma_r), float(T), int(N),
-                           _dptr(out, "out"), ctypes.byref(opts),
+    o = _pitch_opts(opts, pitch if pitch != W else 0)
+    st = load().bf_forward(pimg, H, W, int(r), float(sigma_r), float(T), int(N), pout,
+                           ctypes.byref(o),
                            _dptr(saved, "saved") if saved is not None else None,
                            _stream_handle(stream))
     _check("bf_forward", st)
@@ -260,21 +304,29 @@ def bf_forward(img, r: int, sigma_r: float, T: float = 1.0, N: int = 0, out=None
 def bf_backward(img, out, grad_out, saved, r: int, sigma_r: float, T: float = 1.0, N: int = 0,
                 grad_img=None, grad_sigma=None, workspace=None, opts: BfOpts | None = None,
                 stream=None):
-    """Adjoint pass; writes grad_img (H, W) and/or grad_sigma (1,) if given."""
+    """Adjoint pass; writes grad_img (H, W) and/or grad_sigma (1,) if given.
+    grad_out and grad_img may be row-pitched views sharing one row pitch
+    (bf_opts.pitch); the saved quads are compact."""
     H, W = img.shape
     if opts is None:
         opts = _opts(in_dtype=_in_dtype(img))
     ws_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
     _check_bytes(saved, bf_saved_bytes(H, W), "saved")
-    _check_bytes(grad_out, 4 * H * W, "grad_out")
+    pg, pitch = _rows(grad_out, "grad_out")
+    if tuple(grad_out.shape) != (H, W):
+        raise ValueError("grad_out must be (H, W)")
+    pgi = None
     if grad_img is not None:
-        _check_bytes(grad_img, 4 * H * W, "grad_img")
-    st = load().bf_backward(_dptr(img, "img"), _dptr(out, "out"), _dptr(grad_out, "grad_out"),
+        pgi, gpitch = _rows(grad_img, "grad_img")
+        if tuple(grad_img.shape) != (H, W) or gpitch != pitch:
+            raise ValueError("grad_img must be (H, W) with the row pitch of grad_out")
+    o = _pitch_opts(opts, pitch if pitch != W else 0)
+    st = load().bf_backward(ctypes.c_void_p(img.data_ptr()), ctypes.c_void_p(out.data_ptr()), pg,
                             _dptr(saved, "saved"), H, W, int(r), float(sigma_r), float(T), int(N),
-                            _dptr(grad_img, "grad_img") if grad_img is not None else None,
+                            pgi,
                             _dptr(grad_sigma, "grad_sigma") if grad_sigma is not None else None,
                             _dptr(workspace, "workspace") if workspace is not None else None,
-                            ws_bytes, ctypes.byref(opts), _stream_handle(stream))
+                            ws_bytes, ctypes.byref(o), _stream_handle(stream))
     _check("bf_backward", st)
 
 
@@ -431,12 +483,25 @@ def bf_backward3d(img, out, grad_out, saved, r: int, sigma_r: float, T: float = 
     _check("bf_backward3d", st)
 
 
-def make_descs(imgs, outs, rs, sigmas, T=1.0, Ns=None):
+def make_descs(imgs, outs, rs, sigmas, T=1.0, Ns=None, dens=None):
+    """Batch descriptors; each image, output (and den, if given) may be a
+    row-pitched view sharing one row pitch per image."""
     descs = []
     for i, (im, o) in enumerate(zip(imgs, outs)):
         d = BfDesc()
-        d.img, d.out = _dptr(im, "img").value, _dptr(o, "out").value
+        pi, pitch = _rows(im, "img")
+        po, opitch = _rows(o, "out")
+        if opitch != pitch or tuple(o.shape) != tuple(im.shape):
+            raise ValueError("out must match img in shape and row pitch")
+        d.img, d.out = pi.value, po.value
+        d.den = None
+        if dens is not None and dens[i] is not None:
+            pd, dpitch = _rows(dens[i], "den")
+            if dpitch != pitch or tuple(dens[i].shape) != tuple(im.shape):
+                raise ValueError("den must match img in shape and row pitch")
+            d.den = pd.value
         d.H, d.W = int(im.shape[0]), int(im.shape[1])
+        d.pitch = pitch if pitch != d.W else 0
         d.r, d.N = int(rs[i]), int(Ns[i]) if Ns is not None else 0
         d.sigma_r, d.T = float(sigmas[i]), float(T)
         descs.append(d)

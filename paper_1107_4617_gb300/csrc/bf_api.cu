@@ -120,7 +120,7 @@ static bf_status choose_tiles(int H, int W, int r, const bf_opts* o, Tiles* t) {
 // strips up to r = 40 (two CTAs per SM: measured faster than wider strips
 // with one CTA per SM even at r = 30, where half the lanes are halo),
 // 256-thread strips above. Bands: one wave of resident CTAs.
-static bool sys_tiles(int H, int W, int r, const bf_opts* o, Tiles* t) {
+static bool sys_tiles(int H, int W, int ld, int r, const bf_opts* o, Tiles* t) {
     int wi = (r <= 40) ? 128 : 256;
     if (o && o->tile_w > 0) {
         if (o->tile_w > SYS_MAX_THREADS || o->tile_w % 32 != 0) return false;
@@ -129,7 +129,7 @@ static bool sys_tiles(int H, int W, int r, const bf_opts* o, Tiles* t) {
     if (wi - 2 * r < 16) return false;
     // the engine addresses one image with 32-bit element offsets (rows of the
     // skew ramp above and below the image included)
-    if ((long long)(H + 2 * wi + 4 * r) * W >= 0x7fffffffLL) return false;
+    if ((long long)(H + 2 * wi + 4 * r) * (ld > W ? ld : W) >= 0x7fffffffLL) return false;
     t->nt = wi;
     t->Tw = wi - 2 * r;
     t->gx = (W + t->Tw - 1) / t->Tw;
@@ -152,7 +152,9 @@ static bool sys_tiles(int H, int W, int r, const bf_opts* o, Tiles* t) {
 static void fill_sys(const FwdParams& p, SysParams* q) {
     memset(q, 0, sizeof(*q));
     q->img = p.img;
+    q->dout = p.den;
     q->H = p.H; q->W = p.W; q->r = p.r; q->K = p.K; q->kstart = p.kstart;
+    q->ld = p.ld;
     q->Hb = 0; q->Tw = 0;
     q->k0 = p.kstart;
     q->gamma = p.gamma;
@@ -171,16 +173,26 @@ bf_status check_opts(const bf_opts* o) {
     if (o->tile_h < 0 || o->tile_w < 0) return BF_ERR_INVALID_ARG;
     if (o->kp_max < 0 || o->kp_max > SYS_KP_MAX) return BF_ERR_INVALID_ARG;
     if (!(o->trunc_tol >= 0.f && o->trunc_tol < 1.f)) return BF_ERR_INVALID_ARG;
+    if (o->pitch < 0) return BF_ERR_INVALID_ARG;
     return BF_OK;
 }
 
-bf_status fill_fwd_params(const void* img, float* out, void* saved, int H, int W, int r,
-                          float sigma_r, float T, int N, const bf_opts* opts, FwdParams* pp,
-                          int* nt, int* gx, int* gy) {
+// Row pitch of the image buffers: pitch (from bf_opts or bf_desc) or W when 0;
+// -1 when it is shorter than a row.
+int row_pitch(int pitch, int W) {
+    const int ld = pitch > 0 ? pitch : W;
+    return ld < W ? -1 : ld;
+}
+
+bf_status fill_fwd_params(const void* img, float* out, void* saved, int H, int W, int pitch,
+                          int r, float sigma_r, float T, int N, const bf_opts* opts,
+                          FwdParams* pp, int* nt, int* gx, int* gy) {
     if (!img || !out || H < 1 || W < 1) return BF_ERR_INVALID_ARG;
     if ((const void*)out == img) return BF_ERR_INVALID_ARG;
     bf_status st = check_opts(opts);
     if (st != BF_OK) return st;
+    const int ld = row_pitch(pitch, W);
+    if (ld < 0) return BF_ERR_INVALID_ARG;
     const int gm = opts ? opts->gamma_mode : BF_GAMMA_FIXED;
     Resolved rs;
     st = resolve(r, sigma_r, T, N, gm, opts ? opts->trunc_tol : 0.f, &rs);
@@ -196,6 +208,7 @@ bf_status fill_fwd_params(const void* img, float* out, void* saved, int H, int W
     p.out = out;
     p.sv = static_cast<float4*>(saved);
     p.H = H; p.W = W; p.r = r; p.K = rs.K; p.kstart = rs.kstart;
+    p.ld = ld;
     p.Hb = t.Hb; p.Tw = t.Tw;
     p.gamma = (float)rs.gamma;
     for (int i = 0; i < rs.K; ++i) p.a[i] = (float)rs.a[i];
@@ -257,8 +270,8 @@ static bf_status forward_impl(const void* img, int B, int H, int W, int r, float
     if (B < 1) return BF_ERR_INVALID_ARG;
     FwdParams p;
     int nt = 0, gx = 0, gy = 0;
-    bf_status st = fill_fwd_params(img, out, saved, H, W, r, sigma_r, T, N, opts, &p, &nt,
-                                   &gx, &gy);
+    bf_status st = fill_fwd_params(img, out, saved, H, W, opts ? opts->pitch : 0, r, sigma_r, T,
+                                   N, opts, &p, &nt, &gx, &gy);
     if (st != BF_OK) return st;
     const int in_dtype = opts ? opts->in_dtype : BF_F32;
     const size_t esz = in_dtype == BF_BF16 ? 2 : 4;
@@ -267,7 +280,7 @@ static bf_status forward_impl(const void* img, int B, int H, int W, int r, float
     cudaError_t e = cudaSuccess;
     // harmonic chunks accumulate in the saved buffers, so chunking needs them
     const int kpm = opts ? opts->kp_max : 0;
-    if (sys_tiles(H, W, r, opts, &t) && (sys_chunks(p.K, kahan, kpm) == 1 || saved)) {
+    if (sys_tiles(H, W, p.ld, r, opts, &t) && (sys_chunks(p.K, kahan, kpm) == 1 || saved)) {
         SysParams q;
         fill_sys(p, &q);
         q.out = out;
@@ -277,11 +290,11 @@ static bf_status forward_impl(const void* img, int B, int H, int W, int r, float
         e = launch_sys(q, saved ? 1 : 0, kahan, in_dtype, t.nt, t.gx, t.gy,
                        (cudaStream_t)stream, kpm);
     } else {
-        const size_t hw = (size_t)H * W;
+        const size_t hw = (size_t)H * W, hp = (size_t)H * p.ld;
         for (int b = 0; b < B && e == cudaSuccess; ++b) {
             FwdParams pb = p;
-            pb.img = static_cast<const char*>(img) + b * hw * esz;
-            pb.out = out + b * hw;
+            pb.img = static_cast<const char*>(img) + b * hp * esz;
+            pb.out = out + b * hp;
             if (saved) pb.sv = p.sv + b * hw;
             e = launch_forward(pb, nt, kahan ? 1 : 0, in_dtype, (cudaStream_t)stream);
         }
@@ -299,7 +312,9 @@ struct BwdWs {
 
 static bf_status bwd_ws(int B, int H, int W, int r, int K, const bf_opts* opts, BwdWs* ws,
                         Tiles* t, bool* use_sys) {
-    *use_sys = sys_tiles(H, W, r, opts, t);
+    const int ld = row_pitch(opts ? opts->pitch : 0, W);
+    if (ld < 0) return BF_ERR_INVALID_ARG;
+    *use_sys = sys_tiles(H, W, ld, r, opts, t);
     if (!*use_sys) {
         bf_status st = choose_tiles(H, W, r, opts, t);
         if (st != BF_OK) return st;
@@ -362,6 +377,8 @@ static bf_status backward_impl(const void* img, const float* out, const float* g
     BwdParams p;
     memset(&p, 0, sizeof(p));
     const size_t n = (size_t)H * W;
+    p.ld = row_pitch(opts ? opts->pitch : 0, W);
+    const size_t np = (size_t)H * p.ld;
     p.img = img; p.gout = grad_out;
     p.sv = static_cast<const float4*>(saved);
     p.gimg = grad_img;
@@ -374,6 +391,7 @@ static bf_status backward_impl(const void* img, const float* out, const float* g
         FwdParams fp;
         memset(&fp, 0, sizeof(fp));
         fp.img = img; fp.H = H; fp.W = W; fp.r = r; fp.K = p.K; fp.kstart = p.kstart;
+        fp.ld = p.ld;
         fp.gamma = p.gamma;
         for (int i = 0; i < p.K; ++i) fp.a[i] = p.a[i];
         SysParams q;
@@ -395,10 +413,10 @@ static bf_status backward_impl(const void* img, const float* out, const float* g
         e = cudaSuccess;
         for (int b = 0; b < B && e == cudaSuccess; ++b) {
             BwdParams pb = p;
-            pb.img = static_cast<const char*>(img) + b * n * esz;
-            pb.gout = grad_out + b * n;
+            pb.img = static_cast<const char*>(img) + b * np * esz;
+            pb.gout = grad_out + b * np;
             pb.sv = p.sv + b * n;
-            pb.gimg = grad_img ? grad_img + b * n : nullptr;
+            pb.gimg = grad_img ? grad_img + b * np : nullptr;
             pb.partial = p.partial ? p.partial + (size_t)b * t.gx * t.gy : nullptr;
             e = launch_backward(pb, t.nt, opts ? opts->in_dtype : BF_F32, s);
         }

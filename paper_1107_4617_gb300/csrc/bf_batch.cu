@@ -67,11 +67,15 @@ static bf_status plan_image(const bf_desc& d, const bf_opts* opts, Plan* pl) {
     o.tile_h = 0;
     o.save_for_backward = 0;
     int nt = 0, gx = 0, gy = 0;
-    bf_status st = fill_fwd_params(d.img, d.out, nullptr, d.H, d.W, d.r, d.sigma_r, d.T, d.N, &o,
-                                   &pl->p, &nt, &gx, &gy);
+    bf_status st = fill_fwd_params(d.img, d.out, nullptr, d.H, d.W, d.pitch, d.r, d.sigma_r, d.T,
+                                   d.N, &o, &pl->p, &nt, &gx, &gy);
     if (st != BF_OK) return st;
+    pl->p.den = d.den;
+    if (d.den && (d.den == d.out || (const void*)d.den == d.img)) return BF_ERR_INVALID_ARG;
     pl->wi = sys_width(d.r, opts);
     if (!pl->wi) return BF_ERR_UNSUPPORTED;
+    // the engine addresses one image with 32-bit element offsets
+    if ((long long)(d.H + 2 * pl->wi + 4 * d.r) * pl->p.ld >= 0x7fffffffLL) return BF_ERR_UNSUPPORTED;
     const int Tw = pl->wi - 2 * d.r;
     pl->Hb = sys_batch_rows(d.r, d.H, opts);
     pl->gx = (d.W + Tw - 1) / Tw;
@@ -111,9 +115,11 @@ static bf_status prepare_v0(const bf_desc* descs, int n, const bf_opts* opts, vo
         o.save_for_backward = 0;
         o.tile_h = v0_batch_rows(d.r < 0 ? 0 : d.r, opts);
         int nt = 0, gx = 0, gy = 0;
-        bf_status st = fill_fwd_params(d.img, d.out, nullptr, d.H, d.W, d.r, d.sigma_r, d.T, d.N,
-                                       &o, &imgs[i].p, &nt, &gx, &gy);
+        bf_status st = fill_fwd_params(d.img, d.out, nullptr, d.H, d.W, d.pitch, d.r, d.sigma_r,
+                                       d.T, d.N, &o, &imgs[i].p, &nt, &gx, &gy);
         if (st != BF_OK) return st;
+        imgs[i].p.den = d.den;
+        if (d.den && (d.den == d.out || (const void*)d.den == d.img)) return BF_ERR_INVALID_ARG;
         imgs[i].gx = gx;
         imgs[i].n_tiles = gx * gy;
         imgs[i].pad = 0;
@@ -216,8 +222,10 @@ bf_status bf_batch_prepare(const bf_desc* descs, int n, const bf_opts* opts, voi
             memset(&q, 0, sizeof(q));
             q.img = pl.p.img;
             q.out = pl.p.out;
+            q.dout = pl.p.den;
             q.acc_den = acc_den;
             q.H = pl.p.H; q.W = pl.p.W; q.r = pl.p.r;
+            q.ld = pl.p.ld;
             q.K = kc;
             q.kstart = pl.p.kstart;
             q.Hb = pl.Hb;

@@ -75,14 +75,14 @@ __global__ void __launch_bounds__(256, 1) bf_bwd_strip_kernel(BwdParams p) {
             const size_t q = (size_t)e * p.W + c;
             const float4 sv = __ldg(p.sv + q);
             fe = sv.x;
-            ae = __ldg(p.gout + q) * sv.y;
+            ae = __ldg(p.gout + (size_t)e * p.ld + c) * sv.y;
             be = -ae * sv.z;
         }
         if (ml) {
             const size_t q = (size_t)l * p.W + c;
             const float4 sv = __ldg(p.sv + q);
             fl = sv.x;
-            al = __ldg(p.gout + q) * sv.y;
+            al = __ldg(p.gout + (size_t)l * p.ld + c) * sv.y;
             bl = -al * sv.z;
         }
         BSeed se = bseed(fe, p.gamma, p.kstart, me);
@@ -105,10 +105,11 @@ __global__ void __launch_bounds__(256, 1) bf_bwd_strip_kernel(BwdParams p) {
             if (i < p.K) vrow[i * NT + j] = V[i];
         __syncthreads();
         if (is_out) {
-            const size_t o = (size_t)rho * p.W + c;
+            const size_t o = (size_t)rho * p.W + c;    // compact (saved quads)
+            const size_t op = (size_t)rho * p.ld + c;  // row-pitched (dL/dout, dL/dimg)
             const float4 svc = __ldg(p.sv + o);
             const float fc = svc.x;
-            const float ac = __ldg(p.gout + o) * svc.y;
+            const float ac = __ldg(p.gout + op) * svc.y;
             BSeed sc = bseed(fc, p.gamma, p.kstart, true);
             float gv = 0.f, gt = 0.f;
 #pragma unroll 1
@@ -126,7 +127,7 @@ __global__ void __launch_bounds__(256, 1) bf_bwd_strip_kernel(BwdParams p) {
                 brot(sc.zc, sc.zs, sc.wc, sc.ws);
             }
             gt += ac * svc.w;
-            if (p.gimg) p.gimg[o] = gv + p.gamma * gt;
+            if (p.gimg) p.gimg[op] = gv + p.gamma * gt;
             gsum += fc * gt;
         }
         __syncthreads();

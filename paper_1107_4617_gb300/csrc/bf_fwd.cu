@@ -81,8 +81,8 @@ __device__ __forceinline__ void fwd_tile(const FwdParams& p, int bx, int by, flo
         const int l = rho - r - 1;
         const bool me = col_in && e >= 0 && e < p.H;
         const bool ml = col_in && rho > y0 && l >= 0 && l < p.H;
-        const float fe = me ? load_px(img, (size_t)e * p.W + c) : 0.f;
-        const float fl = ml ? load_px(img, (size_t)l * p.W + c) : 0.f;
+        const float fe = me ? load_px(img, (size_t)e * p.ld + c) : 0.f;
+        const float fl = ml ? load_px(img, (size_t)l * p.ld + c) : 0.f;
         Seed se = make_seed(fe, p.gamma, p.kstart, me);
         Seed sl = make_seed(fl, p.gamma, p.kstart, ml);
 #pragma unroll
@@ -113,7 +113,7 @@ __device__ __forceinline__ void fwd_tile(const FwdParams& p, int bx, int by, flo
             if (i < p.K) vrow[i * NT + j] = V[i];
         __syncthreads();
         if (is_out) {
-            const float fc = load_px(img, (size_t)rho * p.W + c);
+            const float fc = load_px(img, (size_t)rho * p.ld + c);
             Seed sc = make_seed(fc, p.gamma, p.kstart, true);
             float num = 0.f, den = 0.f, dnum = 0.f, dden = 0.f;
 #pragma unroll 1
@@ -132,9 +132,11 @@ __device__ __forceinline__ void fwd_tile(const FwdParams& p, int bx, int by, flo
                 dden += ak * (sc.zc * h.w - sc.zs * h.z);
                 rotate(sc.zc, sc.zs, sc.wc, sc.ws);
             }
-            const size_t o = (size_t)rho * p.W + c;
+            const size_t o = (size_t)rho * p.W + c;    // compact (saved quads)
+            const size_t op = (size_t)rho * p.ld + c;  // row-pitched (out, den)
             const float ov = num / den;
-            p.out[o] = ov;
+            p.out[op] = ov;
+            if (p.den) p.den[op] = den;
             // saved for the adjoint: (f, 1/den, out, dnum - out dden)
             if (p.sv) p.sv[o] = make_float4(fc, 1.0f / den, ov, dnum - ov * dden);
         }

@@ -18,10 +18,12 @@ constexpr int KCAP = BF_N_MAX / 2 + 1;
 // parameter (a_k sits in the constant parameter bank, no __constant__
 // symbol, so concurrent launches with different N never race).
 struct FwdParams {
-    const void* img;      // H x W, FP32 or BF16
-    float* out;           // H x W
-    float4* sv;           // saved quads (f, 1/den, out, dnum - out dden); nullable
+    const void* img;      // H x W (row pitch ld), FP32 or BF16
+    float* out;           // H x W (row pitch ld)
+    float4* sv;           // saved quads (f, 1/den, out, dnum - out dden); nullable, compact
+    float* den;           // den of Eq. filter2 (row pitch ld); nullable
     int H, W, r;
+    int ld;               // row pitch of img, out and den in elements (>= W)
     int K;                // number of harmonics
     int kstart;           // N mod 2: frequency of harmonic 0
     int Hb;               // output rows per band (grid.y tiles)
@@ -32,11 +34,12 @@ struct FwdParams {
 
 struct BwdParams {
     const void* img;      // forward input
-    const float* gout;    // dL/dout
-    const float4* sv;     // the forward's saved quads
-    float* gimg;          // dL/dimg (nullable)
+    const float* gout;    // dL/dout (row pitch ld)
+    const float4* sv;     // the forward's saved quads (compact)
+    float* gimg;          // dL/dimg (nullable, row pitch ld)
     float* partial;       // per-CTA sums of f * dL/dtheta (nullable)
     int H, W, r, K, kstart, Hb, Tw;
+    int ld;               // row pitch of gout and gimg in elements (>= W)
     float gamma;
     float a[KCAP];
 };
@@ -56,7 +59,9 @@ struct SysParams {
     float* acc_den;             // forward chunk accumulator for den when not saving
     float* acc_gv;              // adjoint chunk accumulators (value and phase parts)
     float* acc_gt;
+    float* dout;                // forward: den of Eq. filter2 (nullable; row pitch ld)
     int H, W, r, K, kstart, Hb, Tw;
+    int ld;          // row pitch (elements) of img, out, gout, gimg, dout; >= W
     int B;           // images of a [B, H, W] launch (grid.z); 0 or 1 = one image
     int k0;          // frequency of this launch's first harmonic
     int acc;         // 0 all harmonics; 1 first, 2 middle, 3 last harmonic chunk
@@ -80,7 +85,7 @@ cudaError_t launch_sys_w256(const SysParams& p, int mode, int dtype, int kp, int
                             int gy, cudaStream_t s);
 cudaError_t launch_sys_kahan(const SysParams& p, int mode, int dtype, int kp, int wi, int gx,
                              int gy, cudaStream_t s);
-// First (or only) harmonic chunk of an FP32 image on 128-thread strips: KP
+// First (or only) harmonic chunk of a compact FP32 image on 128-thread strips: KP
 // pairs (1..11), half = the last pair holds one harmonic, seed = 1 (odd N,
 // k0 = 1) or 2 (even N, k0 = 0, the constant harmonic kept apart from the
 // pairs). Explicitly instantiated in bf_sys_first_*.cu.
@@ -162,9 +167,10 @@ cudaError_t launch_backward(const BwdParams& p, int nthreads, int in_dtype, cuda
 cudaError_t launch_batch(BatchTable* tab, int grid, int kahan, int in_dtype, cudaStream_t s);
 int sm_count();
 bf_status check_opts(const bf_opts* o);
-bf_status fill_fwd_params(const void* img, float* out, void* saved, int H, int W, int r,
-                          float sigma_r, float T, int N, const bf_opts* opts, FwdParams* p,
-                          int* nt, int* gx, int* gy);
+bf_status fill_fwd_params(const void* img, float* out, void* saved, int H, int W, int pitch,
+                          int r, float sigma_r, float T, int N, const bf_opts* opts,
+                          FwdParams* p, int* nt, int* gx, int* gy);
+int row_pitch(int pitch, int W);
 cudaError_t launch_reduce_sigma(const float* partial, int n, float scale, float* dst,
                                 cudaStream_t s);
 

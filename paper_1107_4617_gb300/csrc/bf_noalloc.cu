@@ -13,38 +13,27 @@
 // The array lives in file-scope device memory: every GPU that loads the
 // library holds it (BF_NOALLOC_MAX_PARTIALS floats) until the process exits.
 // Host code cannot pass the array's name to a kernel: on the host that name
-// is only a stand-in, not a device address. Its device address is looked up
-// once per device with cudaGetSymbolAddress, with that device current.
-#include <mutex>
-
+// is only a stand-in, not a device address. Its device address on the current
+// device is looked up with cudaGetSymbolAddress on every call (a host-side
+// lookup that allocates nothing). Looking it up each time, rather than once
+// per device, keeps the address right after a cudaDeviceReset, which
+// destroys the device's context and can reload the module elsewhere.
 #include "bf_internal.cuh"
 #include "bf_trace.cuh"
 
 namespace {
 
-// Fixed scratch for the per-CTA partial sums; no entry needs to start at
-// zero, because each call writes every slot it later reads.
+// Fixed scratch for the per-CTA partial sums (and, for harmonic chunks, the two
+// image-sized accumulators); no entry needs to start at zero, because each
+// call writes every slot it later reads.
 __device__ __align__(256) float g_noalloc_partials[BF_NOALLOC_MAX_PARTIALS];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void* g_addr[kMaxDevices] = {nullptr};
-
-// Device address of the scratch array on the current device, looked up on
-// the first call for that device.
+// Device address of the scratch array on the current device.
 bf_status scratch_address(void** out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
     if (e != cudaSuccess) return bf::set_cuda_error(e);
-    if (dev < 0 || dev >= kMaxDevices) return BF_ERR_UNSUPPORTED;
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_addr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_partials);
-        if (e != cudaSuccess) return bf::set_cuda_error(e);
-        g_addr[dev] = p;
-    }
-    *out = g_addr[dev];
+    *out = p;
     return BF_OK;
 }
 

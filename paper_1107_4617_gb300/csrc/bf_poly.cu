@@ -289,7 +289,7 @@ static bf_status prepare(int H, int W, int r, float sigma_r, float T, int* N,
     bf_status st = check_opts(opts);
     if (st != BF_OK) return st;
     if (opts && (opts->in_dtype != BF_F32 || opts->kahan || opts->trunc_tol > 0.f ||
-                 opts->gamma_mode != BF_GAMMA_FIXED))
+                 opts->gamma_mode != BF_GAMMA_FIXED || (opts->pitch != 0 && opts->pitch != W)))
         return BF_ERR_UNSUPPORTED;
     if (*N <= 0) {
         *N = bf_poly_resolve_N(sigma_r, T);

@@ -75,7 +75,8 @@ cudaError_t launch_sys(const SysParams& base, int mode, bool kahan, int in_dtype
         if (mode == 2 && c + 1 < nch) p.partial = nullptr;  // reduce only on the last chunk
         cudaError_t e;
         if (kahan) e = launch_sys_kahan(p, mode, in_dtype, kp, wi, gx, gy, s);
-        else if (wi <= 128 && in_dtype == BF_F32 && (p.k0 == 1 || (p.k0 == 0 && kc > 1)))
+        else if (wi <= 128 && in_dtype == BF_F32 && p.ld == p.W &&
+                 (p.k0 == 1 || (p.k0 == 0 && kc > 1)))
             e = launch_first(p, mode, kc, p.k0 == 1 ? 1 : 2, wi, gx, gy, s);
         else if (wi <= 128) e = launch_sys_w128(p, mode, in_dtype, kp, wi, gx, gy, s);
         else e = launch_sys_w256(p, mode, in_dtype, kp, wi, gx, gy, s);

@@ -13,13 +13,13 @@ __device__ __forceinline__ void run_chunk(const SysParams& p, int kp, int bx, in
                                           float4* smem) {
     float gsum = 0.f;
     switch (kp) {
-        case 1: sysd::sys_tile<1, false, false, false, WMAX, Tin>(p, bx, by, 0, smem, gsum); break;
-        case 2: sysd::sys_tile<2, false, false, false, WMAX, Tin>(p, bx, by, 0, smem, gsum); break;
-        case 3: sysd::sys_tile<3, false, false, false, WMAX, Tin>(p, bx, by, 0, smem, gsum); break;
-        case 4: sysd::sys_tile<4, false, false, false, WMAX, Tin>(p, bx, by, 0, smem, gsum); break;
-        case 6: sysd::sys_tile<6, false, false, false, WMAX, Tin>(p, bx, by, 0, smem, gsum); break;
-        case 8: sysd::sys_tile<8, false, false, false, WMAX, Tin>(p, bx, by, 0, smem, gsum); break;
-        default: sysd::sys_tile<KPMAX, false, false, false, WMAX, Tin>(p, bx, by, 0, smem, gsum); break;
+        case 1: sysd::sys_tile<1, false, false, false, WMAX, Tin>(p, bx, by, 0, 0, smem, gsum); break;
+        case 2: sysd::sys_tile<2, false, false, false, WMAX, Tin>(p, bx, by, 0, 0, smem, gsum); break;
+        case 3: sysd::sys_tile<3, false, false, false, WMAX, Tin>(p, bx, by, 0, 0, smem, gsum); break;
+        case 4: sysd::sys_tile<4, false, false, false, WMAX, Tin>(p, bx, by, 0, 0, smem, gsum); break;
+        case 6: sysd::sys_tile<6, false, false, false, WMAX, Tin>(p, bx, by, 0, 0, smem, gsum); break;
+        case 8: sysd::sys_tile<8, false, false, false, WMAX, Tin>(p, bx, by, 0, 0, smem, gsum); break;
+        default: sysd::sys_tile<KPMAX, false, false, false, WMAX, Tin>(p, bx, by, 0, 0, smem, gsum); break;
     }
 }
 

@@ -203,8 +203,10 @@ struct Bases {
 
 // Masked loads leave neutral values (f = 0; in the adjoint g = 0, so the
 // plane weights alpha, beta are 0); the forward masks its own weights.
+// Forward: q = element offset in the row-pitched image. Adjoint: q = offset
+// in the compact saved quads, qg = offset in the row-pitched dL/dout.
 template <bool BWD, typename Tin>
-__device__ __forceinline__ void load_px(Px<BWD>& v, const Bases<Tin>& b, bool on, int q) {
+__device__ __forceinline__ void load_px(Px<BWD>& v, const Bases<Tin>& b, bool on, int q, int qg) {
     if constexpr (!BWD) {
         v.f = 0.f;
         if (on) v.f = ld_img(b.img, q);
@@ -213,7 +215,7 @@ __device__ __forceinline__ void load_px(Px<BWD>& v, const Bases<Tin>& b, bool on
         v.g = 0.f;
         if (on) {
             v.sv = __ldg(b.bsv + q);
-            v.g = __ldg(b.gout + q);
+            v.g = __ldg(b.gout + qg);
         }
     }
 }
@@ -224,7 +226,8 @@ __device__ __forceinline__ float pix_f(const Px<BWD>& v) {
 }
 
 // Masks and element offsets of one step's five pixels (entering and leaving
-// row of the own and the second column, centre).
+// row of the own and the second column, centre): in the row-pitched image for
+// the forward, in the compact saved quads for the adjoint.
 struct Geo {
     bool m0, m1, m2, m3, out;
     int q0, q1, q2, q3, qo;
@@ -241,11 +244,13 @@ __host__ __device__ constexpr int sys_smem_slots(int KP, int WMAX, bool dc = fal
 // One strip x band tile (bx, by) of one image, for one chunk of harmonics.
 // Called uniformly by every thread of the CTA. gsum accumulates f * dL/dtheta
 // (adjoint, last chunk only). KAHAN compensates the vertical running sums.
-// zo: element offset of this image in the image-sized buffers (and quad
-// offset in the saved buffer).
+// zo: element offset of this image in the compact buffers (saved quads, chunk
+// accumulators); zp: in the row-pitched image buffers (img, out, dL/dout,
+// dL/dimg, den), whose rows are p.ld elements apart. PITCH = false builds the
+// compact case (p.ld = W) with the pitch terms compiled out.
 template <int KP, bool BWD, bool SAVE, bool KAHAN, int WMAX, typename Tin, bool HALF = false,
-          int SEED = 0, int FORM = 0>
-__device__ __forceinline__ void sys_tile(const SysParams& p, int bx, int by, size_t zo,
+          int SEED = 0, int FORM = 0, bool PITCH = true>
+__device__ __forceinline__ void sys_tile(const SysParams& p, int bx, int by, size_t zo, size_t zp,
                                          float4* smem, float& gsum) {
     // SEED 2 (even N): the constant harmonic k = 0 runs apart from the pairs
     // (planes f and 1, or alpha in the adjoint: its k = 0 phase terms vanish),
@@ -259,6 +264,10 @@ __device__ __forceinline__ void sys_tile(const SysParams& p, int bx, int by, siz
     const int w = j >> 5;
     const int r = p.r;
     const int W = p.W;
+    const int ld = PITCH ? p.ld : W;      // row pitch of the image buffers
+    const int dld = ld - W;               // extra elements per row past a compact one
+    // row stride of the offsets Geo carries: the image (forward) or the quads (adjoint)
+    const int st = BWD ? W : ld;
     const int x0 = bx * p.Tw;
     const int cw = x0 - r + j;            // own column
     const int c2 = cw - 2 * r - 1;        // column leaving the horizontal window
@@ -275,9 +284,9 @@ __device__ __forceinline__ void sys_tile(const SysParams& p, int bx, int by, siz
     const int ne = min(p.H, y0 + rows + r) - elo;
 
     Bases<Tin> b;
-    b.img = static_cast<const Tin*>(p.img) + zo;
+    b.img = static_cast<const Tin*>(p.img) + zp;
     if constexpr (BWD) {
-        b.gout = p.gout + zo;
+        b.gout = p.gout + zp;
         b.bsv = p.bsv + zo;
     }
 
@@ -298,7 +307,7 @@ __device__ __forceinline__ void sys_tile(const SysParams& p, int bx, int by, siz
     auto geometry = [&](int t) {
         const int e = e0 + t;
         const int tau = t - j;
-        const int oe = e * W;
+        const int oe = e * st;
         const bool act = (unsigned)tau < (unsigned)span;
         const bool in_e = act && (unsigned)(e - elo) < (unsigned)ne;
         const bool in_l = act && (unsigned)(e - 2 * r - 1 - elo) < (unsigned)ne &&
@@ -311,9 +320,9 @@ __device__ __forceinline__ void sys_tile(const SysParams& p, int bx, int by, siz
         g.out = act && out_lane && (unsigned)(e - r - y0) < (unsigned)rows;
         g.q0 = oe + cw;
         g.q1 = oe + c2;
-        g.q2 = oe - (2 * r + 1) * W + cw;
-        g.q3 = oe - (2 * r + 1) * W + c2;
-        g.qo = oe - r * W + co;
+        g.q2 = oe - (2 * r + 1) * st + cw;
+        g.q3 = oe - (2 * r + 1) * st + c2;
+        g.qo = oe - r * st + co;
         return g;
     };
 
@@ -321,11 +330,22 @@ __device__ __forceinline__ void sys_tile(const SysParams& p, int bx, int by, siz
     Px<BWD> v0, v1, v2, v3, vc;
     // a warp is first active at step 32 w; start its prefetch chain there
     Geo g = geometry(w * 32);
-    load_px<BWD, Tin>(v0, b, g.m0, g.q0);
-    load_px<BWD, Tin>(v1, b, g.m1, g.q1);
-    load_px<BWD, Tin>(v2, b, g.m2, g.q2);
-    load_px<BWD, Tin>(v3, b, g.m3, g.q3);
-    load_px<BWD, Tin>(vc, b, g.out, g.qo);
+    // the adjoint's dL/dout offsets: the quads' offsets plus the pitched rows'
+    // extra elements (entering row e, leaving row e - 2r - 1, centre row e - r)
+    auto load_step = [&](const Geo& gg, int t) {
+        int de = 0, dl = 0, dc = 0;
+        if constexpr (BWD) {
+            de = (e0 + t) * dld;
+            dl = de - (2 * r + 1) * dld;
+            dc = de - r * dld;
+        }
+        load_px<BWD, Tin>(v0, b, gg.m0, gg.q0, gg.q0 + de);
+        load_px<BWD, Tin>(v1, b, gg.m1, gg.q1, gg.q1 + de);
+        load_px<BWD, Tin>(v2, b, gg.m2, gg.q2, gg.q2 + dl);
+        load_px<BWD, Tin>(v3, b, gg.m3, gg.q3, gg.q3 + dl);
+        load_px<BWD, Tin>(vc, b, gg.out, gg.qo, gg.qo + dc);
+    };
+    load_step(g, w * 32);
     __syncthreads();
 
     for (int t = 0; t < steps; ++t) {
@@ -342,20 +362,16 @@ __device__ __forceinline__ void sys_tile(const SysParams& p, int bx, int by, siz
                 const int ef = e0 + t + PREFETCH_ROWS;
                 if (own_in && (unsigned)(ef - elo) < (unsigned)ne) {
                     if constexpr (!BWD) {
-                        prefetch_l2(b.img + ef * W + cw);
+                        prefetch_l2(b.img + ef * ld + cw);
                     } else {
                         prefetch_l2(b.bsv + ef * W + cw);
-                        prefetch_l2(b.gout + ef * W + cw);
+                        prefetch_l2(b.gout + ef * ld + cw);
                     }
                 }
             }
             // prefetch the next step's pixels; their latency hides under this step
             g = geometry(t + 1);
-            load_px<BWD, Tin>(v0, b, g.m0, g.q0);
-            load_px<BWD, Tin>(v1, b, g.m1, g.q1);
-            load_px<BWD, Tin>(v2, b, g.m2, g.q2);
-            load_px<BWD, Tin>(v3, b, g.m3, g.q3);
-            load_px<BWD, Tin>(vc, b, g.out, g.qo);
+            load_step(g, t + 1);
 
             // plane weights (u: first two planes, v: last two) with the stream's
             // sign: + own enter, - second enter, - own leave, + second leave;
@@ -618,7 +634,16 @@ __device__ __forceinline__ void sys_tile(const SysParams& p, int bx, int by, siz
                 }
             }
             if (gc.out) {
-                const size_t o = (size_t)gc.qo + zo;   // image-sized buffers
+                // compact buffers (quads, chunk accumulators) and row-pitched ones
+                size_t o, op;
+                if constexpr (!PITCH) {
+                    o = (size_t)gc.qo + zo;
+                    op = o;
+                } else {
+                    const int ro = e0 + t - r;   // the centre's row
+                    o = BWD ? (size_t)gc.qo + zo : (size_t)ro * W + co + zo;
+                    op = BWD ? (size_t)gc.qo + (size_t)ro * dld + zp : (size_t)gc.qo + zp;
+                }
                 float num = NUM.x + NUM.y, den = DEN.x + DEN.y;
                 // chunked harmonics: partial sums live in the output buffers
                 // between chunks (acc: 0 single, 1 first, 2 middle, 3 last)
@@ -632,26 +657,32 @@ __device__ __forceinline__ void sys_tile(const SysParams& p, int bx, int by, siz
                         // dnum - out dden) for the adjoint
                         if (acc >= 2) {
                             const float4 q = p.sv[o];
-                            num += p.out[o]; den += q.y; dn += q.z; dd += q.w;
+                            num += p.out[op]; den += q.y; dn += q.z; dd += q.w;
                         }
                         if (last) {
                             const float ov = num / den;
-                            p.out[o] = ov;
+                            p.out[op] = ov;
                             p.sv[o] = make_float4(cc.f, 1.0f / den, ov, fmaf(-ov, dd, dn));
+                            if constexpr (PITCH) {
+                                if (p.dout) p.dout[op] = den;
+                            }
                         } else {
-                            p.out[o] = num;
+                            p.out[op] = num;
                             p.sv[o] = make_float4(cc.f, den, dn, dd);
                         }
                     } else {
-                        if (acc >= 2) { num += p.out[o]; den += p.acc_den[o]; }
-                        p.out[o] = last ? num / den : num;
+                        if (acc >= 2) { num += p.out[op]; den += p.acc_den[o]; }
+                        p.out[op] = last ? num / den : num;
                         if (acc != 0) p.acc_den[o] = den;
+                        if constexpr (PITCH) {
+                            if (last && p.dout) p.dout[op] = den;
+                        }
                     }
                 } else {
                     if (acc >= 2) { num += p.acc_gv[o]; den += p.acc_gt[o]; }
                     if (last) {
                         const float gt = den + xc;
-                        if (p.gimg) p.gimg[o] = num + p.gamma * gt;
+                        if (p.gimg) p.gimg[op] = num + p.gamma * gt;
                         gsum = fmaf(cc.sv.x, gt, gsum);
                     } else {
                         p.acc_gv[o] = num;
@@ -684,23 +715,24 @@ __device__ __forceinline__ void cta_sum_to(float gsum, float* partial, int slot)
 // One CTA per tile. WMAX = largest strip width (threads) of the instantiation:
 // 128-thread strips run two CTAs per SM, 256-thread strips one.
 template <int KP, bool BWD, bool SAVE, bool KAHAN, int WMAX, typename Tin, bool HALF = false,
-          int SEED = 0, int FORM = 0>
+          int SEED = 0, int FORM = 0, bool PITCH = true>
 __global__ void __launch_bounds__(WMAX, 256 / WMAX) bf_sys_kernel(SysParams p) {
     extern __shared__ float4 smem[];
     float gsum = 0.f;
     const size_t z = blockIdx.z;  // image of a [B, H, W] launch
     const size_t hw = (size_t)p.H * p.W;
-    sysd::sys_tile<KP, BWD, SAVE, KAHAN, WMAX, Tin, HALF, SEED, FORM>(p, blockIdx.x, blockIdx.y,
-                                                                      z * hw, smem, gsum);
+    const size_t hp = PITCH ? (size_t)p.H * p.ld : hw;
+    sysd::sys_tile<KP, BWD, SAVE, KAHAN, WMAX, Tin, HALF, SEED, FORM, PITCH>(
+        p, blockIdx.x, blockIdx.y, z * hw, z * hp, smem, gsum);
     if (BWD && p.partial)
         sysd::cta_sum_to(gsum, p.partial, (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x);
 }
 
 template <int KP, bool BWD, bool SAVE, bool KAHAN, int WMAX, typename Tin, bool HALF = false,
-          int SEED = 0, int FORM = 0>
+          int SEED = 0, int FORM = 0, bool PITCH = true>
 cudaError_t sys_launch_one(const SysParams& p, int wi, int gx, int gy, cudaStream_t s) {
     const int gz = p.B > 0 ? p.B : 1;
-    auto kern = bf_sys_kernel<KP, BWD, SAVE, KAHAN, WMAX, Tin, HALF, SEED, FORM>;
+    auto kern = bf_sys_kernel<KP, BWD, SAVE, KAHAN, WMAX, Tin, HALF, SEED, FORM, PITCH>;
     const size_t smem = sizeof(float4) * (size_t)sysd::sys_smem_slots(KP, WMAX, SEED == 2);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);

@@ -1,5 +1,5 @@
-// Engine instantiations for the first (or only) harmonic chunk of an FP32
-// image on 128-thread strips: the seed is specialised at compile time (odd or
+// Engine instantiations for the first (or only) harmonic chunk of a compact
+// FP32 image on 128-thread strips: the seed is specialised at compile time (odd or
 // even N) and every pair count 1..11 has its own kernel, with a half pair for
 // an odd number of harmonics, so no harmonic is computed with a zero
 // coefficient. Each translation unit bf_sys_first*.cu instantiates a few
@@ -42,11 +42,15 @@ cudaError_t sys_first_modes(const SysParams& p, int mode, int wi, int gx, int gy
     constexpr int F0 = kFirstForm[0][SEED - 1][KP - 1][HALF];
     constexpr int F1 = kFirstForm[1][SEED - 1][KP - 1][HALF];
     constexpr int F2 = kFirstForm[2][SEED - 1][KP - 1][HALF];
+    // compact images only (p.ld == W): the pitch terms are compiled out
     if (mode == 2)
-        return sys_launch_one<KP, true, false, false, 128, float, HALF, SEED, F2>(p, wi, gx, gy, s);
+        return sys_launch_one<KP, true, false, false, 128, float, HALF, SEED, F2, false>(p, wi, gx,
+                                                                                    gy, s);
     if (mode == 1)
-        return sys_launch_one<KP, false, true, false, 128, float, HALF, SEED, F1>(p, wi, gx, gy, s);
-    return sys_launch_one<KP, false, false, false, 128, float, HALF, SEED, F0>(p, wi, gx, gy, s);
+        return sys_launch_one<KP, false, true, false, 128, float, HALF, SEED, F1, false>(p, wi, gx,
+                                                                                    gy, s);
+    return sys_launch_one<KP, false, false, false, 128, float, HALF, SEED, F0, false>(p, wi, gx, gy,
+                                                                                     s);
 }
 
 template <int KP>

@@ -141,6 +141,27 @@ def test_argument_checks_return_before_any_launch():
         lib.bf_default_opts(ctypes.byref(o))
         o.trunc_tol = bad
         assert lib.bf_forward(p, 4, 4, 1, 0.2, 1.0, 0, q, ctypes.byref(o), None, None) == 1
+    # row pitch: negative or shorter than a row is rejected; the variant filters
+    # accept only a compact image (pitch 0 or W)
+    for bad in (-1, 3):
+        lib.bf_default_opts(ctypes.byref(o))
+        o.pitch = bad
+        assert lib.bf_forward(p, 4, 4, 1, 0.2, 1.0, 0, q, ctypes.byref(o), None, None) == 1
+        assert lib.bf_backward(p, q, q, s16, 4, 4, 1, 0.2, 1.0, 0, ctypes.c_void_p(0x4000),
+                               None, None, 0, ctypes.byref(o), None) == 1
+    lib.bf_default_opts(ctypes.byref(o))
+    o.pitch = 8
+    assert lib.bf_spatial_forward(p, 4, 4, 1, 2, 0.0, 1.0, 4, q, ctypes.byref(o), None, None) == 2
+    assert lib.bf_poly_forward(p, 4, 4, 1, 0.0, 1.0, 3, q, ctypes.byref(o), None, None) == 2
+    # batch descriptor: pitch below W, den aliasing the output
+    d = bf.BfDesc()
+    d.img, d.out, d.den = 0x1000, 0x2000, None
+    d.H, d.W, d.pitch, d.r, d.N, d.sigma_r, d.T = 4, 4, 3, 1, 3, 0.2, 1.0
+    arr = (bf.BfDesc * 1)(d)
+    assert lib.bf_batch_workspace_bytes(arr, 1, None) == 0
+    d.pitch, d.den = 0, 0x2000
+    arr = (bf.BfDesc * 1)(d)
+    assert lib.bf_batch_workspace_bytes(arr, 1, None) == 0
 
 
 def test_status_strings():

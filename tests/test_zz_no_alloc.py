@@ -4,10 +4,13 @@ The allocation-free adjoint is for callers that cannot allocate device
 memory (a plugin whose host application owns the GPU's memory pool, a loop
 that cannot afford an allocation's device synchronisation). It keeps its
 dL/dsigma_r partial sums in a fixed array inside the library instead of a
-caller workspace; its results must equal the workspace version's. Two calls
-in a row on different images check that the array's leftover contents from
-the first call do not leak into the second. This file is collected last, so
-a failure here leaves every other test already run.
+caller workspace. Both run the same kernels with the same launch shape and
+sum the partials in the same fixed order, so dL/dimg and dL/dsigma_r must
+equal the workspace version's bit for bit. Calls in a row on different
+images check that the array's leftover contents from one call do not leak
+into the next, also when the harmonics run in chunks (N > 43) and the
+array holds the chunks' image-sized accumulators too. This file is
+collected last, so a failure here leaves every other test already run.
 """
 import ctypes
 
@@ -19,14 +22,12 @@ from paper_1107_4617_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 
-GTOL = 1e-3  # gradient tolerance used by the adjoint tests
 
-
-def _case(bf, H, W, r, sigma, seed):
+def _case(bf, H, W, r, sigma, seed, N=0):
     dev = torch.device("cuda:0")
     f = torch.from_numpy(synth.rectangles(H, W, seed=seed)).to(dev)
     g = torch.from_numpy(synth.weights((H, W), seed=seed + 1)).to(dev)
-    N = bf.bf_resolve_N(sigma, 1.0)
+    N = N or bf.bf_resolve_N(sigma, 1.0)
     opts = bf._opts(save=True, gamma_mode=bf.GAMMA_FROM_SIGMA)
     sv = torch.empty((H, W, 4), device=dev)
     out = bf.bf_forward(f, r, sigma, 1.0, N, opts=opts, saved=sv)
@@ -61,22 +62,28 @@ def _noalloc_raw(bf, f, g, out, sv, r, sigma, N, opts):
     return gi, gs
 
 
-def _close(a, b):
-    a = a.detach().cpu().numpy().astype(np.float64)
-    b = b.detach().cpu().numpy().astype(np.float64)
-    scale = max(np.abs(b).max(), 1e-30)
-    assert np.abs(a - b).max() <= GTOL * scale, (np.abs(a - b).max(), scale)
+def _equal(a, b):
+    a = a.detach().cpu().numpy()
+    b = b.detach().cpu().numpy()
+    assert np.array_equal(a, b), float(np.abs(a.astype(np.float64) - b).max())
 
 
-def test_noalloc_matches_workspace_version_twice(cuda_lib):
+@pytest.mark.parametrize("cases", [
+    # whole harmonics in one launch, two images in a row
+    [(300, 410, 7, 0.15, 3, 0), (257, 129, 4, 0.3, 11, 0)],
+    # harmonic chunks (N = 50): the accumulators live in the array too; the
+    # larger image first leaves its contents behind for the smaller one
+    [(88, 90, 6, 0.1, 5, 50), (48, 64, 5, 0.1, 7, 50)],
+])
+def test_noalloc_matches_workspace_version_bit_for_bit(cuda_lib, cases):
     bf = cuda_lib
-    for (H, W, r, sigma, seed) in [(300, 410, 7, 0.15, 3), (257, 129, 4, 0.3, 11)]:
-        f, g, out, sv, N, opts = _case(bf, H, W, r, sigma, seed)
+    for (H, W, r, sigma, seed, N) in cases:
+        f, g, out, sv, N, opts = _case(bf, H, W, r, sigma, seed, N)
         gi_ref, gs_ref = _reference(bf, f, g, out, sv, r, sigma, N, opts)
         gi, gs = _noalloc_raw(bf, f, g, out, sv, r, sigma, N, opts)
         torch.cuda.synchronize()
-        _close(gi, gi_ref)
-        assert abs(float(gs) - float(gs_ref)) <= GTOL * max(1.0, abs(float(gs_ref)))
+        _equal(gi, gi_ref)
+        _equal(gs, gs_ref)
 
 
 def test_noalloc_rejects_oversize(cuda_lib):
