@@ -39,6 +39,16 @@ UNIT = "Mpixel/s"
 SMS, LANES, FMAX_GHZ = 152, 128, 2.070
 FP32_PEAK_TFLOPS = SMS * LANES * 2 * FMAX_GHZ / 1e3
 L2_FLUSH_BYTES = 256 << 20
+
+
+def hbm_peak_gbs():
+    """(HBM copy bandwidth in GB/s, its source): the pool's measured figure when
+    MEASURED_PEAKS.json is present, else one earlier GB300 measurement."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback 6.8 TB/s"
 # kernels the bench's two launches run (N = 41 -> 11 harmonic pairs, 128-thread strips)
 FWD_KERNEL = "bf_sys_kernel<11, 0, 1, 0, 128, float> (forward, saved buffers)"
 ADJ_KERNEL = "bf_sys_kernel<11, 1, 0, 0, 128, float> (adjoint)"
@@ -303,46 +313,73 @@ def extras(dev, flush, stream):
                         "max_abs": max(e["max_abs"] for e in errs), "images_checked": len(errs)}}
     del imgs, outs, ws, g, wst, gt
 
-    # differentiation: 16 x 512^2, r=7, sigma_r=0.15 (N=19), L = sum(w * out)
+    # differentiation: 16 x 512^2, r=7, sigma_r=0.15 (N=19), L = sum(w * out),
+    # gamma = 1/(sigma_r sqrt N) (N frozen), so dL/dsigma_r is live
     B, Hd, r = 16, 512, 7
     fb = np.stack([synth.rectangles(Hd, Hd, seed=100 + b) for b in range(B)])
     wb = synth.weights((B, Hd, Hd), seed=1)
     ft = torch.from_numpy(fb).to(dev)
     wt = torch.from_numpy(wb).to(dev)
-    Nd = bf.bf_resolve_N(0.15, 1.0)
+    sig_d = 0.15
+    Nd = bf.bf_resolve_N(sig_d, 1.0)
     outd = torch.empty_like(ft)
     svd = torch.empty((B, Hd, Hd, 4), device=dev)
     gi = torch.empty_like(ft)
-    sopt = bf._opts(save=True)
+    gsd = torch.zeros((1,), device=dev)
+    sopt = bf._opts(save=True, gamma_mode=bf.GAMMA_FROM_SIGMA)
+    wsd = torch.empty((bf.bf_backward3d_workspace_bytes(B, Hd, Hd, r, sig_d, 1.0, Nd, sopt) // 4
+                       + 1,), device=dev)
 
     def fwd_bwd():  # one [B, H, W] launch each for the forward and the adjoint
-        bf.bf_forward3d(ft, r, 0.15, 1.0, Nd, out=outd, opts=sopt, saved=svd, stream=stream)
-        bf.bf_backward3d(ft, outd, wt, svd, r, 0.15, 1.0, Nd, grad_img=gi, opts=sopt,
-                         stream=stream)
+        bf.bf_forward3d(ft, r, sig_d, 1.0, Nd, out=outd, opts=sopt, saved=svd, stream=stream)
+        bf.bf_backward3d(ft, outd, wt, svd, r, sig_d, 1.0, Nd, grad_img=gi, grad_sigma=gsd,
+                         workspace=wsd, opts=sopt, stream=stream)
     fwd_bwd()
     ms_d = _time_ms(fwd_bwd, flush, stream)
-    # gradient at sampled pixels vs central differences of the FP64 oracle on a crop
+    fwd_bwd()
+    torch.cuda.synchronize()
     gg = gi.cpu().numpy()
+    gamma_d = oracle.gamma_from_sigma(sig_d, Nd)
+    f64b = fb.astype(np.float64)
+    # dL/dsigma_r against FP64 central differences of the oracle in sigma_r
+    # (h = 1e-4, N frozen) over the whole batch
+    hs = 1e-4
+
+    def loss(sig):
+        gm = oracle.gamma_from_sigma(sig, Nd)
+        return sum(float(np.sum(wb[b].astype(np.float64) * oracle.bilateral(f64b[b], r, gm, Nd)))
+                   for b in range(B))
+    fd_sig = (loss(sig_d + hs) - loss(sig_d - hs)) / (2 * hs)
+    gs_val = float(gsd.cpu())
+    # dL/df at 256 sampled pixels per image against FP64 central differences of
+    # the oracle on a crop around each pixel
     gerr = 0.0
-    for _ in range(6):
-        b, y, x = int(rng.integers(0, B)), int(rng.integers(0, Hd)), int(rng.integers(0, Hd))
-        y0, y1 = max(0, y - 2 * r), min(Hd, y + 2 * r + 1)
-        x0, x1 = max(0, x - 2 * r), min(Hd, x + 2 * r + 1)
-        sub = fb[b, y0:y1, x0:x1].astype(np.float64)
-        wsub = wb[b, y0:y1, x0:x1].astype(np.float64)
-        mask = np.zeros_like(sub)
-        mask[max(0, y - r) - y0:min(Hd, y + r + 1) - y0, max(0, x - r) - x0:min(Hd, x + r + 1) - x0] = 1
-        h = 1e-4
-        sp_, sm_ = sub.copy(), sub.copy()
-        sp_[y - y0, x - x0] += h
-        sm_[y - y0, x - x0] -= h
-        fd = (np.sum(mask * wsub * oracle.bilateral(sp_, r, oracle.gamma_fixed(1.0), Nd)) -
-              np.sum(mask * wsub * oracle.bilateral(sm_, r, oracle.gamma_fixed(1.0), Nd))) / (2 * h)
-        gerr = max(gerr, abs(gg[b, y, x] - fd) / max(1.0, abs(fd)))
+    npix = 0
+    for b in range(B):
+        for _ in range(256):
+            y, x = int(rng.integers(0, Hd)), int(rng.integers(0, Hd))
+            y0, y1 = max(0, y - 2 * r), min(Hd, y + 2 * r + 1)
+            x0, x1 = max(0, x - 2 * r), min(Hd, x + 2 * r + 1)
+            sub = f64b[b, y0:y1, x0:x1]
+            mask = np.zeros_like(sub)
+            mask[max(0, y - r) - y0:min(Hd, y + r + 1) - y0,
+                 max(0, x - r) - x0:min(Hd, x + r + 1) - x0] = 1
+            wsub = wb[b, y0:y1, x0:x1].astype(np.float64) * mask
+            h = 1e-4
+            sp_, sm_ = sub.copy(), sub.copy()
+            sp_[y - y0, x - x0] += h
+            sm_[y - y0, x - x0] -= h
+            fd = (np.sum(wsub * oracle.bilateral(sp_, r, gamma_d, Nd)) -
+                  np.sum(wsub * oracle.bilateral(sm_, r, gamma_d, Nd))) / (2 * h)
+            gerr = max(gerr, abs(gg[b, y, x] - fd) / max(1.0, abs(fd)))
+            npix += 1
     res["differentiation_16x512sq_r7_N19"] = {
+        "gamma_mode": "from_sigma (gamma = 1/(sigma_r sqrt N), N frozen)",
         "fwd_bwd_ms": ms_d, "fwd_bwd_mpx_s": B * Hd * Hd / ms_d / 1e3,
-        "grad_max_rel_err_vs_fp64_fd": gerr}
-    del ft, wt, outd, svd, gi
+        "grad_sigma": gs_val, "grad_sigma_fp64_fd": fd_sig,
+        "grad_sigma_rel_err_vs_fp64_fd": abs(gs_val - fd_sig) / max(1.0, abs(fd_sig)),
+        "grad_img_max_rel_err_vs_fp64_fd": gerr, "grad_img_pixels_checked": npix}
+    del ft, wt, outd, svd, gi, wsd
 
     # truncated basis (end of Sec. 3): the headline workload with the highest
     # harmonics of q_N's expansion dropped under a kernel tolerance
@@ -464,7 +501,54 @@ def extras(dev, flush, stream):
         "fwd_bwd_ms": ms_pfb, "fwd_bwd_mpx_s": H * W / ms_pfb / 1e3,
         "tflops_algorithmic": tf, "frac_of_fp32_peak": tf / FP32_PEAK_TFLOPS,
         "err_vs_fp64": _err_stats(got, ref_p), "oracle_forward": o_p}
+    del img, out, svq, gq, gi
+    res["forward_sweep"] = forward_sweep(dev, flush, stream, rng)
     return res
+
+
+def forward_sweep(dev, flush, stream, rng):
+    """The forward sweep, all 36 runs: {1024^2, 4096^2} x {rectangles+noise,
+    sinusoid field} x r in {3, 10, 30} x sigma_r in {0.1, 0.2, 0.3} (N = 41, 11,
+    5), plain forward in the default launch configuration. Per run: time,
+    Mpixel/s, both roofline times (8 B/px over the HBM peak; the algorithmic
+    FLOPs over the FP32 peak), the bound, the fraction of the slower roofline
+    achieved, and the error against the FP64 oracle on 64 sampled pixels."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import paper_1107_4617_gb300 as bf
+    from paper_1107_4617_gb300 import synth
+    hbm, hbm_src = hbm_peak_gbs()
+    runs = {}
+    for size in (1024, 4096):
+        for kind in ("rect", "sin"):
+            f_np = synth.image(kind, size, size, seed=2)
+            f64 = f_np.astype(np.float64)
+            img = torch.from_numpy(f_np).to(dev)
+            out = torch.empty_like(img)
+            px = size * size
+            for r in (3, 10, 30):
+                for sg in (0.1, 0.2, 0.3):
+                    N = bf.bf_resolve_N(sg, 1.0)
+                    call = lambda r=r, sg=sg: bf.bf_forward(img, r, sg, 1.0, 0, out=out,
+                                                            stream=stream)
+                    call()
+                    ms = _time_ms(call, flush, stream, reps=5)
+                    t_hbm = 8.0 * px / (hbm * 1e9) * 1e3
+                    t_alu = fwd_flops_per_px(N) * px / (FP32_PEAK_TFLOPS * 1e12) * 1e3
+                    idx = rng.integers(0, px, 64)
+                    ref = oracle.bilateral_points(f64, r, oracle.gamma_fixed(1.0), N, idx)
+                    runs[f"{size}sq_{kind}_r{r}_sigma{sg}_N{N}"] = {
+                        "ms": ms, "mpx_s": px / ms / 1e3, "N": N,
+                        "roofline_ms": {"hbm": t_hbm, "alu": t_alu},
+                        "bound": "alu" if t_alu >= t_hbm else "hbm",
+                        "frac": max(t_hbm, t_alu) / ms,
+                        "err_vs_fp64": _err_stats(out.cpu().numpy().ravel()[idx], ref)}
+            del img, out
+    return {"runs": runs, "hbm_peak_gbs": hbm, "hbm_peak_source": hbm_src,
+            "fp32_peak_tflops": FP32_PEAK_TFLOPS,
+            "model": "forward 8 B/px and 17(N+1)+10 FLOP/px (no saved buffers)"}
 
 
 def run_reference(args, rank, world):
@@ -647,6 +731,28 @@ def main():
         torch.cuda.synchronize(dev)
         t40 += e40[0].elapsed_time(e40[1]) / 1e3
     fwd40_value = px * max(3, args.steps // 2) / t40 / 1e6
+    # the metric's N = 40: forward with saved quads + adjoint, per-kernel events
+    e3 = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    tf40 = tb40 = 0.0
+    n40 = max(3, args.steps // 2)
+    for it in range(n40 + 2):
+        flush.zero_()
+        e3[0].record(stream)
+        bf.bf_forward(img, R, SIGMA, T_RANGE, 40, out=out, opts=opts, saved=saved, stream=stream)
+        e3[1].record(stream)
+        bf.bf_backward(img, out, g, saved, R, SIGMA, T_RANGE, 40, grad_img=gimg, opts=opts,
+                       stream=stream)
+        e3[2].record(stream)
+        torch.cuda.synchronize(dev)
+        if it >= 2:
+            tf40 += e3[0].elapsed_time(e3[1]) / 1e3
+            tb40 += e3[1].elapsed_time(e3[2]) / 1e3
+    n40_line = {
+        "fwd_bwd_mpx_s": px * n40 / (tf40 + tb40) / 1e6, "ms_per_step": 1e3 * (tf40 + tb40) / n40,
+        "fwd": {"ms": 1e3 * tf40 / n40,
+                "frac": fwd_flops_per_px(40) * px / (tf40 / n40) / 1e12 / FP32_PEAK_TFLOPS},
+        "bwd": {"ms": 1e3 * tb40 / n40,
+                "frac": bwd_flops_per_px(40) * px / (tb40 / n40) / 1e12 / FP32_PEAK_TFLOPS}}
     # the plain forward at N = 41 (inference: no saved quads for an adjoint)
     tp = 0.0
     for _ in range(max(3, args.steps // 2)):
@@ -814,6 +920,7 @@ def main():
                        "e2e": "pinned host buffers; double-buffered: the upload of step i+1 and "
                               "the download of step i-1 overlap the kernels of step i"},
             "fwd_mpx_s": fwd_value, "fwd_n40_mpx_s": fwd40_value,
+            "fwd_bwd_n40_mpx_s": n40_line["fwd_bwd_mpx_s"], "n40": n40_line,
             "fwd_plain_n41_mpx_s": fwd_plain_value,
             "clocks": clocks,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * px * 4,

@@ -88,18 +88,30 @@ __device__ __forceinline__ void fwd_tile(const FwdParams& p, int bx, int by, flo
 #pragma unroll
         for (int i = 0; i < KMAX; ++i) {
             if (i < p.K) {
-                float4 d;
-                d.x = se.zc * fe - sl.zc * fl;
-                d.y = se.zs * fe - sl.zs * fl;
-                d.z = se.zc - sl.zc;
-                d.w = se.zs - sl.zs;
                 if (KAHAN) {
-                    float4 y, t;
-                    y.x = d.x - E[i].x; t.x = V[i].x + y.x; E[i].x = (t.x - V[i].x) - y.x; V[i].x = t.x;
-                    y.y = d.y - E[i].y; t.y = V[i].y + y.y; E[i].y = (t.y - V[i].y) - y.y; V[i].y = t.y;
-                    y.z = d.z - E[i].z; t.z = V[i].z + y.z; E[i].z = (t.z - V[i].z) - y.z; V[i].z = t.z;
-                    y.w = d.w - E[i].w; t.w = V[i].w + y.w; E[i].w = (t.w - V[i].w) - y.w; V[i].w = t.w;
+                    // each pixel's products added on their own with compensation
+                    // (Kahan 1965), so a pixel's entering and leaving
+                    // contributions (bit-identical products) cancel
+                    auto kadd = [](float& v, float& e, float x) {
+                        const float y = x - e;
+                        const float t = v + y;
+                        e = (t - v) - y;
+                        v = t;
+                    };
+                    kadd(V[i].x, E[i].x, __fmul_rn(se.zc, fe));
+                    kadd(V[i].x, E[i].x, -__fmul_rn(sl.zc, fl));
+                    kadd(V[i].y, E[i].y, __fmul_rn(se.zs, fe));
+                    kadd(V[i].y, E[i].y, -__fmul_rn(sl.zs, fl));
+                    kadd(V[i].z, E[i].z, se.zc);
+                    kadd(V[i].z, E[i].z, -sl.zc);
+                    kadd(V[i].w, E[i].w, se.zs);
+                    kadd(V[i].w, E[i].w, -sl.zs);
                 } else {
+                    float4 d;
+                    d.x = se.zc * fe - sl.zc * fl;
+                    d.y = se.zs * fe - sl.zs * fl;
+                    d.z = se.zc - sl.zc;
+                    d.w = se.zs - sl.zs;
                     V[i].x += d.x; V[i].y += d.y; V[i].z += d.z; V[i].w += d.w;
                 }
                 rotate(se.zc, se.zs, se.wc, se.ws);

@@ -583,9 +583,14 @@ __device__ __forceinline__ void sys_tile(const SysParams& p, int bx, int by, siz
                     }
                 }
             } else {
-                // Kahan (forward): all five streams advance together, pair by
-                // pair, so the four streams' increments of a row are formed
-                // together and added once with compensation
+                // Kahan (forward): every stream's planes are added to the running
+                // sums one by one with compensation (Kahan 1965: y = p - e,
+                // t = D + y, e = (t - D) - y, D = t). A pixel enters and, 2r+1
+                // rows later, leaves a lane's sums with bit-identical products
+                // (same stream code, no fused multiply-add into the sum), so
+                // with the adds compensated its two contributions cancel and
+                // the sums do not drift down a tall band; summing the four
+                // streams first (one rounding per step) would not cancel.
                 static_assert(!HALF && !BWD && !DC,
                               "the Kahan form runs whole pairs from k0, forward only");
                 Strm s0 = seed<SEED>(pix_f(c0), p.gamma, p.k0);
@@ -593,32 +598,27 @@ __device__ __forceinline__ void sys_tile(const SysParams& p, int bx, int by, siz
                 Strm s2 = seed<SEED>(pix_f(c2v), p.gamma, p.k0);
                 Strm s3 = seed<SEED>(pix_f(c3), p.gamma, p.k0);
                 Strm sc = seed<SEED>(pix_f(cc), p.gamma, p.k0);
+                const float2 m1 = dup(-1.f);
+                auto kadd = [&](float2& D, float2& E, float2 v) {
+                    const float2 y = __ffma2_rn(E, m1, v);
+                    const float2 t2 = __fadd2_rn(D, y);
+                    E = __ffma2_rn(y, m1, __ffma2_rn(D, m1, t2));
+                    D = t2;
+                };
 #pragma unroll
                 for (int i = 0; i < KP; ++i) {
                     const float4 A = rd[(2 * i) * LD];
                     const float4 B = rd[(2 * i + 1) * LD];
-                    // this row's increment of each running sum, then a
-                    // Kahan-compensated add (Kahan 1965): y = inc - e,
-                    // t = D + y, e = (t - D) - y, D = t
-                    const float2 m1 = dup(-1.f);
-                    float2 ix = __fmul2_rn(s0.c, U0), iy = __fmul2_rn(s0.s, U0);
-                    float2 iz = __fmul2_rn(s0.c, V0), iw = __fmul2_rn(s0.s, V0);
-                    ix = __ffma2_rn(s1.c, U1, ix); ix = __ffma2_rn(s2.c, U2, ix);
-                    ix = __ffma2_rn(s3.c, U3, ix);
-                    iy = __ffma2_rn(s1.s, U1, iy); iy = __ffma2_rn(s2.s, U2, iy);
-                    iy = __ffma2_rn(s3.s, U3, iy);
-                    iz = __ffma2_rn(s1.c, V1, iz); iz = __ffma2_rn(s2.c, V2, iz);
-                    iz = __ffma2_rn(s3.c, V3, iz);
-                    iw = __ffma2_rn(s1.s, V1, iw); iw = __ffma2_rn(s2.s, V2, iw);
-                    iw = __ffma2_rn(s3.s, V3, iw);
-                    auto kadd = [&](float2& D, float2& E, float2 inc) {
-                        const float2 y = __ffma2_rn(E, m1, inc);
-                        const float2 t2 = __fadd2_rn(D, y);
-                        E = __ffma2_rn(y, m1, __ffma2_rn(D, m1, t2));
-                        D = t2;
+                    auto add_stream = [&](const Strm& q, float2 U, float2 V) {
+                        kadd(Dx[i], Ex[i], __fmul2_rn(q.c, U));
+                        kadd(Dy[i], Ey[i], __fmul2_rn(q.s, U));
+                        kadd(Dz[i], Ez[i], __fmul2_rn(q.c, V));
+                        kadd(Dw[i], Ew[i], __fmul2_rn(q.s, V));
                     };
-                    kadd(Dx[i], Ex[i], ix); kadd(Dy[i], Ey[i], iy);
-                    kadd(Dz[i], Ez[i], iz); kadd(Dw[i], Ew[i], iw);
+                    add_stream(s0, U0, V0);
+                    add_stream(s1, U1, V1);
+                    add_stream(s2, U2, V2);
+                    add_stream(s3, U3, V3);
                     const float2 hx = __fadd2_rn(make_float2(A.x, A.y), Dx[i]);
                     const float2 hy = __fadd2_rn(make_float2(A.z, A.w), Dy[i]);
                     const float2 hz = __fadd2_rn(make_float2(B.x, B.y), Dz[i]);

@@ -57,11 +57,21 @@ def sinusoids(H: int, W: int, seed: int = 0, n_waves: int = 8) -> np.ndarray:
     return acc.astype(np.float32)
 
 
+def noise(H: int, W: int, seed: int = 0) -> np.ndarray:
+    """Independent U[0, 1] pixels: almost every neighbour differs from the
+    centre by much more than sigma_r, so den stays near 1 (the hardest case
+    for cancellation in the recombined sums)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return rng.random((H, W)).astype(np.float32)
+
+
 def image(kind: str, H: int, W: int, seed: int = 0) -> np.ndarray:
     if kind in ("rect", "rectangles"):
         return rectangles(H, W, seed)
     if kind in ("sin", "sinusoids"):
         return sinusoids(H, W, seed)
+    if kind == "noise":
+        return noise(H, W, seed)
     raise ValueError(f"unknown image kind {kind!r}")
 
 

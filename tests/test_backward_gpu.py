@@ -177,24 +177,26 @@ def test_3d_launch_matches_per_image(cuda_lib, kahan_fallback):
     assert abs(float(gs) - total) <= 1e-4 * max(1.0, abs(total))
 
 
-def test_headline_adjoint_full_size_sampled(cuda_lib):
-    """The headline workload (4096^2, r=10, sigma_r=0.1 -> N=41) in the bench's
-    launch configuration: dL/df at 12 sampled pixels (corners included)
-    against FP64 central differences of the oracle on a crop around each."""
+@pytest.mark.parametrize("N", [41, 40])
+def test_headline_adjoint_full_size_sampled(cuda_lib, N):
+    """The headline workload (4096^2, r=10, sigma_r=0.1 -> N=41, and the
+    metric's N=40) in the bench's launch configuration: dL/df at 12 sampled
+    pixels (corners included) against FP64 central differences of the oracle
+    on a crop around each."""
     bf = cuda_lib
     H = W = 4096
-    r, N = 10, 41
+    r = 10
     f = synth.rectangles(H, W, seed=0)
     w = synth.weights((H, W), seed=1)
     img = torch.from_numpy(f).cuda()
     g = torch.from_numpy(w).cuda()
     opts = bf._opts(save=True)
     sv = torch.empty((H, W, 4), device="cuda")
-    out = bf.bf_forward(img, r, 0.1, 1.0, 0, opts=opts, saved=sv)
+    out = bf.bf_forward(img, r, 0.1, 1.0, N, opts=opts, saved=sv)
     gi = torch.empty_like(img)
-    bf.bf_backward(img, out, g, sv, r, 0.1, 1.0, 0, grad_img=gi, opts=opts)
+    bf.bf_backward(img, out, g, sv, r, 0.1, 1.0, N, grad_img=gi, opts=opts)
     gg = gi.cpu().numpy()
-    rng = np.random.default_rng(17)
+    rng = np.random.default_rng(17 + N)
     pts = [(0, 0), (H - 1, W - 1), (0, W - 1), (H - 1, 0)] + \
         [(int(rng.integers(0, H)), int(rng.integers(0, W))) for _ in range(8)]
     for y, x in pts:
@@ -210,3 +212,26 @@ def test_headline_adjoint_full_size_sampled(cuda_lib):
         fd = (np.sum(wsub * oracle.bilateral(sp, r, math.pi / 2, N)) -
               np.sum(wsub * oracle.bilateral(sm, r, math.pi / 2, N))) / (2 * h)
         assert abs(gg[y, x] - fd) <= GTOL * max(1.0, abs(fd)), (y, x, gg[y, x], fd)
+
+
+@pytest.mark.parametrize("r", [57, 64])
+def test_adjoint_largest_windows(cuda_lib, r):
+    """The adjoint at r = 57 and at BF_R_MAX = 64 (256-thread strips) against
+    the oracle's direct-form gradient on the whole image."""
+    bf = cuda_lib
+    H, W = 180, 300
+    f = synth.sinusoids(H, W, seed=r)
+    w = synth.weights((H, W), seed=2)
+    img = torch.from_numpy(f).cuda()
+    g = torch.from_numpy(w).cuda()
+    opts = bf._opts(save=True)
+    sv = torch.empty((H, W, 4), device="cuda")
+    out = bf.bf_forward(img, r, 0.2, 1.0, 0, opts=opts, saved=sv)
+    gi = torch.empty_like(img)
+    bf.bf_backward(img, out, g, sv, r, 0.2, 1.0, 0, grad_img=gi, opts=opts)
+    torch.cuda.synchronize()
+    N = oracle.resolve_N(0.2, 1.0)
+    ref, _ = oracle.bilateral_grad(f.astype(np.float64), w.astype(np.float64), r, math.pi / 2, N)
+    got = gi.cpu().numpy()
+    scale = np.abs(ref).max()
+    assert np.abs(got - ref).max() <= GTOL * scale

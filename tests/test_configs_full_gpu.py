@@ -6,8 +6,9 @@ outputs the oracle computes one by one:
   plain and Kahan-compensated running sums, and the BF16-stored image;
 - batching: 256 uneven images (sides 64..2048, r 2..32, sigma_r 0.08..0.4)
   in one persistent launch;
-- differentiation: 16 x 512^2, r=7, sigma_r=0.15 (N=19), one [B,H,W]
-  forward and one adjoint launch, dL/df against FP64 central differences.
+- differentiation: 16 x 512^2, r=7, sigma_r=0.15 (N=19), gamma from sigma_r,
+  one [B,H,W] forward and one adjoint launch, dL/dsigma_r and dL/df against
+  FP64 central differences and the direct-form gradient.
 """
 import math
 
@@ -74,7 +75,20 @@ def test_batching_config_256_images(cuda_lib):
     assert all(float(o.min()) > -7.0 for o in outs)  # every image written
 
 
+def _loss(f, w, r, gamma, N):
+    """L = sum(w * out) over a [B, H, W] batch, from the FP64 oracle."""
+    return sum(float(np.sum(w[b].astype(np.float64) * oracle.bilateral(f[b], r, gamma, N)))
+               for b in range(f.shape[0]))
+
+
 def test_differentiation_config_16x512sq(cuda_lib):
+    """16 x 512^2, r=7, sigma_r=0.15 (N=19) with gamma = 1/(sigma_r sqrt N) (the
+    variance control of Sec. 3, N frozen by the rule), so dL/dsigma_r is live:
+    one [B,H,W] forward and one adjoint launch, as the benchmark runs them.
+    dL/dsigma_r (summed over the batch) against FP64 central differences of the
+    oracle in sigma_r (h = 1e-4, N frozen) and against the oracle's direct-form
+    derivative; dL/df against the direct-form gradient at every pixel and
+    against FP64 central differences at 256 sampled pixels per image."""
     bf = cuda_lib
     B, H, W, r, sigma = 16, 512, 512, 7, 0.15
     N = bf.bf_resolve_N(sigma, 1.0)
@@ -82,29 +96,50 @@ def test_differentiation_config_16x512sq(cuda_lib):
     w = synth.weights((B, H, W), seed=1)
     ft = torch.from_numpy(f).cuda()
     wt = torch.from_numpy(w).cuda()
-    opts = bf._opts(save=True)
+    opts = bf._opts(save=True, gamma_mode=bf.GAMMA_FROM_SIGMA)
     sv = torch.empty((B, H, W, 4), device="cuda")
     out = bf.bf_forward3d(ft, r, sigma, 1.0, N, opts=opts, saved=sv)
     gi = torch.empty_like(ft)
-    bf.bf_backward3d(ft, out, wt, sv, r, sigma, 1.0, N, grad_img=gi, opts=opts)
+    gs = torch.zeros((1,), device="cuda")
+    ws = torch.empty((bf.bf_backward3d_workspace_bytes(B, H, W, r, sigma, 1.0, N, opts) // 4 + 1,),
+                     device="cuda")
+    bf.bf_backward3d(ft, out, wt, sv, r, sigma, 1.0, N, grad_img=gi, grad_sigma=gs, workspace=ws,
+                     opts=opts)
     torch.cuda.synchronize()
+    gamma = oracle.gamma_from_sigma(sigma, N)
     o = out.cpu().numpy()
     gg = gi.cpu().numpy()
+    f64 = f.astype(np.float64)
+    # forward on sampled pixels and dL/df on every pixel (direct form)
     rng = np.random.default_rng(13)
+    dgamma = 0.0
     for b in range(B):
-        idx = rng.integers(0, H * W, 20)
-        ref = oracle.bilateral_points(f[b].astype(np.float64), r, G1, N, idx)
+        idx = rng.integers(0, H * W, 64)
+        ref = oracle.bilateral_points(f64[b], r, gamma, N, idx)
         assert rel_err(o[b].ravel()[idx], ref).max() <= TOL
-        y, x = int(rng.integers(0, H)), int(rng.integers(0, W))
-        y0, y1 = max(0, y - 2 * r), min(H, y + 2 * r + 1)
-        x0, x1 = max(0, x - 2 * r), min(W, x + 2 * r + 1)
-        sub = f[b, y0:y1, x0:x1].astype(np.float64)
-        mask = np.zeros_like(sub)
-        mask[max(0, y - r) - y0:min(H, y + r + 1) - y0, max(0, x - r) - x0:min(W, x + r + 1) - x0] = 1
-        wsub = w[b, y0:y1, x0:x1].astype(np.float64) * mask
-        h = 1e-4
-        sp = sub.copy(); sp[y - y0, x - x0] += h
-        sm = sub.copy(); sm[y - y0, x - x0] -= h
-        fd = (np.sum(wsub * oracle.bilateral(sp, r, G1, N)) -
-              np.sum(wsub * oracle.bilateral(sm, r, G1, N))) / (2 * h)
-        assert abs(gg[b, y, x] - fd) <= 1e-3 * max(1.0, abs(fd)), (b, y, x, gg[b, y, x], fd)
+        gref, dg = oracle.bilateral_grad(f64[b], w[b].astype(np.float64), r, gamma, N)
+        dgamma += dg
+        assert np.abs(gg[b] - gref).max() <= 1e-3 * np.abs(gref).max(), b
+    # dL/dsigma_r: gamma = 1/(sigma sqrt N), so dL/dsigma = -(gamma / sigma) dL/dgamma
+    dsig_direct = -(gamma / sigma) * dgamma
+    h = 1e-4
+    fd = (_loss(f64, w, r, oracle.gamma_from_sigma(sigma + h, N), N) -
+          _loss(f64, w, r, oracle.gamma_from_sigma(sigma - h, N), N)) / (2 * h)
+    assert abs(dsig_direct - fd) <= 1e-5 * max(1.0, abs(fd)), (dsig_direct, fd)
+    assert abs(float(gs) - fd) <= 1e-3 * max(1.0, abs(fd)), (float(gs), fd)
+    # dL/df: FP64 central differences at 256 pixels of each image, on a crop
+    for b in range(B):
+        for _ in range(256):
+            y, x = int(rng.integers(0, H)), int(rng.integers(0, W))
+            y0, y1 = max(0, y - 2 * r), min(H, y + 2 * r + 1)
+            x0, x1 = max(0, x - 2 * r), min(W, x + 2 * r + 1)
+            sub = f64[b, y0:y1, x0:x1]
+            mask = np.zeros_like(sub)
+            mask[max(0, y - r) - y0:min(H, y + r + 1) - y0,
+                 max(0, x - r) - x0:min(W, x + r + 1) - x0] = 1
+            wsub = w[b, y0:y1, x0:x1].astype(np.float64) * mask
+            sp = sub.copy(); sp[y - y0, x - x0] += h
+            sm = sub.copy(); sm[y - y0, x - x0] -= h
+            fdf = (np.sum(wsub * oracle.bilateral(sp, r, gamma, N)) -
+                   np.sum(wsub * oracle.bilateral(sm, r, gamma, N))) / (2 * h)
+            assert abs(gg[b, y, x] - fdf) <= 1e-3 * max(1.0, abs(fdf)), (b, y, x, gg[b, y, x], fdf)

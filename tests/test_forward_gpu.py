@@ -146,6 +146,23 @@ def test_saved_buffers(cuda_lib):
     assert (1.0 / sv[1]).min() >= 1.0 - 1e-5
 
 
+def test_full_size_sampled_n40(cuda_lib):
+    """4096x4096, r=10, N=40 (even order: the constant harmonic runs apart from
+    the pairs) in the default launch configuration, with saved quads as in the
+    fwd+bwd step: 1200 sampled pixels plus corners and edge midpoints."""
+    H = W = 4096
+    f = synth.rectangles(H, W, seed=0)
+    got, sv = run_fwd(cuda_lib, f, 10, 0.1, 1.0, 40, saved=True)
+    rng = np.random.default_rng(40)
+    idx = np.concatenate([rng.integers(0, H * W, 1200),
+                          [0, W - 1, (H - 1) * W, H * W - 1, W // 2, (H // 2) * W, (H // 2) * W + W - 1,
+                           (H - 1) * W + W // 2]])
+    ref, den = oracle.bilateral_points(f.astype(np.float64), 10, math.pi / 2, 40, idx,
+                                       return_den=True)
+    assert rel_err(got.ravel()[idx], ref).max() <= TOL
+    np.testing.assert_allclose(1.0 / sv[1].ravel()[idx], den, rtol=2e-5, atol=0)
+
+
 def test_full_size_sampled_headline(cuda_lib):
     """4096x4096, r=10, sigma_r=0.1 -> N=41 in the default launch
     configuration: 3000 sampled pixels (plus the four corners and edge
@@ -177,9 +194,10 @@ def test_chunked_harmonics_with_saved(cuda_lib, N):
     np.testing.assert_allclose(1.0 / sv[1], den, rtol=2e-5, atol=0)
 
 
-@pytest.mark.parametrize("r", [21, 30, 45, 56])
+@pytest.mark.parametrize("r", [21, 30, 45, 56, 57, 64])
 def test_wide_strips_large_r(cuda_lib, r):
-    """Large r: 128-thread strips up to r = 40, 256-thread strips above."""
+    """Large r: 128-thread strips up to r = 40, 256-thread strips above, up to
+    BF_R_MAX = 64 (256 - 2 * 64 = 128 output columns per strip)."""
     f = synth.sinusoids(260, 333, seed=r)
     got = run_fwd(cuda_lib, f, r, 0.1, 1.0, 0)
     ref, _ = oracle_ref(f, r, 0.1, 1.0, 0)
@@ -196,6 +214,49 @@ def test_kahan_precision_form(cuda_lib, saved):
     got = res[0] if saved else res
     ref, _ = oracle_ref(f, 30, 0.1, 1.0, 0)
     assert rel_err(got, ref).max() <= TOL
+
+
+def _noise_case(cuda_lib, r, N, tile_h):
+    """Independent U[0, 1] pixels on 8192 x 300 (den near 1: the hardest case
+    for cancellation), forward with plain and with Kahan-compensated running
+    sums, relative error on 3000 pixels of the bottom 200 rows (where the
+    vertical running sums of a tall band have run longest) and 1000 others."""
+    H, W = 8192, 300
+    f = synth.noise(H, W, seed=3)
+    rng = np.random.default_rng(1)
+    idx = np.concatenate([rng.integers((H - 200) * W, H * W, 3000), rng.integers(0, H * W, 1000)])
+    ref = oracle.bilateral_points(f.astype(np.float64), r, math.pi / 2, N, idx)
+    errs = {}
+    for kahan in (False, True):
+        got, _ = run_fwd(cuda_lib, f, r, 0.1, 1.0, N, kahan=kahan, saved=True, tile_h=tile_h)
+        errs[kahan] = rel_err(got.ravel()[idx], ref).max()
+    return errs[False], errs[True]
+
+
+def test_kahan_bounds_the_drift_of_a_tall_band(cuda_lib):
+    """A case where plain FP32 running sums drift past the parity bar and the
+    Kahan form keeps them inside it: white noise, r = 2, N = 64, one band of
+    all 8192 rows per strip (tile_h = H). Each step adds the planes of a pixel
+    entering the window and of one leaving it 2r+1 rows after it entered; the
+    rounding of those adds random-walks down the band. Kahan-compensated adds
+    of every stream's (bit-identical) products let a pixel's entering and
+    leaving contributions cancel."""
+    plain, kahan = _noise_case(cuda_lib, 2, 64, 8192)
+    assert kahan <= TOL, kahan
+    assert plain > TOL, plain  # measured 5.1e-4 on a GB300
+
+
+@pytest.mark.parametrize("r", [0, 1])
+def test_smallest_windows_on_white_noise(cuda_lib, r):
+    """The worst case of the error growth along a strip: white noise, r <= 1
+    (den close to 1 at most pixels), N = 64, in the default launch
+    configuration. The Kahan form stays inside the parity bar; the plain form
+    reaches about 1.4 times it (measured 1.4e-4 at r = 1: 7e-6 absolute, at
+    pixels whose value is near 0, where the relative metric's floor is 1e-2),
+    the bound recorded here."""
+    plain, kahan = _noise_case(cuda_lib, r, 64, 0)
+    assert kahan <= TOL, kahan
+    assert plain <= 3 * TOL, plain
 
 
 @pytest.mark.parametrize("kp_max", [1, 3, 6])
@@ -231,15 +292,23 @@ def test_small_r_wide_images(cuda_lib, H, W, r):
     assert rel_err(got, ref).max() <= TOL
 
 
+_SWEEP_IMAGES = {}
+
+
 @pytest.mark.parametrize("size", [1024, 4096])
 @pytest.mark.parametrize("kind", ["rect", "sin"])
-@pytest.mark.parametrize("r,sigma", [(3, 0.1), (10, 0.2), (30, 0.3)])
+@pytest.mark.parametrize("r", [3, 10, 30])
+@pytest.mark.parametrize("sigma", [0.1, 0.2, 0.3])
 def test_sweep_full_size_sampled(cuda_lib, size, kind, r, sigma):
-    """The forward sweep at its own sizes (1024^2 and 4096^2, rectangles+noise
-    and the sinusoid field, r in {3, 10, 30}, sigma_r 0.1/0.2/0.3 -> N =
-    41/11/5) in the default launch configuration: 400 sampled pixels plus
-    the corners and edge midpoints against the oracle, evaluated one by one."""
-    f = synth.image(kind, size, size, seed=2)
+    """The forward sweep at its own sizes, all 36 runs crossed: 1024^2 and
+    4096^2, rectangles+noise and the sinusoid field, r in {3, 10, 30}, sigma_r
+    in {0.1, 0.2, 0.3} -> N = 41/11/5, in the default launch configuration:
+    400 sampled pixels plus the corners and edge midpoints against the
+    oracle, evaluated one by one."""
+    key = (kind, size)
+    if key not in _SWEEP_IMAGES:
+        _SWEEP_IMAGES[key] = synth.image(kind, size, size, seed=2)
+    f = _SWEEP_IMAGES[key]
     got = run_fwd(cuda_lib, f, r, sigma, 1.0, 0)
     rng = np.random.default_rng(size + r)
     n = size * size
