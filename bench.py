@@ -551,6 +551,95 @@ def forward_sweep(dev, flush, stream, rng):
             "model": "forward 8 B/px and 17(N+1)+10 FLOP/px (no saved buffers)"}
 
 
+def banded_run(dev, stream, flush, rank, world, steps, warmup, e2e=False):
+    """One 4096^2 image (rectangles+noise, r = 10, N = 41) split over the ranks
+    in row bands. Algorithm 2's moving sums are local, so a band with r rows of
+    f from each neighbour gives its own rows of the output exactly, and the
+    adjoint needs 2r rows of f and r of dL/dout. Per step: two point-to-point
+    halo exchanges (f with 2r rows, dL/dout with r), the forward with saved
+    quads and the adjoint on the haloed frame (the library's kernels), and one
+    all-reduce of the loss L = sum(w * out) over the bands. With one rank the
+    split is the identity. Returns (whole-image pixels / slowest rank's
+    seconds per step, the rank's dL/df band, timing and layout)."""
+    import numpy as np
+    import torch
+
+    import paper_1107_4617_gb300 as bf
+    from paper_1107_4617_gb300 import dist as bdist
+    from paper_1107_4617_gb300 import synth
+    import torch.distributed as tdist
+    f_np = synth.rectangles(H, W, seed=0)
+    w_np = synth.weights((H, W), seed=1)
+    y0, y1 = bdist.band(H, rank, world)
+    rows = y1 - y0
+    fb = torch.from_numpy(f_np[y0:y1]).to(dev)
+    gb = torch.from_numpy(w_np[y0:y1]).to(dev)
+    if e2e:  # this rank's band in pinned host memory, uploaded and downloaded every step
+        h_f = torch.from_numpy(np.ascontiguousarray(f_np[y0:y1])).pin_memory()
+        h_g = torch.from_numpy(np.ascontiguousarray(w_np[y0:y1])).pin_memory()
+        h_out = torch.empty((y1 - y0, W), dtype=torch.float32).pin_memory()
+        h_gi = torch.empty((y1 - y0, W), dtype=torch.float32).pin_memory()
+    N = bf.bf_resolve_N(SIGMA, T_RANGE)
+    opts = bf._opts(save=True)
+    use_pg = world > 1 and tdist.is_available() and tdist.is_initialized()
+    frame = {}
+
+    def step():
+        if e2e:
+            with torch.cuda.stream(stream):
+                fb.copy_(h_f, non_blocking=True)
+                gb.copy_(h_g, non_blocking=True)
+        ext_f, top2 = bdist.exchange_halo(fb, 2 * R, rank, world)
+        ext_g, top1 = bdist.exchange_halo(gb, R, rank, world)
+        h = ext_f.shape[0]
+        if frame.get("h") != h:
+            frame.update(h=h, out=torch.empty_like(ext_f), sv=torch.empty((h, W, 4), device=dev),
+                         gi=torch.empty_like(ext_f), g=torch.zeros_like(ext_f))
+        gfr = frame["g"]
+        gfr.zero_()
+        gfr[top2 - top1:top2 - top1 + ext_g.shape[0]] = ext_g
+        bf.bf_forward(ext_f, R, SIGMA, T_RANGE, N, out=frame["out"], opts=opts, saved=frame["sv"],
+                      stream=stream)
+        bf.bf_backward(ext_f, frame["out"], gfr, frame["sv"], R, SIGMA, T_RANGE, N,
+                       grad_img=frame["gi"], opts=opts, stream=stream)
+        loss = torch.dot(gb.reshape(-1), frame["out"][top2:top2 + rows].reshape(-1))
+        if use_pg:
+            tdist.all_reduce(loss)
+        frame["top"] = top2
+        if e2e:
+            with torch.cuda.stream(stream):
+                h_out.copy_(frame["out"][top2:top2 + rows], non_blocking=True)
+                h_gi.copy_(frame["gi"][top2:top2 + rows], non_blocking=True)
+        return loss
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    if use_pg:
+        tdist.barrier()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t = 0.0
+    for _ in range(steps):
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        a.record(stream)
+        step()
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        t += a.elapsed_time(b) / 1e3
+    if use_pg:
+        tdist.barrier()
+    t_max = bdist.max_over_ranks(t, dev)
+    gi = frame["gi"][frame["top"]:frame["top"] + rows]
+    info = {"ms_per_step": 1e3 * t_max / steps, "ranks": world, "band_rows": rows,
+            "h2d_bytes_per_step": 2 * rows * W * 4 * world if e2e else 0,
+            "d2h_bytes_per_step": 2 * rows * W * 4 * world if e2e else 0,
+            "halo_rows_f": 2 * R if world > 1 else 0, "halo_rows_dL_dout": R if world > 1 else 0,
+            "collectives_per_step": "2 halo exchanges (isend/irecv) + 1 all-reduce of L"
+            if world > 1 else "none (one band)"}
+    return H * W * steps / t_max / 1e6, gi, info
+
+
 def run_reference(args, rank, world):
     """Reference arm: the FP64 oracle as it stands, on host cores, timed on a
     bounded band of the workload per step."""
@@ -599,6 +688,9 @@ def main():
                              "trunc_1e-3"],
                     help="launch only this 4096^2 r=10 workload's kernel, warmup + steps "
                          "times (profiler captures of the extra workloads)")
+    ap.add_argument("--bands", action="store_true",
+                    help="one image split over the ranks in row bands (halo exchange + one "
+                         "all-reduce per step, strong scaling) as the headline step")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -663,6 +755,35 @@ def main():
         if rank == 0:
             print(json.dumps({"profile_workload": pw, "ms": ms, "mpx_s": H * W / ms / 1e3}),
                   flush=True)
+        return
+
+    if args.bands:
+        sampler = ClockSampler(dev.index if dev.index is not None else 0)
+        sampler.start()
+        time.sleep(0.15)
+        value, _, info = banded_run(dev, stream, flush, rank, world, args.steps, args.warmup)
+        clocks = sampler.stop()
+        e2e_value, _, e2e_info = banded_run(dev, stream, flush, rank, world,
+                                            max(3, args.steps // 2), args.warmup, e2e=True)
+        if rank == 0:
+            print(json.dumps({
+                "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": info["ms_per_step"],
+                "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic",
+                "config": {"workload": f"bilateral cos^N fwd+bwd {H}x{W} r={R} sigma_r={SIGMA} "
+                                       f"N={N} T={T_RANGE}, rectangles+noise, one image in "
+                                       f"{world} row bands",
+                           "H": H, "W": W, "r": R, "N": N, "parallelism": f"row bands x{world}",
+                           "l2": "flushed between timed steps (256 MiB write)"},
+                "bands": info, "clocks": clocks,
+                "e2e": {"value": e2e_value, "unit": UNIT,
+                        "h2d_bytes_per_step": e2e_info["h2d_bytes_per_step"],
+                        "d2h_bytes_per_step": e2e_info["d2h_bytes_per_step"]},
+                "gpu_launches": 2 * args.steps}), flush=True)
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
         return
 
     def step():
@@ -819,6 +940,16 @@ def main():
     e2e_value = bdist.throughput(px * e2e_steps, t_e2e, dev) / 1e6
     del bufs[1]
 
+    # the same step with the image split over the ranks in row bands (halo
+    # exchange + one all-reduce per step; the identity split at one GPU)
+    bands_value, bands_gi, bands_info = banded_run(dev, stream, flush, rank, world,
+                                                   max(3, args.steps // 10), 3)
+    bands_info["mpx_s"] = bands_value
+    bands_info["scaling"] = "strong"
+    if world == 1:  # the identity split reproduces the headline step's dL/df
+        bands_info["grad_equal_to_whole_image_step"] = bool(torch.equal(bands_gi, gimg))
+    del bands_gi
+
     # accuracy vs the FP64 oracle on sampled pixels (reported, not timed)
     err = None
     if rank == 0:
@@ -929,6 +1060,7 @@ def main():
             "roofline": roofline,
             "cpu_baseline": cpu,
             "max_err_vs_fp64": err,
+            "bands": bands_info,
             "workloads": extra,
         }
         print(json.dumps(line), flush=True)
