@@ -158,6 +158,7 @@ static void fill_sys(const FwdParams& p, SysParams* q) {
     q->Hb = 0; q->Tw = 0;
     q->k0 = p.kstart;
     q->gamma = p.gamma;
+    q->mid = p.mid;
     q->gpi = (float)((double)p.gamma / M_PI);
     for (int i = 0; i < p.K; ++i) {
         q->a[i] = p.a[i];
@@ -211,6 +212,7 @@ bf_status fill_fwd_params(const void* img, float* out, void* saved, int H, int W
     p.ld = ld;
     p.Hb = t.Hb; p.Tw = t.Tw;
     p.gamma = (float)rs.gamma;
+    p.mid = 0.5f * T;
     for (int i = 0; i < rs.K; ++i) p.a[i] = (float)rs.a[i];
     *nt = t.nt; *gx = t.gx; *gy = t.gy;
     return BF_OK;

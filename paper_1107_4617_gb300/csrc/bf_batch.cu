@@ -233,6 +233,7 @@ bf_status bf_batch_prepare(const bf_desc* descs, int n, const bf_opts* opts, voi
             q.k0 = pl.p.kstart + 2 * i0;
             q.acc = (pl.nch == 1) ? 0 : (c == 0 ? 1 : 3);
             q.gamma = pl.p.gamma;
+            q.mid = pl.p.mid;
             q.gpi = (float)((double)pl.p.gamma / M_PI);
             for (int h = 0; h < kc; ++h) {
                 q.a[h] = pl.p.a[i0 + h];

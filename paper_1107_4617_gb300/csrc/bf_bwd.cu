@@ -15,8 +15,14 @@
 // same with Box[S_k], Box[C_k] (saved by the forward). Since theta = gamma f,
 // dL/dgamma = sum_p f(p) G_theta(p).
 //
+// Everything here is unchanged when f and out are shifted by one constant c:
+// the weights depend on differences of theta only, so sum_p G_theta(p) = 0
+// and dL/dgamma = sum_p (f(p) - c) G_theta(p) as well. The saved quads carry
+// f and out shifted by the range midpoint (c = T / 2), and this pass uses
+// them as they are.
+//
 // The stack (alpha C_k, alpha S_k, beta C_k, beta S_k) is recomputed from g
-// and the forward's saved quads (f, 1/den, out, dnum - out dden) with the same
+// and the forward's saved quads (f - c, 1/den, out - c, dnum - out dden) with the same
 // vertical-walker / horizontal-window tile organisation as the forward
 // kernel; it is never stored.
 #include "bf_internal.cuh"

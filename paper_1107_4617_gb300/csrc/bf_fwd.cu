@@ -149,8 +149,8 @@ __device__ __forceinline__ void fwd_tile(const FwdParams& p, int bx, int by, flo
             const float ov = num / den;
             p.out[op] = ov;
             if (p.den) p.den[op] = den;
-            // saved for the adjoint: (f, 1/den, out, dnum - out dden)
-            if (p.sv) p.sv[o] = make_float4(fc, 1.0f / den, ov, dnum - ov * dden);
+            // saved for the adjoint: (f - mid, 1/den, out - mid, dnum - out dden)
+            if (p.sv) p.sv[o] = make_float4(fc - p.mid, 1.0f / den, ov - p.mid, dnum - ov * dden);
         }
         __syncthreads();
     }

@@ -20,7 +20,7 @@ constexpr int KCAP = BF_N_MAX / 2 + 1;
 struct FwdParams {
     const void* img;      // H x W (row pitch ld), FP32 or BF16
     float* out;           // H x W (row pitch ld)
-    float4* sv;           // saved quads (f, 1/den, out, dnum - out dden); nullable, compact
+    float4* sv;           // saved quads (f - mid, 1/den, out - mid, dnum - out dden); nullable, compact
     float* den;           // den of Eq. filter2 (row pitch ld); nullable
     int H, W, r;
     int ld;               // row pitch of img, out and den in elements (>= W)
@@ -29,6 +29,7 @@ struct FwdParams {
     int Hb;               // output rows per band (grid.y tiles)
     int Tw;               // output columns per strip (grid.x tiles)
     float gamma;
+    float mid;            // T / 2, the centre of the range [0, T]
     float a[KCAP];        // a_k for harmonic i (frequency kstart + 2 i)
 };
 
@@ -66,6 +67,7 @@ struct SysParams {
     int k0;          // frequency of this launch's first harmonic
     int acc;         // 0 all harmonics; 1 first, 2 middle, 3 last harmonic chunk
     float gamma;
+    float mid;       // forward: T / 2, the value the planes centre f on
     float gpi;       // gamma / pi
     float a[KCAP];   // a_k of harmonic i (of this chunk)
     float ak[KCAP];  // k * a_k (centre-derivative terms)

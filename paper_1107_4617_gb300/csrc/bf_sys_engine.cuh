@@ -23,6 +23,14 @@
 // harmonic a thread keeps 4 floats of state (D) in registers; S passes
 // through shared memory (16 B written and read per harmonic and step).
 //
+// The forward's planes carry f - mid in place of f (mid = T / 2, the centre
+// of the range [0, T]) and it writes out = num / den + mid: num - mid den =
+// sum_y (f(y) - mid) w(x, y), so the result is the same while the sums round
+// against values half as large. The saved quads keep f and out shifted by
+// mid. The adjoint depends on f only through differences (of theta, and of f
+// against out), so it runs on the shifted values as they are; that removes
+// most of the cancellation between its f and out terms.
+//
 // Harmonics come in pairs (k, k+2), packed in FP32x2 registers. Pair i+1
 // follows from pairs i and i-1 by cos((n+1)x) = 2 cos(x) cos(nx) -
 // cos((n-1)x) with x = 4 theta (the shift identity of Sec. 1 applied twice).
@@ -185,7 +193,7 @@ template <>
 struct Px<false> {
     float f;
 };
-// Adjoint: the forward's saved quad of the pixel (f, 1/den, out,
+// Adjoint: the forward's saved quad of the pixel (f - mid, 1/den, out - mid,
 // dnum - out * dden) and dL/dout.
 template <>
 struct Px<true> {
@@ -379,9 +387,12 @@ __device__ __forceinline__ void sys_tile(const SysParams& p, int bx, int by, siz
             float2 U0, U1, U2, U3, V0, V1, V2, V3;
             float xc = 0.f;  // adjoint: alpha dnum + beta dden of the centre
             if constexpr (!BWD) {
-                U0 = dup(c0.f); U1 = dup(-c1.f); U2 = dup(-c2v.f); U3 = dup(c3.f);
+                // u = f - mid, v = 1 (0 for a masked stream)
                 V0 = dup(gc.m0 ? 1.f : 0.f); V1 = dup(gc.m1 ? -1.f : 0.f);
                 V2 = dup(gc.m2 ? -1.f : 0.f); V3 = dup(gc.m3 ? 1.f : 0.f);
+                const float mc = p.mid;
+                U0 = dup(gc.m0 ? c0.f - mc : 0.f); U1 = dup(gc.m1 ? mc - c1.f : 0.f);
+                U2 = dup(gc.m2 ? mc - c2v.f : 0.f); U3 = dup(gc.m3 ? c3.f - mc : 0.f);
             } else {
                 // alpha = g / den, beta = -alpha out
                 const float a0 = c0.g * c0.sv.y, a1 = c1.g * c1.sv.y;
@@ -660,9 +671,9 @@ __device__ __forceinline__ void sys_tile(const SysParams& p, int bx, int by, siz
                             num += p.out[op]; den += q.y; dn += q.z; dd += q.w;
                         }
                         if (last) {
-                            const float ov = num / den;
-                            p.out[op] = ov;
-                            p.sv[o] = make_float4(cc.f, 1.0f / den, ov, fmaf(-ov, dd, dn));
+                            const float qv = num / den;   // out - mid
+                            p.out[op] = qv + p.mid;
+                            p.sv[o] = make_float4(cc.f - p.mid, 1.0f / den, qv, fmaf(-qv, dd, dn));
                             if constexpr (PITCH) {
                                 if (p.dout) p.dout[op] = den;
                             }
@@ -672,7 +683,7 @@ __device__ __forceinline__ void sys_tile(const SysParams& p, int bx, int by, siz
                         }
                     } else {
                         if (acc >= 2) { num += p.out[op]; den += p.acc_den[o]; }
-                        p.out[op] = last ? num / den : num;
+                        p.out[op] = last ? num / den + p.mid : num;
                         if (acc != 0) p.acc_den[o] = den;
                         if constexpr (PITCH) {
                             if (last && p.dout) p.dout[op] = den;

@@ -134,14 +134,15 @@ def test_bf16_input(cuda_lib):
 
 
 def test_saved_buffers(cuda_lib):
-    """The saved quads: f and out exactly as read and written, 1/den equal to
-    the oracle's normaliser's reciprocal; den >= 1."""
+    """The saved quads: f and out shifted by the range midpoint T/2 (exactly
+    as read and written, in FP32), 1/den equal to the oracle's normaliser's
+    reciprocal; den >= 1."""
     f = synth.rectangles(90, 110, seed=13)
     got, sv = run_fwd(cuda_lib, f, 5, 0.2, 1.0, 0, saved=True)
     ref, den = oracle_ref(f, 5, 0.2, 1.0, 0)
     assert rel_err(got, ref).max() <= TOL
-    np.testing.assert_array_equal(sv[0], f)
-    np.testing.assert_array_equal(sv[2], got)
+    np.testing.assert_array_equal(sv[0], f - np.float32(0.5))
+    np.testing.assert_array_equal(sv[2] + np.float32(0.5), got)
     np.testing.assert_allclose(1.0 / sv[1], den, rtol=2e-5, atol=0)
     assert (1.0 / sv[1]).min() >= 1.0 - 1e-5
 
@@ -189,8 +190,8 @@ def test_chunked_harmonics_with_saved(cuda_lib, N):
     got, sv = run_fwd(cuda_lib, f, 6, 0.2, 1.0, N, saved=True)
     ref, den = oracle_ref(f, 6, 0.2, 1.0, N)
     assert rel_err(got, ref).max() <= TOL
-    np.testing.assert_array_equal(sv[0], f)
-    np.testing.assert_array_equal(sv[2], got)
+    np.testing.assert_array_equal(sv[0], f - np.float32(0.5))
+    np.testing.assert_array_equal(sv[2] + np.float32(0.5), got)
     np.testing.assert_allclose(1.0 / sv[1], den, rtol=2e-5, atol=0)
 
 
