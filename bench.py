@@ -49,9 +49,14 @@ def hbm_peak_gbs():
             return float(json.load(fh)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
     except (OSError, ValueError, KeyError):
         return 6800.0, "fallback 6.8 TB/s"
-# kernels the bench's two launches run (N = 41 -> 11 harmonic pairs, 128-thread strips)
-FWD_KERNEL = "bf_sys_kernel<11, 0, 1, 0, 128, float> (forward, saved buffers)"
-ADJ_KERNEL = "bf_sys_kernel<11, 1, 0, 0, 128, float> (adjoint)"
+# kernels the bench's two launches run: N = 41 -> harmonics 1, 3, .., 41 in 10
+# pairs and a half pair (template <KP, BWD, SAVE, KAHAN, WMAX, Tin, HALF, SEED,
+# FORM, PITCH>), 128-thread strips
+FWD_KERNEL = "bf_sys_kernel<11, 0, 1, 0, 128, float, 1, 1, 0, 0> (forward, saved buffers)"
+ADJ_KERNEL = "bf_sys_kernel<11, 1, 0, 0, 128, float, 1, 1, 0, 0> (adjoint)"
+# N = 40: harmonics 2, 4, .., 40 in 10 pairs, the constant harmonic apart (SEED 2)
+FWD_KERNEL_N40 = "bf_sys_kernel<10, 0, 1, 0, 128, float, 0, 2, 0, 0> (forward, saved buffers)"
+ADJ_KERNEL_N40 = "bf_sys_kernel<10, 1, 0, 0, 128, float, 0, 2, 0, 0> (adjoint)"
 
 
 def fwd_flops_per_px(N: int) -> int:
@@ -71,7 +76,7 @@ def bwd_flops_per_px(N: int) -> int:
 
 # sources that define the headline kernels and their launch shape
 HEADLINE_SOURCES = ("bf_api.cu", "bf_internal.cuh", "bf_sys.cu", "bf_sys_engine.cuh",
-                    "bf_sys_w128.cu")
+                    "bf_sys_first.cuh", "bf_sys_first_d.cu", "bf_sys_first_e.cu")
 
 
 def src_hash() -> str:
@@ -683,6 +688,9 @@ def main():
     ap.add_argument("--kernels-only", action="store_true",
                     help="time the device step only (no e2e, N=40, CPU or accuracy legs); "
                          "used for profiler captures")
+    ap.add_argument("--order", type=int, default=0,
+                    help="with --kernels-only: time N = ORDER instead of the headline's "
+                         "N = 41 (profiler captures of the even-order kernels)")
     ap.add_argument("--profile-workload", default=None,
                     choices=["spatial_M2_N4", "spatial_M2_N4_fb", "alg1_M2", "poly_N6",
                              "trunc_1e-3"],
@@ -721,6 +729,8 @@ def main():
     bf.load()
 
     N = bf.bf_resolve_N(SIGMA, T_RANGE)
+    if args.kernels_only and args.order > 0:
+        N = args.order
     f_np = synth.rectangles(H, W, seed=rank)
     w_np = synth.weights((H, W), seed=1 + rank)
     img = torch.from_numpy(f_np).to(dev)
@@ -870,10 +880,12 @@ def main():
             tb40 += e3[1].elapsed_time(e3[2]) / 1e3
     n40_line = {
         "fwd_bwd_mpx_s": px * n40 / (tf40 + tb40) / 1e6, "ms_per_step": 1e3 * (tf40 + tb40) / n40,
-        "fwd": {"ms": 1e3 * tf40 / n40,
-                "frac": fwd_flops_per_px(40) * px / (tf40 / n40) / 1e12 / FP32_PEAK_TFLOPS},
-        "bwd": {"ms": 1e3 * tb40 / n40,
-                "frac": bwd_flops_per_px(40) * px / (tb40 / n40) / 1e12 / FP32_PEAK_TFLOPS}}
+        "fwd": {"kernel": FWD_KERNEL_N40, "ms": 1e3 * tf40 / n40,
+                "frac": fwd_flops_per_px(40) * px / (tf40 / n40) / 1e12 / FP32_PEAK_TFLOPS,
+                "traffic": load_traffic(FWD_KERNEL_N40)},
+        "bwd": {"kernel": ADJ_KERNEL_N40, "ms": 1e3 * tb40 / n40,
+                "frac": bwd_flops_per_px(40) * px / (tb40 / n40) / 1e12 / FP32_PEAK_TFLOPS,
+                "traffic": load_traffic(ADJ_KERNEL_N40)}}
     # the plain forward at N = 41 (inference: no saved quads for an adjoint)
     tp = 0.0
     for _ in range(max(3, args.steps // 2)):
