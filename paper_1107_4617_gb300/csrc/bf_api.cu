@@ -115,14 +115,54 @@ static bf_status choose_tiles(int H, int W, int r, const bf_opts* o, Tiles* t) {
     return BF_OK;
 }
 
+// Whether launch_sys runs the first-chunk kernels (bf_sys_first*.cu) for
+// this request: FP32 input, compact rows, plain sums, one harmonic chunk, and
+// a seed the first chunk specialises (odd N, or even N with harmonics beside
+// the constant one).
+static bool first_chunk_path(int K, int kstart, int ld, int W, const bf_opts* o, bool kahan) {
+    const int dtype = o ? o->in_dtype : BF_F32;
+    return dtype == BF_F32 && ld == W && !kahan && sys_chunks(K, false, o ? o->kp_max : 0) == 1 &&
+           (kstart == 1 || K > 1);
+}
+
+// Band shape of strips of wi threads: one wave of `slots` resident CTAs over
+// the B images' strips (rounding the band count up would start a second,
+// nearly empty wave), at least 32 rows. Returns the model cost, waves x steps
+// per CTA (a CTA of wi lanes sweeps its band, the 2r warm-up rows and the
+// wi - 1 steps of the skew ramp; a full SM runs the same number of lane-steps
+// per step at either strip width).
+static long long band_shape(int H, int W, int r, int wi, int B, int slots, Tiles* t) {
+    t->nt = wi;
+    t->Tw = wi - 2 * r;
+    t->gx = (W + t->Tw - 1) / t->Tw;
+    int nb = slots / (t->gx * (B > 1 ? B : 1));
+    if (nb < 1) nb = 1;
+    int hb = (H + nb - 1) / nb;
+    if (hb < 32) hb = 32;
+    t->Hb = hb;
+    t->gy = (H + t->Hb - 1) / t->Hb;
+    const long long ctas = (long long)t->gx * t->gy * (B > 1 ? B : 1);
+    const long long waves = (ctas + slots - 1) / slots;
+    return waves * (long long)(t->Hb + 2 * r + wi - 1);
+}
+
 // The skewed-strip engine (bf_sys.cu) serves every request whose strip of
 // Wi threads keeps at least 16 output columns (Wi - 2r >= 16): 128-thread
 // strips up to r = 40 (two CTAs per SM: measured faster than wider strips
 // with one CTA per SM even at r = 30, where half the lanes are halo),
-// 256-thread strips above. Bands: one wave of resident CTAs.
-static bool sys_tiles(int H, int W, int ld, int r, const bf_opts* o, Tiles* t) {
+// 256-thread strips above. Bands: one wave of resident CTAs; the B images of
+// a [B, H, W] launch share the wave. When the launch runs the first-chunk
+// kernels (narrow64: FP32, compact, one harmonic chunk), 64-thread strips
+// (four CTAs per SM) are taken where the model cost says they finish sooner:
+// small images, whose 128-thread bands are short next to the skew ramp.
+// Measured on a GB300 (forward / fwd+bwd against 128-thread strips): 1024^2
+// r = 3 1.48x / 1.51x, r = 10 1.33x / 1.37x; 16 x 512^2 r = 7 1.22x;
+// 4096^2 r = 3 1.09x; 4096^2 r = 10 0.85x, where the model keeps 128.
+static bool sys_tiles(int H, int W, int ld, int r, const bf_opts* o, Tiles* t, int B = 1,
+                      bool narrow64 = false) {
     int wi = (r <= 40) ? 128 : 256;
-    if (o && o->tile_w > 0) {
+    const bool fixed_w = o && o->tile_w > 0;
+    if (fixed_w) {
         if (o->tile_w > SYS_MAX_THREADS || o->tile_w % 32 != 0) return false;
         wi = o->tile_w;
     }
@@ -130,22 +170,18 @@ static bool sys_tiles(int H, int W, int ld, int r, const bf_opts* o, Tiles* t) {
     // the engine addresses one image with 32-bit element offsets (rows of the
     // skew ramp above and below the image included)
     if ((long long)(H + 2 * wi + 4 * r) * (ld > W ? ld : W) >= 0x7fffffffLL) return false;
-    t->nt = wi;
-    t->Tw = wi - 2 * r;
-    t->gx = (W + t->Tw - 1) / t->Tw;
-    if (o && o->tile_h > 0) {
-        t->Hb = o->tile_h;
-    } else {
-        // one wave of resident CTAs (rounding the band count up would start a
-        // second, nearly empty wave)
-        const int target = (wi <= 128 ? 2 : 1) * sm_count();
-        int nb = target / t->gx;
-        if (nb < 1) nb = 1;
-        int hb = (H + nb - 1) / nb;
-        if (hb < 32) hb = 32;
-        t->Hb = hb;
+    const int slots = (wi <= 64 ? 4 : wi <= 128 ? 2 : 1) * sm_count();
+    const long long cost = band_shape(H, W, r, wi, B, slots, t);
+    const bool fixed_h = o && o->tile_h > 0;
+    if (!fixed_w && !fixed_h && narrow64 && wi == 128 && 64 - 2 * r >= 16) {
+        Tiles t64;
+        const long long c64 = band_shape(H, W, r, 64, B, 4 * sm_count(), &t64);
+        if (100 * c64 < 97 * cost) *t = t64;  // 3 % margin over the model's error
     }
-    t->gy = (H + t->Hb - 1) / t->Hb;
+    if (fixed_h) {
+        t->Hb = o->tile_h;
+        t->gy = (H + t->Hb - 1) / t->Hb;
+    }
     return true;
 }
 
@@ -282,7 +318,8 @@ static bf_status forward_impl(const void* img, int B, int H, int W, int r, float
     cudaError_t e = cudaSuccess;
     // harmonic chunks accumulate in the saved buffers, so chunking needs them
     const int kpm = opts ? opts->kp_max : 0;
-    if (sys_tiles(H, W, p.ld, r, opts, &t) && (sys_chunks(p.K, kahan, kpm) == 1 || saved)) {
+    if (sys_tiles(H, W, p.ld, r, opts, &t, B, first_chunk_path(p.K, p.kstart, p.ld, W, opts, kahan)) &&
+        (sys_chunks(p.K, kahan, kpm) == 1 || saved)) {
         SysParams q;
         fill_sys(p, &q);
         q.out = out;
@@ -312,11 +349,12 @@ struct BwdWs {
     bool chunked;
 };
 
-static bf_status bwd_ws(int B, int H, int W, int r, int K, const bf_opts* opts, BwdWs* ws,
-                        Tiles* t, bool* use_sys) {
+static bf_status bwd_ws(int B, int H, int W, int r, int K, int kstart, const bf_opts* opts,
+                        BwdWs* ws, Tiles* t, bool* use_sys) {
     const int ld = row_pitch(opts ? opts->pitch : 0, W);
     if (ld < 0) return BF_ERR_INVALID_ARG;
-    *use_sys = sys_tiles(H, W, ld, r, opts, t);
+    // the adjoint always runs plain sums
+    *use_sys = sys_tiles(H, W, ld, r, opts, t, B, first_chunk_path(K, kstart, ld, W, opts, false));
     if (!*use_sys) {
         bf_status st = choose_tiles(H, W, r, opts, t);
         if (st != BF_OK) return st;
@@ -338,7 +376,7 @@ static size_t backward_ws_impl(int B, int H, int W, int r, float sigma_r, float 
     BwdWs ws;
     Tiles t;
     bool use_sys = false;
-    if (bwd_ws(B, H, W, r, rs.K, opts, &ws, &t, &use_sys) != BF_OK) return 0;
+    if (bwd_ws(B, H, W, r, rs.K, rs.kstart, opts, &ws, &t, &use_sys) != BF_OK) return 0;
     return ws.total;
 }
 
@@ -362,7 +400,7 @@ static bf_status backward_impl(const void* img, const float* out, const float* g
     Tiles t;
     BwdWs ws;
     bool use_sys = false;
-    st = bwd_ws(B, H, W, r, rs.K, opts, &ws, &t, &use_sys);
+    st = bwd_ws(B, H, W, r, rs.K, rs.kstart, opts, &ws, &t, &use_sys);
     if (st != BF_OK) return st;
     const bool need_ws = ws.chunked || (grad_sigma && gm == BF_GAMMA_FROM_SIGMA);
     if (need_ws && (!workspace || ws_bytes < ws.total)) return BF_ERR_NOMEM;

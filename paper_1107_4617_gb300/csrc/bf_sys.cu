@@ -18,7 +18,8 @@ static int sys_kp(int K) {
     return -1;
 }
 
-// First-chunk kernels of FP32 images on 128-thread strips: odd N (seed 1) runs
+// First-chunk kernels of FP32 images on 128- or 64-thread strips (wi <= 64
+// takes the 64-column instantiations): odd N (seed 1) runs
 // kc harmonics in (kc + 1) / 2 pairs, even N (seed 2) the constant harmonic
 // apart and kc - 1 harmonics in pairs; the last pair is half when the paired
 // count is odd.
@@ -26,18 +27,34 @@ static cudaError_t launch_first(const SysParams& p, int mode, int kc, int seed, 
                                 int gy, cudaStream_t s) {
     const int np = seed == 2 ? kc - 1 : kc;
     const bool half = np & 1;
+    if (wi <= 64) {
+        switch ((np + 1) / 2) {
+            case 1: return sys_first_kp<1, 64>(p, mode, half, seed, wi, gx, gy, s);
+            case 2: return sys_first_kp<2, 64>(p, mode, half, seed, wi, gx, gy, s);
+            case 3: return sys_first_kp<3, 64>(p, mode, half, seed, wi, gx, gy, s);
+            case 4: return sys_first_kp<4, 64>(p, mode, half, seed, wi, gx, gy, s);
+            case 5: return sys_first_kp<5, 64>(p, mode, half, seed, wi, gx, gy, s);
+            case 6: return sys_first_kp<6, 64>(p, mode, half, seed, wi, gx, gy, s);
+            case 7: return sys_first_kp<7, 64>(p, mode, half, seed, wi, gx, gy, s);
+            case 8: return sys_first_kp<8, 64>(p, mode, half, seed, wi, gx, gy, s);
+            case 9: return sys_first_kp<9, 64>(p, mode, half, seed, wi, gx, gy, s);
+            case 10: return sys_first_kp<10, 64>(p, mode, half, seed, wi, gx, gy, s);
+            case 11: return sys_first_kp<11, 64>(p, mode, half, seed, wi, gx, gy, s);
+        }
+        return cudaErrorInvalidValue;
+    }
     switch ((np + 1) / 2) {
-        case 1: return sys_first_kp<1>(p, mode, half, seed, wi, gx, gy, s);
-        case 2: return sys_first_kp<2>(p, mode, half, seed, wi, gx, gy, s);
-        case 3: return sys_first_kp<3>(p, mode, half, seed, wi, gx, gy, s);
-        case 4: return sys_first_kp<4>(p, mode, half, seed, wi, gx, gy, s);
-        case 5: return sys_first_kp<5>(p, mode, half, seed, wi, gx, gy, s);
-        case 6: return sys_first_kp<6>(p, mode, half, seed, wi, gx, gy, s);
-        case 7: return sys_first_kp<7>(p, mode, half, seed, wi, gx, gy, s);
-        case 8: return sys_first_kp<8>(p, mode, half, seed, wi, gx, gy, s);
-        case 9: return sys_first_kp<9>(p, mode, half, seed, wi, gx, gy, s);
-        case 10: return sys_first_kp<10>(p, mode, half, seed, wi, gx, gy, s);
-        case 11: return sys_first_kp<11>(p, mode, half, seed, wi, gx, gy, s);
+        case 1: return sys_first_kp<1, 128>(p, mode, half, seed, wi, gx, gy, s);
+        case 2: return sys_first_kp<2, 128>(p, mode, half, seed, wi, gx, gy, s);
+        case 3: return sys_first_kp<3, 128>(p, mode, half, seed, wi, gx, gy, s);
+        case 4: return sys_first_kp<4, 128>(p, mode, half, seed, wi, gx, gy, s);
+        case 5: return sys_first_kp<5, 128>(p, mode, half, seed, wi, gx, gy, s);
+        case 6: return sys_first_kp<6, 128>(p, mode, half, seed, wi, gx, gy, s);
+        case 7: return sys_first_kp<7, 128>(p, mode, half, seed, wi, gx, gy, s);
+        case 8: return sys_first_kp<8, 128>(p, mode, half, seed, wi, gx, gy, s);
+        case 9: return sys_first_kp<9, 128>(p, mode, half, seed, wi, gx, gy, s);
+        case 10: return sys_first_kp<10, 128>(p, mode, half, seed, wi, gx, gy, s);
+        case 11: return sys_first_kp<11, 128>(p, mode, half, seed, wi, gx, gy, s);
     }
     return cudaErrorInvalidValue;
 }

@@ -1,9 +1,11 @@
 // Engine instantiations for the first (or only) harmonic chunk of a compact
-// FP32 image on 128-thread strips: the seed is specialised at compile time (odd or
-// even N) and every pair count 1..11 has its own kernel, with a half pair for
-// an odd number of harmonics, so no harmonic is computed with a zero
-// coefficient. Each translation unit bf_sys_first*.cu instantiates a few
-// pair counts (they compile in parallel).
+// FP32 image on 128- or 64-thread strips: the seed is specialised at compile
+// time (odd or even N) and every pair count 1..11 has its own kernel, with a
+// half pair for an odd number of harmonics, so no harmonic is computed with a
+// zero coefficient. Each translation unit bf_sys_first*.cu instantiates a few
+// pair counts for one strip width (they compile in parallel). 64-thread strips
+// (shared memory for 64 columns, four CTAs per SM) serve small images, whose
+// 128-thread tiles would spend most steps in the skew ramp.
 #pragma once
 #include "bf_sys_engine.cuh"
 
@@ -17,7 +19,8 @@ namespace bf {
 // instruction schedule, and the fastest one differs between instantiations
 // by up to 1.9x. Each entry is the fastest of the four on a GB300 at
 // 4096^2, r = 10 (median of 12 launches with L2 flushed, every N = 2..43;
-// form 0 is kept unless another is at least 2 % faster).
+// form 0 is kept unless another is at least 2 % faster), on 128-thread
+// strips; the 64-thread kernels take the same forms.
 constexpr unsigned char kFirstForm[3][2][11][2] = {
     // plain forward
     {
@@ -36,7 +39,7 @@ constexpr unsigned char kFirstForm[3][2][11][2] = {
     },
 };
 
-template <int KP, bool HALF, int SEED>
+template <int KP, bool HALF, int SEED, int WMAX>
 cudaError_t sys_first_modes(const SysParams& p, int mode, int wi, int gx, int gy,
                             cudaStream_t s) {
     constexpr int F0 = kFirstForm[0][SEED - 1][KP - 1][HALF];
@@ -44,23 +47,23 @@ cudaError_t sys_first_modes(const SysParams& p, int mode, int wi, int gx, int gy
     constexpr int F2 = kFirstForm[2][SEED - 1][KP - 1][HALF];
     // compact images only (p.ld == W): the pitch terms are compiled out
     if (mode == 2)
-        return sys_launch_one<KP, true, false, false, 128, float, HALF, SEED, F2, false>(p, wi, gx,
+        return sys_launch_one<KP, true, false, false, WMAX, float, HALF, SEED, F2, false>(p, wi, gx,
                                                                                     gy, s);
     if (mode == 1)
-        return sys_launch_one<KP, false, true, false, 128, float, HALF, SEED, F1, false>(p, wi, gx,
+        return sys_launch_one<KP, false, true, false, WMAX, float, HALF, SEED, F1, false>(p, wi, gx,
                                                                                     gy, s);
-    return sys_launch_one<KP, false, false, false, 128, float, HALF, SEED, F0, false>(p, wi, gx, gy,
+    return sys_launch_one<KP, false, false, false, WMAX, float, HALF, SEED, F0, false>(p, wi, gx, gy,
                                                                                      s);
 }
 
-template <int KP>
+template <int KP, int WMAX>
 cudaError_t sys_first_kp(const SysParams& p, int mode, bool half, int seed, int wi, int gx,
                          int gy, cudaStream_t s) {
     if (seed == 1)
-        return half ? sys_first_modes<KP, true, 1>(p, mode, wi, gx, gy, s)
-                    : sys_first_modes<KP, false, 1>(p, mode, wi, gx, gy, s);
-    return half ? sys_first_modes<KP, true, 2>(p, mode, wi, gx, gy, s)
-                : sys_first_modes<KP, false, 2>(p, mode, wi, gx, gy, s);
+        return half ? sys_first_modes<KP, true, 1, WMAX>(p, mode, wi, gx, gy, s)
+                    : sys_first_modes<KP, false, 1, WMAX>(p, mode, wi, gx, gy, s);
+    return half ? sys_first_modes<KP, true, 2, WMAX>(p, mode, wi, gx, gy, s)
+                : sys_first_modes<KP, false, 2, WMAX>(p, mode, wi, gx, gy, s);
 }
 
 }  // namespace bf

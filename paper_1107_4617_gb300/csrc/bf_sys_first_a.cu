@@ -1,10 +1,15 @@
-// First-chunk engine instantiations (see bf_sys_first.cuh): pair counts 1 2 3 4 5.
+// First-chunk engine instantiations (see bf_sys_first.cuh), 128-thread strips: pair counts 1 2 3 4 5.
 #include "bf_sys_first.cuh"
 
 namespace bf {
-template cudaError_t sys_first_kp<1>(const SysParams&, int, bool, int, int, int, int, cudaStream_t);
-template cudaError_t sys_first_kp<2>(const SysParams&, int, bool, int, int, int, int, cudaStream_t);
-template cudaError_t sys_first_kp<3>(const SysParams&, int, bool, int, int, int, int, cudaStream_t);
-template cudaError_t sys_first_kp<4>(const SysParams&, int, bool, int, int, int, int, cudaStream_t);
-template cudaError_t sys_first_kp<5>(const SysParams&, int, bool, int, int, int, int, cudaStream_t);
+template cudaError_t sys_first_kp<1, 128>(const SysParams&, int, bool, int, int, int, int,
+                                          cudaStream_t);
+template cudaError_t sys_first_kp<2, 128>(const SysParams&, int, bool, int, int, int, int,
+                                          cudaStream_t);
+template cudaError_t sys_first_kp<3, 128>(const SysParams&, int, bool, int, int, int, int,
+                                          cudaStream_t);
+template cudaError_t sys_first_kp<4, 128>(const SysParams&, int, bool, int, int, int, int,
+                                          cudaStream_t);
+template cudaError_t sys_first_kp<5, 128>(const SysParams&, int, bool, int, int, int, int,
+                                          cudaStream_t);
 }  // namespace bf

@@ -1,7 +1,9 @@
-// First-chunk engine instantiations (see bf_sys_first.cuh): pair counts 6 7.
+// First-chunk engine instantiations (see bf_sys_first.cuh), 128-thread strips: pair counts 6 7.
 #include "bf_sys_first.cuh"
 
 namespace bf {
-template cudaError_t sys_first_kp<6>(const SysParams&, int, bool, int, int, int, int, cudaStream_t);
-template cudaError_t sys_first_kp<7>(const SysParams&, int, bool, int, int, int, int, cudaStream_t);
+template cudaError_t sys_first_kp<6, 128>(const SysParams&, int, bool, int, int, int, int,
+                                          cudaStream_t);
+template cudaError_t sys_first_kp<7, 128>(const SysParams&, int, bool, int, int, int, int,
+                                          cudaStream_t);
 }  // namespace bf

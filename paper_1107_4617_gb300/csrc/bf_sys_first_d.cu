@@ -1,6 +1,7 @@
-// First-chunk engine instantiations (see bf_sys_first.cuh): pair counts 10.
+// First-chunk engine instantiations (see bf_sys_first.cuh), 128-thread strips: pair counts 10.
 #include "bf_sys_first.cuh"
 
 namespace bf {
-template cudaError_t sys_first_kp<10>(const SysParams&, int, bool, int, int, int, int, cudaStream_t);
+template cudaError_t sys_first_kp<10, 128>(const SysParams&, int, bool, int, int, int, int,
+                                          cudaStream_t);
 }  // namespace bf

@@ -69,6 +69,60 @@ def test_grad_sigma_from_sigma(cuda_lib, sigma, r):
     assert abs(float(s.grad) - dsig_ref) <= GTOL * max(1.0, abs(dsig_ref)), (float(s.grad), dsig_ref)
 
 
+def test_adjoint_range_shift_invariance(cuda_lib):
+    """The engine runs on f - T/2 and out - T/2 (the saved quads hold the
+    shifted values). Shifting the input by a constant inside [0, T] must then
+    shift out by the same constant and leave dL/df and dL/dsigma_r unchanged,
+    as the oracle's pins fix; both runs are also checked against the oracle."""
+    bf = cuda_lib
+    H, W, r, sigma = 80, 150, 6, 0.15
+    f = 0.75 * synth.rectangles(H, W, seed=31)
+    w = synth.weights((H, W), seed=3)
+    N = oracle.resolve_N(sigma, 1.0)
+    g = oracle.gamma_from_sigma(sigma, N)
+    res = []
+    for c in (0.0, 0.25):
+        fc = (f + np.float32(c)).astype(np.float32)
+        ft = torch.from_numpy(fc).cuda().requires_grad_(True)
+        s = torch.tensor(sigma, requires_grad=True)
+        out = bf.bilateral(ft, r, s, 1.0, N=N, gamma_mode=bf.GAMMA_FROM_SIGMA)
+        (torch.from_numpy(w).cuda() * out).sum().backward()
+        gref, dgam = oracle.bilateral_grad(fc.astype(np.float64), w.astype(np.float64), r, g, N)
+        check_grad(ft.grad.cpu().numpy(), gref)
+        dsig = -(g / sigma) * dgam
+        assert abs(float(s.grad) - dsig) <= 3e-4 * max(1.0, abs(dsig)), (c, float(s.grad), dsig)
+        res.append((out.detach().cpu().numpy().astype(np.float64), ft.grad.cpu().numpy(),
+                    float(s.grad)))
+    (o0, g0, s0), (o1, g1, s1) = res
+    assert np.abs(o1 - 0.25 - o0).max() <= 1e-4
+    assert np.abs(g1 - g0).max() <= GTOL * np.abs(g0).max()
+    assert abs(s1 - s0) <= 3e-4 * max(1.0, abs(s0)), (s0, s1)
+
+
+@pytest.mark.parametrize("H,W,r,sigma", [(160, 230, 10, 0.1), (120, 333, 24, 0.2)])
+def test_adjoint_narrow_strips(cuda_lib, H, W, r, sigma):
+    """The adjoint on 64-thread strips (small images): dL/df against the
+    oracle's direct-form gradient, and against explicit 128-thread strips."""
+    bf = cuda_lib
+    f = synth.rectangles(H, W, seed=H + W + r)
+    w = synth.weights((H, W), seed=5)
+    N = oracle.resolve_N(sigma, 1.0)
+    ft = torch.from_numpy(f).cuda()
+    wt = torch.from_numpy(w).cuda()
+    res = []
+    for tw in (0, 128):
+        o = bf._opts(save=True, tile_w=tw)
+        sv = torch.empty((H, W, 4), device="cuda")
+        out = bf.bf_forward(ft, r, sigma, 1.0, N, opts=o, saved=sv)
+        gi = torch.empty_like(ft)
+        bf.bf_backward(ft, out, wt, sv, r, sigma, 1.0, N, grad_img=gi, opts=o)
+        torch.cuda.synchronize()
+        res.append(gi.cpu().numpy())
+    gref, _ = oracle.bilateral_grad(f.astype(np.float64), w.astype(np.float64), r, math.pi / 2, N)
+    check_grad(res[0], gref)
+    assert np.abs(res[0] - res[1]).max() <= 1e-4 * np.abs(gref).max()
+
+
 def test_grad_batch_differentiation_config(cuda_lib):
     """Differentiation workload shape: a batch of 512x512 images, r=7,
     sigma_r=0.15 (N=19); image gradient checked on 2 images against the

@@ -41,7 +41,7 @@ def run_fwd(bf, img_np, r, sigma_r=0.2, T=1.0, N=0, kahan=False, dtype=torch.flo
         b = buf.cpu().numpy()
         assert np.all(b[:guard] == 12345.0) and np.all(b[guard + H * W:] == 12345.0), "guard band written"
     res = out.cpu().numpy()
-    # saved quads as planes: (f, 1/den, out, dnum_s - out dden_s)
+    # saved quads as planes: (f - T/2, 1/den, out - T/2, dnum_s - out dden_s)
     return (res, np.moveaxis(sv.cpu().numpy(), 2, 0)) if saved else res
 
 
@@ -336,3 +336,28 @@ def test_check_range(cuda_lib, H, W):
     mb = bf.bf_check_range(tb).cpu().numpy()
     fb = tb.float().cpu().numpy()
     assert mb[0] == fb.min() and mb[1] == fb.max()
+
+
+@pytest.mark.parametrize("H,W,r,sigma,N", [(300, 500, 10, 0.1, 40), (257, 390, 3, 0.1, 41),
+                                           (200, 333, 24, 0.2, 11), (1024, 1024, 3, 0.1, 41)])
+def test_narrow_strips_on_small_images(cuda_lib, H, W, r, sigma, N):
+    """Small images take 64-thread strips (four CTAs per SM) where the launch
+    model says they finish sooner; r = 24 is the widest window they hold
+    (64 - 2r = 16 output columns). The default launch against the oracle
+    (whole image, or 2000 sampled pixels at 1024^2) and against explicit
+    128-thread strips, with and without the saved quads."""
+    f = synth.rectangles(H, W, seed=H + r)
+    got, sv = run_fwd(cuda_lib, f, r, sigma, 1.0, N, saved=True)
+    wide, sv_w = run_fwd(cuda_lib, f, r, sigma, 1.0, N, saved=True, tile_w=128)
+    plain = run_fwd(cuda_lib, f, r, sigma, 1.0, N)
+    if H * W <= 200000:
+        ref, den = oracle_ref(f, r, sigma, 1.0, N)
+        assert rel_err(got, ref).max() <= TOL
+        np.testing.assert_allclose(1.0 / sv[1], den, rtol=2e-5, atol=0)
+    else:
+        idx = np.random.default_rng(H).integers(0, H * W, 2000)
+        ref = oracle.bilateral_points(f.astype(np.float64), r, math.pi / 2, N, idx)
+        assert rel_err(got.ravel()[idx], ref).max() <= TOL
+    assert np.abs(got - wide).max() <= 1e-5
+    assert np.abs(plain - got).max() <= 1e-5
+    np.testing.assert_array_equal(sv[0], sv_w[0])

@@ -182,6 +182,21 @@ def test_gradient_vs_central_differences(N):
     assert abs(fd - gg) <= 1e-7 * max(1.0, abs(fd)), (fd, gg)
 
 
+@pytest.mark.parametrize("N", [4, 11])
+def test_gradient_range_shift_invariance(N):
+    """out(f + c) = out(f) + c (the weights depend on differences of f only),
+    so L(f + c) = L(f) + c sum(g): dL/df and dL/dgamma do not change when the
+    whole range moves by a constant. The GPU engine relies on this when it
+    runs on f - T/2."""
+    rng = np.random.default_rng(20 + N)
+    f = 0.7 * rng.uniform(0, 1, (12, 15))
+    g = rng.normal(0, 1, f.shape)
+    gf, gg = oracle.bilateral_grad(f, g, 3, GAMMA1, N)
+    gf2, gg2 = oracle.bilateral_grad(f + 0.3, g, 3, GAMMA1, N)
+    np.testing.assert_allclose(gf2, gf, rtol=0, atol=1e-12 * np.abs(gf).max())
+    assert abs(gg2 - gg) <= 1e-11 * max(1.0, abs(gg)), (gg, gg2)
+
+
 def test_gradient_N0_closed_form():
     """N = 0 is the linear box mean, whose adjoint is Box[g / count]."""
     rng = np.random.default_rng(3)
