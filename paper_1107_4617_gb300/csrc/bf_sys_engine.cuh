@@ -265,6 +265,9 @@ __device__ __forceinline__ void sys_tile(const SysParams& p, int bx, int by, siz
     // and pair i holds harmonics 4i + 2, 4i + 4, i.e. coefficients CO + 2i.
     constexpr bool DC = SEED == 2;
     constexpr int CO = DC ? 1 : 0;
+    // FORM: bits 0-1 the step-body form, bit 2 the ping-pong step loop
+    constexpr int BODY = FORM & 3;
+    constexpr bool PINGPONG = (FORM & 4) != 0;
     constexpr int LD = WMAX + 1;          // row of one plane in shared memory
     constexpr int BUF = (2 * KP + (DC ? 1 : 0)) * LD;  // one step-parity buffer
     const int Wi = blockDim.x;
@@ -335,33 +338,40 @@ __device__ __forceinline__ void sys_tile(const SysParams& p, int bx, int by, siz
     };
 
     // pixel values of the current step, loaded during the previous one
-    Px<BWD> v0, v1, v2, v3, vc;
+    Px<BWD> vA[5], vB[5];
     // a warp is first active at step 32 w; start its prefetch chain there
-    Geo g = geometry(w * 32);
+    Geo gA = geometry(w * 32), gB = gA;
     // the adjoint's dL/dout offsets: the quads' offsets plus the pitched rows'
     // extra elements (entering row e, leaving row e - 2r - 1, centre row e - r)
-    auto load_step = [&](const Geo& gg, int t) {
+    auto load_step = [&](const Geo& gg, int t, Px<BWD> (&v)[5]) {
         int de = 0, dl = 0, dc = 0;
         if constexpr (BWD) {
             de = (e0 + t) * dld;
             dl = de - (2 * r + 1) * dld;
             dc = de - r * dld;
         }
-        load_px<BWD, Tin>(v0, b, gg.m0, gg.q0, gg.q0 + de);
-        load_px<BWD, Tin>(v1, b, gg.m1, gg.q1, gg.q1 + de);
-        load_px<BWD, Tin>(v2, b, gg.m2, gg.q2, gg.q2 + dl);
-        load_px<BWD, Tin>(v3, b, gg.m3, gg.q3, gg.q3 + dl);
-        load_px<BWD, Tin>(vc, b, gg.out, gg.qo, gg.qo + dc);
+        load_px<BWD, Tin>(v[0], b, gg.m0, gg.q0, gg.q0 + de);
+        load_px<BWD, Tin>(v[1], b, gg.m1, gg.q1, gg.q1 + de);
+        load_px<BWD, Tin>(v[2], b, gg.m2, gg.q2, gg.q2 + dl);
+        load_px<BWD, Tin>(v[3], b, gg.m3, gg.q3, gg.q3 + dl);
+        load_px<BWD, Tin>(v[4], b, gg.out, gg.qo, gg.qo + dc);
     };
-    load_step(g, w * 32);
+    load_step(gA, w * 32, vA);
     __syncthreads();
 
-    for (int t = 0; t < steps; ++t) {
+    // One step t: its pixels (cur, loaded during step t - 1) are copied out
+    // first, then step t + 1's loads are issued into nxt. The plain loop
+    // passes one register set as both; the ping-pong loop alternates two sets
+    // over pairs of steps, so no copy is made between steps. The two loops
+    // compute the same sums; which schedules better differs between
+    // instantiations.
+    auto step = [&](int t, const Geo& gcur, const Px<BWD> (&cur)[5], Geo& gnext,
+                    Px<BWD> (&nxt)[5]) {
         const int warp_first = t - (w * 32 + 31);
         const int warp_last = t - w * 32;
         if (warp_last >= 0 && warp_first < span) {
-            const Geo gc = g;  // geometry of this step
-            const Px<BWD> c0 = v0, c1 = v1, c2v = v2, c3 = v3, cc = vc;
+            const Geo gc = gcur;  // geometry of this step
+            const Px<BWD> c0 = cur[0], c1 = cur[1], c2v = cur[2], c3 = cur[3], cc = cur[4];
             // pull the entering row of a later step into L2 (no registers held;
             // only rows that enter this band's window, so nothing past the
             // band is fetched): the other four streams re-read pixels the
@@ -378,8 +388,8 @@ __device__ __forceinline__ void sys_tile(const SysParams& p, int bx, int by, siz
                 }
             }
             // prefetch the next step's pixels; their latency hides under this step
-            g = geometry(t + 1);
-            load_step(g, t + 1);
+            gnext = geometry(t + 1);
+            load_step(gnext, t + 1, nxt);
 
             // plane weights (u: first two planes, v: last two) with the stream's
             // sign: + own enter, - second enter, - own leave, + second leave;
@@ -449,7 +459,7 @@ __device__ __forceinline__ void sys_tile(const SysParams& p, int bx, int by, siz
                     DEN.x = fmaf(ak, fmaf(FC.x, pp, qq), DEN.x);
                 }
             };
-            if constexpr (!KAHAN && FORM != 1) {
+            if constexpr (!KAHAN && BODY != 1) {
                 // the vertical running sums one stream at a time (only that
                 // stream's recurrence is live, and its harmonic pairs update
                 // independent sums), then the horizontal step and the centre
@@ -492,7 +502,7 @@ __device__ __forceinline__ void sys_tile(const SysParams& p, int bx, int by, siz
                 // FORM 2 / 3: the left neighbour's sums of pair i + PF are loaded
                 // before this lane stores pair i (the two step-parity buffers
                 // never overlap), so the loads stay in flight across the stores
-                constexpr int PF = FORM == 2 ? 2 : (FORM == 3 ? 1 : 0);
+                constexpr int PF = BODY == 2 ? 2 : (BODY == 3 ? 1 : 0);
                 float4 PA[KP], PB[KP];
 #pragma unroll
                 for (int i = 0; i < PF && i < KP; ++i) {
@@ -525,7 +535,7 @@ __device__ __forceinline__ void sys_tile(const SysParams& p, int bx, int by, siz
                     }
                     if (i + 1 < KP) advance(sc, i, i + 2 < KP, HALF && i + 2 == KP - 1);
                 }
-            } else if constexpr (FORM == 1) {
+            } else if constexpr (BODY == 1) {
                 // all five streams advance together, pair by pair: the four
                 // streams' updates of pair i sit between the load of the left
                 // neighbour's sums of pair i and their use
@@ -703,6 +713,16 @@ __device__ __forceinline__ void sys_tile(const SysParams& p, int bx, int by, siz
             }
         }
         __syncthreads();
+    };
+    if constexpr (PINGPONG) {
+        int t = 0;
+        for (; t + 1 < steps; t += 2) {
+            step(t, gA, vA, gB, vB);
+            step(t + 1, gB, vB, gA, vA);
+        }
+        if (t < steps) step(t, gA, vA, gB, vB);
+    } else {
+        for (int t = 0; t < steps; ++t) step(t, gA, vA, gA, vA);
     }
 }
 

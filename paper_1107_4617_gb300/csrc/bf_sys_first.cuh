@@ -11,31 +11,33 @@
 
 namespace bf {
 
-// Form of the step body per launch mode, seed (odd / even N), pair count and
-// half pair: 0 = the four vertical streams one after another, then the
-// centre; 1 = all five streams pair by pair; 2 / 3 = form 0 with the left
-// neighbour's sums loaded two / one pair ahead of this lane's stores. The
-// forms compute the same sums in the same order; they differ only in
-// instruction schedule, and the fastest one differs between instantiations
-// by up to 1.9x. Each entry is the fastest of the four on a GB300 at
-// 4096^2, r = 10 (median of 12 launches with L2 flushed, every N = 2..43;
-// form 0 is kept unless another is at least 2 % faster), on 128-thread
-// strips; the 64-thread kernels take the same forms.
+// Form of the step per launch mode, seed (odd / even N), pair count and half
+// pair. Bits 0-1, the step body: 0 = the four vertical streams one after
+// another, then the centre; 1 = all five streams pair by pair; 2 / 3 = form
+// 0 with the left neighbour's sums loaded two / one pair ahead of this
+// lane's stores. Bit 2: the ping-pong step loop (two register sets for the
+// pixels of consecutive steps, no copies between steps). The forms compute
+// the same sums in the same order; they differ only in instruction schedule,
+// and the fastest one differs between instantiations by up to 1.9x. Each
+// entry is the fastest of the eight on a GB300 at 4096^2, r = 10 (median of
+// 12 launches with L2 flushed, every N = 2..43; the previous entry is kept
+// unless another is at least 2 % faster), on 128-thread strips; the
+// 64-thread kernels take the same forms.
 constexpr unsigned char kFirstForm[3][2][11][2] = {
     // plain forward
     {
-        {{0, 0}, {0, 2}, {0, 2}, {0, 0}, {0, 0}, {2, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}},
-        {{0, 0}, {2, 0}, {0, 0}, {0, 1}, {1, 3}, {0, 0}, {0, 0}, {0, 0}, {0, 1}, {0, 0}, {0, 0}},
+        {{6, 0}, {6, 5}, {6, 5}, {5, 5}, {0, 5}, {4, 4}, {0, 5}, {0, 5}, {0, 0}, {0, 0}, {0, 0}},
+        {{5, 6}, {5, 6}, {6, 5}, {4, 5}, {5, 5}, {2, 5}, {0, 6}, {0, 0}, {1, 1}, {0, 0}, {0, 0}},
     },
     // forward with saved quads
     {
-        {{3, 0}, {3, 3}, {0, 3}, {0, 3}, {0, 3}, {1, 1}, {0, 0}, {0, 0}, {0, 0}, {1, 0}, {0, 0}},
-        {{3, 3}, {0, 3}, {1, 0}, {3, 1}, {0, 3}, {1, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}},
+        {{5, 0}, {5, 6}, {5, 5}, {0, 5}, {0, 5}, {1, 4}, {0, 0}, {1, 0}, {1, 0}, {1, 1}, {0, 0}},
+        {{5, 5}, {5, 4}, {5, 5}, {3, 5}, {2, 5}, {1, 0}, {0, 5}, {0, 0}, {0, 0}, {0, 0}, {0, 0}},
     },
     // adjoint
     {
-        {{0, 0}, {3, 0}, {0, 2}, {2, 2}, {2, 2}, {2, 2}, {0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}},
-        {{0, 0}, {0, 0}, {2, 0}, {3, 0}, {2, 2}, {0, 0}, {0, 0}, {1, 0}, {0, 0}, {0, 0}, {0, 1}},
+        {{0, 0}, {6, 6}, {0, 6}, {6, 6}, {6, 5}, {4, 5}, {0, 6}, {0, 6}, {0, 0}, {0, 0}, {0, 0}},
+        {{0, 6}, {6, 5}, {2, 6}, {5, 6}, {5, 2}, {0, 6}, {0, 6}, {1, 0}, {0, 0}, {0, 0}, {0, 1}},
     },
 };
 
