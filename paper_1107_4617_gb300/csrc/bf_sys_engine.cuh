@@ -179,7 +179,7 @@ __device__ __forceinline__ void advance(Strm& q, int i, bool need, bool half = f
 }
 
 // Rows ahead of the current entering row that are pulled into L2.
-constexpr int PREFETCH_ROWS = 8;
+constexpr int PREFETCH_ROWS = 4;
 
 template <typename T>
 __device__ __forceinline__ void prefetch_l2(const T* ptr) {
@@ -265,9 +265,12 @@ __device__ __forceinline__ void sys_tile(const SysParams& p, int bx, int by, siz
     // and pair i holds harmonics 4i + 2, 4i + 4, i.e. coefficients CO + 2i.
     constexpr bool DC = SEED == 2;
     constexpr int CO = DC ? 1 : 0;
-    // FORM: bits 0-1 the step-body form, bit 2 the ping-pong step loop
+    // FORM: bits 0-1 the step-body form, bit 2 the ping-pong step loop, bit 3
+    // the combine's sine terms negated on the box sums instead of on the
+    // centre's harmonics
     constexpr int BODY = FORM & 3;
     constexpr bool PINGPONG = (FORM & 4) != 0;
+    constexpr bool NEGFOLD = (FORM & 8) != 0;
     constexpr int LD = WMAX + 1;          // row of one plane in shared memory
     constexpr int BUF = (2 * KP + (DC ? 1 : 0)) * LD;  // one step-parity buffer
     const int Wi = blockDim.x;
@@ -425,19 +428,29 @@ __device__ __forceinline__ void sys_tile(const SysParams& p, int bx, int by, siz
                                float2 hw) {
                 const float2 A2 = make_float2(p.a[CO + 2 * i], p.a[CO + 2 * i + 1]);
                 const float2 AK2 = make_float2(p.ak[CO + 2 * i], p.ak[CO + 2 * i + 1]);
+                // -S_k h: the negation on the centre's sines (one product per
+                // pair) or on the box sums (folded into the products)
                 const float2 nzs = __fmul2_rn(sc.s, dup(-1.f));
+                auto msh = [&](float2 h) {
+                    if constexpr (NEGFOLD) return __fmul2_rn(sc.s, make_float2(-h.x, -h.y));
+                    else return __fmul2_rn(nzs, h);
+                };
+                auto hms = [&](float2 h) {  // the same, operands in the adjoint's order
+                    if constexpr (NEGFOLD) return __fmul2_rn(make_float2(-h.x, -h.y), sc.s);
+                    else return __fmul2_rn(h, nzs);
+                };
                 if constexpr (!BWD) {
                     NUM = __ffma2_rn(A2, __ffma2_rn(sc.c, hx, __fmul2_rn(sc.s, hy)), NUM);
                     DEN = __ffma2_rn(A2, __ffma2_rn(sc.c, hz, __fmul2_rn(sc.s, hw)), DEN);
                     if constexpr (SAVE) {
-                        DNUM = __ffma2_rn(AK2, __ffma2_rn(sc.c, hy, __fmul2_rn(nzs, hx)), DNUM);
-                        DDEN = __ffma2_rn(AK2, __ffma2_rn(sc.c, hw, __fmul2_rn(nzs, hz)), DDEN);
+                        DNUM = __ffma2_rn(AK2, __ffma2_rn(sc.c, hy, msh(hx)), DNUM);
+                        DDEN = __ffma2_rn(AK2, __ffma2_rn(sc.c, hw, msh(hz)), DDEN);
                     }
                 } else {
                     // h = (Box[alpha C], Box[alpha S], Box[beta C], Box[beta S])
                     NUM = __ffma2_rn(A2, __ffma2_rn(hx, sc.c, __fmul2_rn(hy, sc.s)), NUM);
-                    const float2 pp = __ffma2_rn(hy, sc.c, __fmul2_rn(hx, nzs));
-                    const float2 qq = __ffma2_rn(hw, sc.c, __fmul2_rn(hz, nzs));
+                    const float2 pp = __ffma2_rn(hy, sc.c, hms(hx));
+                    const float2 qq = __ffma2_rn(hw, sc.c, hms(hz));
                     DEN = __ffma2_rn(AK2, __ffma2_rn(FC, pp, qq), DEN);
                 }
             };
