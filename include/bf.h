@@ -356,11 +356,15 @@ bf_status bf_poly_backward(const float* grad_out, const void* saved, int H, int 
 size_t bf_batch_workspace_bytes(const bf_desc* descs, int n, const bf_opts* opts);
 
 /*
- * Filters n images of uneven sizes, each with its own r, sigma_r, N, in ONE
- * persistent launch: CTAs pull tiles from a device work counter over a tile
- * table held in `workspace`. descs is a HOST array; each image is validated
- * like bf_forward. Equivalent to bf_batch_prepare followed by
- * bf_batch_launch.
+ * Filters n images of uneven sizes, each with its own r, sigma_r, N, in
+ * persistent launches: CTAs pull tiles from device work counters over a tile
+ * table held in `workspace`. The images are grouped by kernel (three groups:
+ * 128-thread strips whose harmonics fit one chunk of at most 4 pairs, which
+ * run the compile-time-specialised kernels at three CTAs per SM; the other
+ * 128-thread strips; 256-thread strips for r > 40), one launch per group.
+ * descs is a HOST array; each image is validated like bf_forward;
+ * opts->tile_w, if set, must be 128 or 256 (else BF_ERR_UNSUPPORTED).
+ * Equivalent to bf_batch_prepare followed by bf_batch_launch.
  */
 bf_status bf_batch(const bf_desc* descs, int n, const bf_opts* opts, void* workspace,
                    size_t ws_bytes, void* stream);
@@ -370,9 +374,10 @@ bf_status bf_batch(const bf_desc* descs, int n, const bf_opts* opts, void* works
 bf_status bf_batch_prepare(const bf_desc* descs, int n, const bf_opts* opts, void* workspace,
                            size_t ws_bytes, void* stream);
 
-/* Launches the persistent batch kernel over a table bf_batch_prepare wrote
-   into workspace: a memset of the work counter and one kernel, nothing
-   else, so it can be captured into a CUDA graph and replayed. opts must
+/* Launches the persistent batch kernels over a table bf_batch_prepare wrote
+   into workspace: a memset of the work counters and one kernel per group
+   (the Kahan path: one kernel), nothing else, so it can be captured into a
+   CUDA graph and replayed. opts must
    carry the same kahan / in_dtype as the prepare call. On the plain (non-
    Kahan) path a table without the tag bf_batch_prepare writes (a workspace
    never prepared, or overwritten) launches no work: outputs stay untouched. */

@@ -46,10 +46,15 @@ static size_t sys_table_bytes(int n) {
 }
 
 // Strip width of an image on the skewed-strip engine (same rule as a single
-// image), or 0 when the strip would keep fewer than 16 output columns.
+// image), or 0 when the strip would keep fewer than 16 output columns. The
+// persistent launches run 128- or 256-thread CTAs, so a batch takes only
+// those two widths.
 static int sys_width(int r, const bf_opts* o) {
     int wi = (r <= 40) ? 128 : 256;
-    if (o && o->tile_w > 0) wi = o->tile_w;
+    if (o && o->tile_w > 0) {
+        if (o->tile_w != 128 && o->tile_w != 256) return 0;
+        wi = o->tile_w;
+    }
     if (wi % 32 != 0 || wi > SYS_MAX_THREADS || wi - 2 * r < 16) return 0;
     return wi;
 }
@@ -57,6 +62,8 @@ static int sys_width(int r, const bf_opts* o) {
 struct Plan {
     FwdParams p;
     int wi, gx, gy, Hb, nch;
+    int group;  // persistent launch (SysBatchTable::g)
+    int kind;   // its specialised kernel within the group, or -1
     long long cost;
 };
 
@@ -82,6 +89,9 @@ static bf_status plan_image(const bf_desc& d, const bf_opts* opts, Plan* pl) {
     pl->gy = (d.H + pl->Hb - 1) / pl->Hb;
     pl->nch = sys_chunks(pl->p.K, false, 0);
     if (pl->nch > SYS_BATCH_MAX_CHUNKS) return BF_ERR_UNSUPPORTED;
+    int kg = 1;
+    pl->kind = (pl->wi <= 128 && pl->nch == 1) ? sys_batch_kind(pl->p.K, pl->p.kstart, &kg) : -1;
+    pl->group = pl->wi > 128 ? 2 : (pl->kind >= 0 ? kg : 1);
     pl->cost = (long long)(pl->Hb + 2 * d.r + pl->wi) * (pl->p.K + 2);
     return BF_OK;
 }
@@ -178,13 +188,12 @@ bf_status bf_batch_prepare(const bf_desc* descs, int n, const bf_opts* opts, voi
     if (st != BF_OK) return st;
     if (ws_bytes < total) return BF_ERR_NOMEM;
 
-    // group 0: 128-thread strips, group 1: 256-thread strips; within a group
-    // the most expensive tiles first
+    // groups in order (SysBatchTable::g); within a group the most expensive
+    // tiles first
     std::vector<int> order((size_t)n);
     for (int i = 0; i < n; ++i) order[i] = i;
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
-        const int ga = plans[a].wi > 128, gb = plans[b].wi > 128;
-        if (ga != gb) return ga < gb;
+        if (plans[a].group != plans[b].group) return plans[a].group < plans[b].group;
         return plans[a].cost > plans[b].cost;
     });
     const size_t tbytes = sys_table_bytes(n);
@@ -194,13 +203,14 @@ bf_status bf_batch_prepare(const bf_desc* descs, int n, const bf_opts* opts, voi
     tab->in_dtype = opts ? opts->in_dtype : BF_F32;
     char* acc_base = static_cast<char*>(workspace) + align256(tbytes);
     size_t acc_off = 0;
-    long long tiles[2] = {0, 0};
-    int count[2] = {0, 0};
+    long long tiles[SYS_BATCH_GROUPS] = {};
+    int count[SYS_BATCH_GROUPS] = {};
     for (int k = 0; k < n; ++k) {
         const int i = order[k];
         const Plan& pl = plans[i];
-        const int grp = pl.wi > 128;
+        const int grp = pl.group;
         SysBatchImage& im = tab->img[k];
+        im.kind = pl.kind;
         im.nch = pl.nch;
         im.gx = pl.gx;
         im.n_tiles = pl.gx * pl.gy;
@@ -244,10 +254,10 @@ bf_status bf_batch_prepare(const bf_desc* descs, int n, const bf_opts* opts, voi
             im.kp[c] = kp <= 4 ? kp : (kp <= 6 ? 6 : (kp <= 8 ? 8 : SYS_KP_MAX));
         }
     }
-    for (int grp = 0; grp < 2; ++grp) {
+    for (int grp = 0; grp < SYS_BATCH_GROUPS; ++grp) {
         tab->g[grp].n_tiles = (int)tiles[grp];
         tab->g[grp].n_images = count[grp];
-        tab->g[grp].wi = grp ? 256 : 128;
+        tab->g[grp].wi = grp == 2 ? 256 : 128;
     }
     cudaError_t e = cudaMemcpyAsync(workspace, host.data(), tbytes, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return set_cuda_error(e);
@@ -273,9 +283,10 @@ bf_status bf_batch_launch(void* workspace, size_t ws_bytes, const bf_opts* opts,
     SysBatchTable* tab = static_cast<SysBatchTable*>(workspace);
     const int dtype = opts ? opts->in_dtype : BF_F32;
     e = cudaMemsetAsync(tab->counters, 0, sizeof(tab->counters), s);
-    // a group with no tiles exits at its first pop
-    if (e == cudaSuccess) e = launch_sys_batch(tab, 0, 128, 2 * sm_count(), dtype, s);
-    if (e == cudaSuccess) e = launch_sys_batch(tab, 1, 256, sm_count(), dtype, s);
+    // one persistent launch per group, each with its resident CTAs; a group
+    // with no tiles exits at its first pop
+    for (int grp = 0; grp < SYS_BATCH_GROUPS && e == cudaSuccess; ++grp)
+        e = launch_sys_batch(tab, grp, sys_batch_grid(grp, dtype), dtype, s);
     if (e != cudaSuccess) return set_cuda_error(e);
     return BF_OK;
 }

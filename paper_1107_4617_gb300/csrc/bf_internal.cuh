@@ -130,6 +130,7 @@ struct SysBatchImage {
     int gx;
     int first_tile;
     int n_tiles;
+    int kind;   // index of its specialised kernel (sys_batch_kind), or -1
 };
 
 // Work of one persistent launch (one strip width): image range and tiles.
@@ -140,16 +141,29 @@ struct SysBatchGroup {
     int wi;         // threads per strip
 };
 
+// Groups of one batch, one persistent launch each: on 128-thread strips, 0 =
+// harmonics in one chunk of at most SYS_BATCH_SMALL_KP pairs (the first-chunk
+// specialisations, compile-time seed and half pair, three CTAs per SM), 1 =
+// the rest (general kernel); 2 = 256-thread strips (general kernel).
+constexpr int SYS_BATCH_GROUPS = 3;
+constexpr int SYS_BATCH_SMALL_KP = 4;
+
 struct SysBatchTable {
     int counters[4];  // next tile of each group (reset by every launch)
     int magic;
     int in_dtype;
     int pad[2];
-    SysBatchGroup g[2];  // 128-thread and 256-thread strips
+    SysBatchGroup g[SYS_BATCH_GROUPS];
     SysBatchImage img[1];  // all images, group 0 first
 };
 
-cudaError_t launch_sys_batch(SysBatchTable* tab, int group, int wi, int grid, int in_dtype,
+// Specialised kernel of a one-chunk image with K harmonics starting at kstart
+// (N mod 2): sets *group to 0 and returns the kernel's index within it when
+// the harmonics fit SYS_BATCH_SMALL_KP pairs, else -1 (the general kernel).
+int sys_batch_kind(int K, int kstart, int* group);
+// Resident CTAs of a group's persistent kernel on this device.
+int sys_batch_grid(int group, int in_dtype);
+cudaError_t launch_sys_batch(SysBatchTable* tab, int group, int grid, int in_dtype,
                              cudaStream_t s);
 
 // Host-side parameter preparation shared by the entry points.
