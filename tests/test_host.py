@@ -162,6 +162,14 @@ def test_argument_checks_return_before_any_launch():
     d.pitch, d.den = 0, 0x2000
     arr = (bf.BfDesc * 1)(d)
     assert lib.bf_batch_workspace_bytes(arr, 1, None) == 0
+    # the persistent batch launches run 128- or 256-thread strips only
+    d.den = None
+    arr = (bf.BfDesc * 1)(d)
+    assert lib.bf_batch_workspace_bytes(arr, 1, None) > 0
+    for tw, ok in ((96, False), (64, False), (128, True), (256, True)):
+        lib.bf_default_opts(ctypes.byref(o))
+        o.tile_w = tw
+        assert (lib.bf_batch_workspace_bytes(arr, 1, ctypes.byref(o)) > 0) == ok, tw
 
 
 def test_status_strings():
