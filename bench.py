@@ -54,9 +54,10 @@ def hbm_peak_gbs():
 # FORM, PITCH>), 128-thread strips
 FWD_KERNEL = "bf_sys_kernel<11, 0, 1, 0, 128, float, 1, 1, 0, 0> (forward, saved buffers)"
 ADJ_KERNEL = "bf_sys_kernel<11, 1, 0, 0, 128, float, 1, 1, 0, 0> (adjoint)"
-# N = 40: harmonics 2, 4, .., 40 in 10 pairs, the constant harmonic apart (SEED 2)
+# N = 40: harmonics 2, 4, .., 40 in 10 pairs, the constant harmonic apart (SEED 2);
+# the adjoint takes form 8 (the combine negates the box sums)
 FWD_KERNEL_N40 = "bf_sys_kernel<10, 0, 1, 0, 128, float, 0, 2, 0, 0> (forward, saved buffers)"
-ADJ_KERNEL_N40 = "bf_sys_kernel<10, 1, 0, 0, 128, float, 0, 2, 0, 0> (adjoint)"
+ADJ_KERNEL_N40 = "bf_sys_kernel<10, 1, 0, 0, 128, float, 0, 2, 8, 0> (adjoint)"
 
 
 def fwd_flops_per_px(N: int) -> int:
