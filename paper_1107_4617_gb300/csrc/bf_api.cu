@@ -115,14 +115,16 @@ static bf_status choose_tiles(int H, int W, int r, const bf_opts* o, Tiles* t) {
     return BF_OK;
 }
 
-// Whether launch_sys runs the first-chunk kernels (bf_sys_first*.cu) for
-// this request: FP32 input, compact rows, plain sums, one harmonic chunk, and
-// a seed the first chunk specialises (odd N, or even N with harmonics beside
-// the constant one).
-static bool first_chunk_path(int K, int kstart, int ld, int W, const bf_opts* o, bool kahan) {
+// Whether launch_sys runs the first-chunk kernels (bf_sys_first*.cu) of
+// 64-thread strips for this request: compact rows, plain sums, one harmonic
+// chunk, a seed the first chunk specialises (odd N, or even N with harmonics
+// beside the constant one), and FP32 input -- or the adjoint, which reads only
+// the saved quads.
+static bool first_chunk_path(int K, int kstart, int ld, int W, const bf_opts* o, bool kahan,
+                             bool adjoint = false) {
     const int dtype = o ? o->in_dtype : BF_F32;
-    return dtype == BF_F32 && ld == W && !kahan && sys_chunks(K, false, o ? o->kp_max : 0) == 1 &&
-           (kstart == 1 || K > 1);
+    return (adjoint || dtype == BF_F32) && ld == W && !kahan &&
+           sys_chunks(K, false, o ? o->kp_max : 0) == 1 && (kstart == 1 || K > 1);
 }
 
 // Band shape of strips of wi threads: one wave of `slots` resident CTAs over
@@ -354,7 +356,7 @@ static bf_status bwd_ws(int B, int H, int W, int r, int K, int kstart, const bf_
     const int ld = row_pitch(opts ? opts->pitch : 0, W);
     if (ld < 0) return BF_ERR_INVALID_ARG;
     // the adjoint always runs plain sums
-    *use_sys = sys_tiles(H, W, ld, r, opts, t, B, first_chunk_path(K, kstart, ld, W, opts, false));
+    *use_sys = sys_tiles(H, W, ld, r, opts, t, B, first_chunk_path(K, kstart, ld, W, opts, false, true));
     if (!*use_sys) {
         bf_status st = choose_tiles(H, W, r, opts, t);
         if (st != BF_OK) return st;

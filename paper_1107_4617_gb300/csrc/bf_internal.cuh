@@ -87,12 +87,13 @@ cudaError_t launch_sys_w256(const SysParams& p, int mode, int dtype, int kp, int
                             int gy, cudaStream_t s);
 cudaError_t launch_sys_kahan(const SysParams& p, int mode, int dtype, int kp, int wi, int gx,
                              int gy, cudaStream_t s);
-// First (or only) harmonic chunk of a compact FP32 image on strips of up to
-// WMAX = 128 or 64 threads: KP pairs (1..11), half = the last pair holds one
+// First (or only) harmonic chunk of a compact image on strips of up to WMAX =
+// 128 or 64 threads: KP pairs (1..11), half = the last pair holds one
 // harmonic, seed = 1 (odd N, k0 = 1) or 2 (even N, k0 = 0, the constant
 // harmonic kept apart from the pairs). Explicitly instantiated in
-// bf_sys_first_*.cu (128) and bf_sys_first64_*.cu (64).
-template <int KP, int WMAX>
+// bf_sys_first_*.cu (128, FP32), bf_sys_first64_*.cu (64, FP32) and
+// bf_sys_first16_*.cu (128, BF16 input: forward modes only).
+template <int KP, int WMAX, typename Tin>
 cudaError_t sys_first_kp(const SysParams& p, int mode, bool half, int seed, int wi, int gx,
                          int gy, cudaStream_t s);
 

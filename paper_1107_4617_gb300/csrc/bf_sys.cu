@@ -18,43 +18,60 @@ static int sys_kp(int K) {
     return -1;
 }
 
-// First-chunk kernels of FP32 images on 128- or 64-thread strips (wi <= 64
-// takes the 64-column instantiations): odd N (seed 1) runs
-// kc harmonics in (kc + 1) / 2 pairs, even N (seed 2) the constant harmonic
-// apart and kc - 1 harmonics in pairs; the last pair is half when the paired
-// count is odd.
+// First-chunk kernels on 128- or 64-thread strips (wi <= 64 takes the
+// 64-column instantiations; BF16 input of the forward has 128-thread ones;
+// the adjoint reads only the saved quads and runs the FP32 ones): odd N
+// (seed 1) runs kc harmonics in (kc + 1) / 2 pairs, even N (seed 2) the
+// constant harmonic apart and kc - 1 harmonics in pairs; the last pair is
+// half when the paired count is odd.
 static cudaError_t launch_first(const SysParams& p, int mode, int kc, int seed, int wi, int gx,
-                                int gy, cudaStream_t s) {
+                                int gy, bool bf16, cudaStream_t s) {
     const int np = seed == 2 ? kc - 1 : kc;
     const bool half = np & 1;
     if (wi <= 64) {
         switch ((np + 1) / 2) {
-            case 1: return sys_first_kp<1, 64>(p, mode, half, seed, wi, gx, gy, s);
-            case 2: return sys_first_kp<2, 64>(p, mode, half, seed, wi, gx, gy, s);
-            case 3: return sys_first_kp<3, 64>(p, mode, half, seed, wi, gx, gy, s);
-            case 4: return sys_first_kp<4, 64>(p, mode, half, seed, wi, gx, gy, s);
-            case 5: return sys_first_kp<5, 64>(p, mode, half, seed, wi, gx, gy, s);
-            case 6: return sys_first_kp<6, 64>(p, mode, half, seed, wi, gx, gy, s);
-            case 7: return sys_first_kp<7, 64>(p, mode, half, seed, wi, gx, gy, s);
-            case 8: return sys_first_kp<8, 64>(p, mode, half, seed, wi, gx, gy, s);
-            case 9: return sys_first_kp<9, 64>(p, mode, half, seed, wi, gx, gy, s);
-            case 10: return sys_first_kp<10, 64>(p, mode, half, seed, wi, gx, gy, s);
-            case 11: return sys_first_kp<11, 64>(p, mode, half, seed, wi, gx, gy, s);
+            case 1: return sys_first_kp<1, 64, float>(p, mode, half, seed, wi, gx, gy, s);
+            case 2: return sys_first_kp<2, 64, float>(p, mode, half, seed, wi, gx, gy, s);
+            case 3: return sys_first_kp<3, 64, float>(p, mode, half, seed, wi, gx, gy, s);
+            case 4: return sys_first_kp<4, 64, float>(p, mode, half, seed, wi, gx, gy, s);
+            case 5: return sys_first_kp<5, 64, float>(p, mode, half, seed, wi, gx, gy, s);
+            case 6: return sys_first_kp<6, 64, float>(p, mode, half, seed, wi, gx, gy, s);
+            case 7: return sys_first_kp<7, 64, float>(p, mode, half, seed, wi, gx, gy, s);
+            case 8: return sys_first_kp<8, 64, float>(p, mode, half, seed, wi, gx, gy, s);
+            case 9: return sys_first_kp<9, 64, float>(p, mode, half, seed, wi, gx, gy, s);
+            case 10: return sys_first_kp<10, 64, float>(p, mode, half, seed, wi, gx, gy, s);
+            case 11: return sys_first_kp<11, 64, float>(p, mode, half, seed, wi, gx, gy, s);
+        }
+        return cudaErrorInvalidValue;
+    }
+    if (bf16 && mode != 2) {
+        switch ((np + 1) / 2) {
+            case 1: return sys_first_kp<1, 128, __nv_bfloat16>(p, mode, half, seed, wi, gx, gy, s);
+            case 2: return sys_first_kp<2, 128, __nv_bfloat16>(p, mode, half, seed, wi, gx, gy, s);
+            case 3: return sys_first_kp<3, 128, __nv_bfloat16>(p, mode, half, seed, wi, gx, gy, s);
+            case 4: return sys_first_kp<4, 128, __nv_bfloat16>(p, mode, half, seed, wi, gx, gy, s);
+            case 5: return sys_first_kp<5, 128, __nv_bfloat16>(p, mode, half, seed, wi, gx, gy, s);
+            case 6: return sys_first_kp<6, 128, __nv_bfloat16>(p, mode, half, seed, wi, gx, gy, s);
+            case 7: return sys_first_kp<7, 128, __nv_bfloat16>(p, mode, half, seed, wi, gx, gy, s);
+            case 8: return sys_first_kp<8, 128, __nv_bfloat16>(p, mode, half, seed, wi, gx, gy, s);
+            case 9: return sys_first_kp<9, 128, __nv_bfloat16>(p, mode, half, seed, wi, gx, gy, s);
+            case 10: return sys_first_kp<10, 128, __nv_bfloat16>(p, mode, half, seed, wi, gx, gy, s);
+            case 11: return sys_first_kp<11, 128, __nv_bfloat16>(p, mode, half, seed, wi, gx, gy, s);
         }
         return cudaErrorInvalidValue;
     }
     switch ((np + 1) / 2) {
-        case 1: return sys_first_kp<1, 128>(p, mode, half, seed, wi, gx, gy, s);
-        case 2: return sys_first_kp<2, 128>(p, mode, half, seed, wi, gx, gy, s);
-        case 3: return sys_first_kp<3, 128>(p, mode, half, seed, wi, gx, gy, s);
-        case 4: return sys_first_kp<4, 128>(p, mode, half, seed, wi, gx, gy, s);
-        case 5: return sys_first_kp<5, 128>(p, mode, half, seed, wi, gx, gy, s);
-        case 6: return sys_first_kp<6, 128>(p, mode, half, seed, wi, gx, gy, s);
-        case 7: return sys_first_kp<7, 128>(p, mode, half, seed, wi, gx, gy, s);
-        case 8: return sys_first_kp<8, 128>(p, mode, half, seed, wi, gx, gy, s);
-        case 9: return sys_first_kp<9, 128>(p, mode, half, seed, wi, gx, gy, s);
-        case 10: return sys_first_kp<10, 128>(p, mode, half, seed, wi, gx, gy, s);
-        case 11: return sys_first_kp<11, 128>(p, mode, half, seed, wi, gx, gy, s);
+        case 1: return sys_first_kp<1, 128, float>(p, mode, half, seed, wi, gx, gy, s);
+        case 2: return sys_first_kp<2, 128, float>(p, mode, half, seed, wi, gx, gy, s);
+        case 3: return sys_first_kp<3, 128, float>(p, mode, half, seed, wi, gx, gy, s);
+        case 4: return sys_first_kp<4, 128, float>(p, mode, half, seed, wi, gx, gy, s);
+        case 5: return sys_first_kp<5, 128, float>(p, mode, half, seed, wi, gx, gy, s);
+        case 6: return sys_first_kp<6, 128, float>(p, mode, half, seed, wi, gx, gy, s);
+        case 7: return sys_first_kp<7, 128, float>(p, mode, half, seed, wi, gx, gy, s);
+        case 8: return sys_first_kp<8, 128, float>(p, mode, half, seed, wi, gx, gy, s);
+        case 9: return sys_first_kp<9, 128, float>(p, mode, half, seed, wi, gx, gy, s);
+        case 10: return sys_first_kp<10, 128, float>(p, mode, half, seed, wi, gx, gy, s);
+        case 11: return sys_first_kp<11, 128, float>(p, mode, half, seed, wi, gx, gy, s);
     }
     return cudaErrorInvalidValue;
 }
@@ -92,9 +109,10 @@ cudaError_t launch_sys(const SysParams& base, int mode, bool kahan, int in_dtype
         if (mode == 2 && c + 1 < nch) p.partial = nullptr;  // reduce only on the last chunk
         cudaError_t e;
         if (kahan) e = launch_sys_kahan(p, mode, in_dtype, kp, wi, gx, gy, s);
-        else if (wi <= 128 && in_dtype == BF_F32 && p.ld == p.W &&
-                 (p.k0 == 1 || (p.k0 == 0 && kc > 1)))
-            e = launch_first(p, mode, kc, p.k0 == 1 ? 1 : 2, wi, gx, gy, s);
+        else if (wi <= 128 && p.ld == p.W && (p.k0 == 1 || (p.k0 == 0 && kc > 1)) &&
+                 (mode == 2 || in_dtype == BF_F32 || (in_dtype == BF_BF16 && wi > 64)))
+            e = launch_first(p, mode, kc, p.k0 == 1 ? 1 : 2, wi, gx, gy,
+                             mode != 2 && in_dtype == BF_BF16, s);
         else if (wi <= 128) e = launch_sys_w128(p, mode, in_dtype, kp, wi, gx, gy, s);
         else e = launch_sys_w256(p, mode, in_dtype, kp, wi, gx, gy, s);
         if (e != cudaSuccess) return e;

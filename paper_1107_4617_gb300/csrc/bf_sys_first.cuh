@@ -7,6 +7,8 @@
 // (shared memory for 64 columns, four CTAs per SM) serve small images, whose
 // 128-thread tiles would spend most steps in the skew ramp.
 #pragma once
+#include <type_traits>
+
 #include "bf_sys_engine.cuh"
 
 namespace bf {
@@ -43,31 +45,37 @@ constexpr unsigned char kFirstForm[3][2][11][2] = {
     },
 };
 
-template <int KP, bool HALF, int SEED, int WMAX>
+// Tin: the forward's input type. The adjoint reads only the saved quads, so it
+// is instantiated for Tin = float alone.
+template <int KP, bool HALF, int SEED, int WMAX, typename Tin>
 cudaError_t sys_first_modes(const SysParams& p, int mode, int wi, int gx, int gy,
                             cudaStream_t s) {
     constexpr int F0 = kFirstForm[0][SEED - 1][KP - 1][HALF];
     constexpr int F1 = kFirstForm[1][SEED - 1][KP - 1][HALF];
     constexpr int F2 = kFirstForm[2][SEED - 1][KP - 1][HALF];
     // compact images only (p.ld == W): the pitch terms are compiled out
-    if (mode == 2)
-        return sys_launch_one<KP, true, false, false, WMAX, float, HALF, SEED, F2, false>(p, wi, gx,
-                                                                                    gy, s);
+    if (mode == 2) {
+        if constexpr (std::is_same<Tin, float>::value)
+            return sys_launch_one<KP, true, false, false, WMAX, float, HALF, SEED, F2, false>(
+                p, wi, gx, gy, s);
+        else
+            return cudaErrorInvalidValue;
+    }
     if (mode == 1)
-        return sys_launch_one<KP, false, true, false, WMAX, float, HALF, SEED, F1, false>(p, wi, gx,
-                                                                                    gy, s);
-    return sys_launch_one<KP, false, false, false, WMAX, float, HALF, SEED, F0, false>(p, wi, gx, gy,
-                                                                                     s);
+        return sys_launch_one<KP, false, true, false, WMAX, Tin, HALF, SEED, F1, false>(p, wi, gx,
+                                                                                  gy, s);
+    return sys_launch_one<KP, false, false, false, WMAX, Tin, HALF, SEED, F0, false>(p, wi, gx, gy,
+                                                                                   s);
 }
 
-template <int KP, int WMAX>
+template <int KP, int WMAX, typename Tin>
 cudaError_t sys_first_kp(const SysParams& p, int mode, bool half, int seed, int wi, int gx,
                          int gy, cudaStream_t s) {
     if (seed == 1)
-        return half ? sys_first_modes<KP, true, 1, WMAX>(p, mode, wi, gx, gy, s)
-                    : sys_first_modes<KP, false, 1, WMAX>(p, mode, wi, gx, gy, s);
-    return half ? sys_first_modes<KP, true, 2, WMAX>(p, mode, wi, gx, gy, s)
-                : sys_first_modes<KP, false, 2, WMAX>(p, mode, wi, gx, gy, s);
+        return half ? sys_first_modes<KP, true, 1, WMAX, Tin>(p, mode, wi, gx, gy, s)
+                    : sys_first_modes<KP, false, 1, WMAX, Tin>(p, mode, wi, gx, gy, s);
+    return half ? sys_first_modes<KP, true, 2, WMAX, Tin>(p, mode, wi, gx, gy, s)
+                : sys_first_modes<KP, false, 2, WMAX, Tin>(p, mode, wi, gx, gy, s);
 }
 
 }  // namespace bf

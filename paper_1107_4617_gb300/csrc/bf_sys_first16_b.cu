@@ -1,0 +1,10 @@
+// First-chunk engine instantiations (see bf_sys_first.cuh), 128-thread strips, BF16 input
+// (forward modes): pair counts 6 7.
+#include "bf_sys_first.cuh"
+
+namespace bf {
+template cudaError_t sys_first_kp<6, 128, __nv_bfloat16>(const SysParams&, int, bool, int, int,
+                                                         int, int, cudaStream_t);
+template cudaError_t sys_first_kp<7, 128, __nv_bfloat16>(const SysParams&, int, bool, int, int,
+                                                         int, int, cudaStream_t);
+}  // namespace bf

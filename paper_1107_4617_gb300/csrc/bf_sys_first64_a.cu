@@ -2,14 +2,14 @@
 #include "bf_sys_first.cuh"
 
 namespace bf {
-template cudaError_t sys_first_kp<1, 64>(const SysParams&, int, bool, int, int, int, int,
-                                          cudaStream_t);
-template cudaError_t sys_first_kp<2, 64>(const SysParams&, int, bool, int, int, int, int,
-                                          cudaStream_t);
-template cudaError_t sys_first_kp<3, 64>(const SysParams&, int, bool, int, int, int, int,
-                                          cudaStream_t);
-template cudaError_t sys_first_kp<4, 64>(const SysParams&, int, bool, int, int, int, int,
-                                          cudaStream_t);
-template cudaError_t sys_first_kp<5, 64>(const SysParams&, int, bool, int, int, int, int,
-                                          cudaStream_t);
+template cudaError_t sys_first_kp<1, 64, float>(const SysParams&, int, bool, int, int, int,
+                                                 int, cudaStream_t);
+template cudaError_t sys_first_kp<2, 64, float>(const SysParams&, int, bool, int, int, int,
+                                                 int, cudaStream_t);
+template cudaError_t sys_first_kp<3, 64, float>(const SysParams&, int, bool, int, int, int,
+                                                 int, cudaStream_t);
+template cudaError_t sys_first_kp<4, 64, float>(const SysParams&, int, bool, int, int, int,
+                                                 int, cudaStream_t);
+template cudaError_t sys_first_kp<5, 64, float>(const SysParams&, int, bool, int, int, int,
+                                                 int, cudaStream_t);
 }  // namespace bf

@@ -2,14 +2,14 @@
 #include "bf_sys_first.cuh"
 
 namespace bf {
-template cudaError_t sys_first_kp<1, 128>(const SysParams&, int, bool, int, int, int, int,
-                                          cudaStream_t);
-template cudaError_t sys_first_kp<2, 128>(const SysParams&, int, bool, int, int, int, int,
-                                          cudaStream_t);
-template cudaError_t sys_first_kp<3, 128>(const SysParams&, int, bool, int, int, int, int,
-                                          cudaStream_t);
-template cudaError_t sys_first_kp<4, 128>(const SysParams&, int, bool, int, int, int, int,
-                                          cudaStream_t);
-template cudaError_t sys_first_kp<5, 128>(const SysParams&, int, bool, int, int, int, int,
-                                          cudaStream_t);
+template cudaError_t sys_first_kp<1, 128, float>(const SysParams&, int, bool, int, int, int,
+                                                 int, cudaStream_t);
+template cudaError_t sys_first_kp<2, 128, float>(const SysParams&, int, bool, int, int, int,
+                                                 int, cudaStream_t);
+template cudaError_t sys_first_kp<3, 128, float>(const SysParams&, int, bool, int, int, int,
+                                                 int, cudaStream_t);
+template cudaError_t sys_first_kp<4, 128, float>(const SysParams&, int, bool, int, int, int,
+                                                 int, cudaStream_t);
+template cudaError_t sys_first_kp<5, 128, float>(const SysParams&, int, bool, int, int, int,
+                                                 int, cudaStream_t);
 }  // namespace bf

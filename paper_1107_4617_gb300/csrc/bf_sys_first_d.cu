@@ -2,6 +2,6 @@
 #include "bf_sys_first.cuh"
 
 namespace bf {
-template cudaError_t sys_first_kp<10, 128>(const SysParams&, int, bool, int, int, int, int,
-                                          cudaStream_t);
+template cudaError_t sys_first_kp<10, 128, float>(const SysParams&, int, bool, int, int, int,
+                                                 int, cudaStream_t);
 }  // namespace bf

@@ -289,3 +289,32 @@ def test_adjoint_largest_windows(cuda_lib, r):
     got = gi.cpu().numpy()
     scale = np.abs(ref).max()
     assert np.abs(got - ref).max() <= GTOL * scale
+
+
+@pytest.mark.parametrize("H,W,r,sigma,N", [(150, 260, 6, 0.1, 41), (120, 200, 4, 0.2, 40),
+                                           (90, 140, 3, 0.3, 5), (100, 130, 5, 0.085, 50)])
+def test_bf16_input_forward_and_adjoint(cuda_lib, H, W, r, sigma, N):
+    """BF16-stored input through the forward with saved quads (the BF16
+    first-chunk kernels, and the general ones for N > 43) and the adjoint
+    (which reads only the quads): against the oracle on the BF16-decoded
+    image, and the quads' f - T/2 exactly as decoded."""
+    bf = cuda_lib
+    f = synth.rectangles(H, W, seed=H + N)
+    w = synth.weights((H, W), seed=7)
+    fb = torch.from_numpy(f).cuda().to(torch.bfloat16)
+    f16 = fb.float().cpu().numpy()
+    o = bf._opts(save=True, in_dtype=bf.BF16)
+    sv = torch.empty((H, W, 4), device="cuda")
+    out = bf.bf_forward(fb, r, sigma, 1.0, N, opts=o, saved=sv)
+    gi = torch.empty((H, W), device="cuda")
+    ws = torch.empty((bf.bf_backward_workspace_bytes(H, W, r, sigma, 1.0, N, o) // 4 + 1,),
+                     device="cuda")
+    bf.bf_backward(fb, out, torch.from_numpy(w).cuda(), sv, r, sigma, 1.0, N, grad_img=gi,
+                   workspace=ws, opts=o)
+    torch.cuda.synchronize()
+    ref = oracle.bilateral(f16.astype(np.float64), r, math.pi / 2, N)
+    got = out.cpu().numpy()
+    assert (np.abs(got - ref) / np.maximum(np.abs(ref), 1e-2)).max() <= 1e-4
+    np.testing.assert_array_equal(sv.cpu().numpy()[..., 0], f16 - np.float32(0.5))
+    gref, _ = oracle.bilateral_grad(f16.astype(np.float64), w.astype(np.float64), r, math.pi / 2, N)
+    check_grad(gi.cpu().numpy(), gref)
