@@ -38,7 +38,7 @@ struct BwdParams {
     const float* gout;    // dL/dout (row pitch ld)
     const float4* sv;     // the forward's saved quads (compact)
     float* gimg;          // dL/dimg (nullable, row pitch ld)
-    float* partial;       // per-CTA sums of f * dL/dtheta (nullable)
+    float* partial;       // per-CTA sums of (f - T/2) * dL/dtheta (nullable)
     int H, W, r, K, kstart, Hb, Tw;
     int ld;               // row pitch of gout and gimg in elements (>= W)
     float gamma;
@@ -56,7 +56,7 @@ struct SysParams {
     const float* gout;          // adjoint: dL/dout
     const float4* bsv;          // adjoint: the forward's saved quads
     float* gimg;                // adjoint: dL/dimg (nullable)
-    float* partial;             // adjoint: per-CTA sum of f * dL/dtheta (nullable)
+    float* partial;             // adjoint: per-CTA sum of (f - T/2) * dL/dtheta (nullable)
     float* acc_den;             // forward chunk accumulator for den when not saving
     float* acc_gv;              // adjoint chunk accumulators (value and phase parts)
     float* acc_gt;

@@ -251,7 +251,9 @@ __host__ __device__ constexpr int sys_smem_slots(int KP, int WMAX, bool dc = fal
 
 // One strip x band tile (bx, by) of one image, for one chunk of harmonics.
 // Called uniformly by every thread of the CTA. gsum accumulates f * dL/dtheta
-// (adjoint, last chunk only). KAHAN compensates the vertical running sums.
+// (adjoint, last chunk only; f as the saved quads hold it, shifted by mid: the
+// same sum, since the dL/dtheta of all pixels sum to 0). KAHAN compensates
+// the vertical running sums.
 // zo: element offset of this image in the compact buffers (saved quads, chunk
 // accumulators); zp: in the row-pitched image buffers (img, out, dL/dout,
 // dL/dimg, den), whose rows are p.ld elements apart. PITCH = false builds the
@@ -512,7 +514,7 @@ __device__ __forceinline__ void sys_tile(const SysParams& p, int bx, int by, siz
                     NUM.x = fmaf(p.a[0], hf, NUM.x);
                     if constexpr (!BWD) DEN.x = fmaf(p.a[0], h1, DEN.x);
                 }
-                // FORM 2 / 3: the left neighbour's sums of pair i + PF are loaded
+                // BODY 2 / 3: the left neighbour's sums of pair i + PF are loaded
                 // before this lane stores pair i (the two step-parity buffers
                 // never overlap), so the loads stay in flight across the stores
                 constexpr int PF = BODY == 2 ? 2 : (BODY == 3 ? 1 : 0);
