@@ -444,7 +444,7 @@ static bf_status backward_impl(const void* img, const float* out, const float* g
         if (ws.chunked) {
             float* acc = reinterpret_cast<float*>(static_cast<char*>(workspace) + ws.acc_offset);
             q.acc_gv = acc;
-            q.acc_gt = acc + (size_t)H * W;
+            q.acc_gt = acc + (size_t)B * H * W;  // both hold B images
         }
         q.Hb = t.Hb; q.Tw = t.Tw;
         q.B = B;
