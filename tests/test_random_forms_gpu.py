@@ -1,0 +1,138 @@
+"""Seeded random cases of the other forms, each against the oracle:
+
+- batches of 1..10 uneven images (sizes 1..300, r 0..64, N by the order rule
+  or given up to 64, row-pitched images, the optional den output, FP32 or
+  BF16 input), the three persistent launch groups mixed in one batch, with the
+  built-in band height or a given one;
+- Kahan-compensated forward, with and without saved quads (the engine's
+  chunked pass and the single-pass kernel);
+- gamma from sigma_r: dL/dsigma_r against the oracle's direct form.
+The cases are drawn from fixed seeds, so every run checks the same ones."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1107_4617_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-4
+SENT = -7.0
+
+
+def _rel(got, ref):
+    return np.abs(np.asarray(got, np.float64) - ref) / np.maximum(np.abs(ref), 1e-2)
+
+
+def _batches(n=8, seed=41):
+    g = np.random.default_rng(seed)
+    out = []
+    for k in range(n):
+        imgs = []
+        for _ in range(int(g.integers(1, 11))):
+            H = int(g.choice([1, 5, 40, 97, 160, 257, 300]))
+            W = int(g.choice([1, 7, 64, 130, 211, 300]))
+            r = int(g.choice([0, 1, 3, 8, 20, 33, 41, 50, 64]))
+            sigma = float(g.uniform(0.08, 0.4))
+            N = int(g.choice([0, 0, 0, 2, 9, 40, 47, 64]))
+            pad = int(g.choice([0, 0, 3]))
+            den = bool(g.random() < 0.5)
+            imgs.append((H, W, r, sigma, N, pad, den))
+        bf16 = bool(g.random() < 0.3)
+        tile_h = int(g.choice([0, 0, 64, 256]))
+        out.append((k, bf16, tile_h, imgs))
+    return out
+
+
+@pytest.mark.parametrize("case", _batches(), ids=lambda c: "batch%d" % c[0])
+def test_random_batch(cuda_lib, case):
+    bf = cuda_lib
+    k, bf16, tile_h, specs = case
+    dt = torch.bfloat16 if bf16 else torch.float32
+    imgs, outs, dens, bigs, fds = [], [], [], [], []
+    for i, (H, W, r, sigma, N, pad, den) in enumerate(specs):
+        f = synth.rectangles(H, W, seed=100 * k + i)
+        P = W + pad
+        big = torch.zeros((H, P), dtype=dt, device="cuda")
+        big[:, :W] = torch.from_numpy(f).to(dt)
+        fds.append(big[:, :W].float().cpu().numpy().astype(np.float64))
+        ob = torch.full((H, P), SENT, device="cuda")
+        db = torch.full((H, P), SENT, device="cuda") if den else None
+        imgs.append(big[:, :W])
+        outs.append(ob[:, :W])
+        dens.append(db[:, :W] if den else None)
+        bigs.append((ob, db, W))
+    o = bf._opts(in_dtype=bf.BF16 if bf16 else bf.F32, tile_h=tile_h)
+    descs = bf.make_descs(imgs, outs, [s[2] for s in specs], [s[3] for s in specs],
+                          Ns=[s[4] for s in specs], dens=dens)
+    ws = torch.empty(((bf.bf_batch_workspace_bytes(descs, o) + 3) // 4,), device="cuda")
+    bf.bf_batch(descs, ws, opts=o)
+    torch.cuda.synchronize()
+    for i, (H, W, r, sigma, N, pad, den) in enumerate(specs):
+        Nr = N if N > 0 else oracle.resolve_N(sigma, 1.0)
+        ref, rden = oracle.bilateral(fds[i], r, math.pi / 2, Nr, return_den=True)
+        got = outs[i].cpu().numpy()
+        assert _rel(got, ref).max() <= TOL, (k, i, specs[i])
+        ob, db, _ = bigs[i]
+        assert np.all(ob[:, W:].cpu().numpy() == SENT), (k, i, "padding written")
+        if den:
+            np.testing.assert_allclose(dens[i].cpu().numpy(), rden, rtol=2e-5, atol=1e-6)
+            assert np.all(db[:, W:].cpu().numpy() == SENT), (k, i, "den padding written")
+
+
+def _kahan_cases(n=8, seed=43):
+    g = np.random.default_rng(seed)
+    return [(i, int(g.choice([1, 33, 150, 260])), int(g.choice([2, 45, 129, 300])),
+             int(g.choice([0, 1, 4, 12, 30, 64])), int(g.choice([3, 11, 24, 41, 64])),
+             bool(g.random() < 0.5), bool(g.random() < 0.3)) for i in range(n)]
+
+
+@pytest.mark.parametrize("case", _kahan_cases(), ids=lambda c: "kahan%d" % c[0])
+def test_random_kahan(cuda_lib, case):
+    bf = cuda_lib
+    i, H, W, r, N, saved, bf16 = case
+    f = synth.rectangles(H, W, seed=7000 + i)
+    dt = torch.bfloat16 if bf16 else torch.float32
+    img = torch.from_numpy(f).cuda().to(dt)
+    fd = img.float().cpu().numpy().astype(np.float64)
+    o = bf._opts(kahan=True, save=saved, in_dtype=bf.BF16 if bf16 else bf.F32)
+    sv = torch.empty((H, W, 4), device="cuda") if saved else None
+    out = bf.bf_forward(img, r, 0.2, 1.0, N, opts=o, saved=sv)
+    torch.cuda.synchronize()
+    ref = oracle.bilateral(fd, r, math.pi / 2, N)
+    assert _rel(out.cpu().numpy(), ref).max() <= TOL, case
+
+
+def _sigma_cases(n=6, seed=47):
+    g = np.random.default_rng(seed)
+    return [(i, int(g.choice([20, 64, 130])), int(g.choice([17, 90, 200])),
+             int(g.choice([1, 3, 9, 24])), float(g.uniform(0.09, 0.35)), int(g.choice([1, 2])))
+            for i in range(n)]
+
+
+@pytest.mark.parametrize("case", _sigma_cases(), ids=lambda c: "sigma%d" % c[0])
+def test_random_sigma_gradient(cuda_lib, case):
+    bf = cuda_lib
+    i, H, W, r, sigma, B = case
+    N = oracle.resolve_N(sigma, 1.0)
+    f = np.stack([synth.rectangles(H, W, seed=8000 + 10 * i + b) for b in range(B)])
+    w = synth.weights((B, H, W), seed=i)
+    ft = torch.from_numpy(f).cuda()
+    opts = bf._opts(save=True, gamma_mode=bf.GAMMA_FROM_SIGMA)
+    sv = torch.empty((B, H, W, 4), device="cuda")
+    out = bf.bf_forward3d(ft, r, sigma, 1.0, N, opts=opts, saved=sv)
+    gs = torch.zeros((1,), device="cuda")
+    gi = torch.empty_like(ft)
+    ws = torch.empty((bf.bf_backward3d_workspace_bytes(B, H, W, r, sigma, 1.0, N, opts) // 4 + 1,),
+                     device="cuda")
+    bf.bf_backward3d(ft, out, torch.from_numpy(w).cuda(), sv, r, sigma, 1.0, N, grad_img=gi,
+                     grad_sigma=gs, workspace=ws, opts=opts)
+    torch.cuda.synchronize()
+    gamma = oracle.gamma_from_sigma(sigma, N)
+    dg = sum(oracle.bilateral_grad(f[b].astype(np.float64), w[b].astype(np.float64), r, gamma,
+                                   N)[1] for b in range(B))
+    ref = -(gamma / sigma) * dg
+    assert abs(float(gs) - ref) <= 1e-3 * max(1.0, abs(ref)), (case, float(gs), ref)
