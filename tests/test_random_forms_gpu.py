@@ -6,7 +6,9 @@
   built-in band height or a given one;
 - Kahan-compensated forward, with and without saved quads (the engine's
   chunked pass and the single-pass kernel);
-- gamma from sigma_r: dL/dsigma_r against the oracle's direct form.
+- gamma from sigma_r: dL/dsigma_r against the oracle's direct form;
+- the variant filters (shiftable spatial kernel, Algorithm 1, p_N, truncated
+  q_N) against the oracle's general direct form.
 The cases are drawn from fixed seeds, so every run checks the same ones."""
 import math
 
@@ -136,3 +138,51 @@ def test_random_sigma_gradient(cuda_lib, case):
                                    N)[1] for b in range(B))
     ref = -(gamma / sigma) * dg
     assert abs(float(gs) - ref) <= 1e-3 * max(1.0, abs(ref)), (case, float(gs), ref)
+
+
+def _variant_cases(n=16, seed=53):
+    g = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        kind = ["spatial", "alg1", "poly", "trunc"][i % 4]
+        H = int(g.choice([1, 9, 64, 131, 200]))
+        W = int(g.choice([2, 33, 100, 170, 256]))
+        r = int(g.choice([0, 1, 4, 11, 25, 40, 56]))
+        if kind == "spatial":
+            M, N = int(g.choice([1, 2])), int(g.choice([1, 2, 3, 4]))
+        elif kind == "alg1":
+            M, N = int(g.choice([1, 2, 3, 4, 6, 8])), 0
+        elif kind == "poly":
+            M, N = 0, int(g.choice([1, 2, 4, 6, 8]))
+        else:
+            M, N = int(g.choice([0, 1, 2])), int(g.choice([11, 19, 41, 64]))   # M: tolerance index
+        out.append((i, kind, H, W, r, M, N))
+    return out
+
+
+@pytest.mark.parametrize("case", _variant_cases(), ids=lambda c: "%s%d" % (c[1], c[0]))
+def test_random_variant(cuda_lib, case):
+    """The variant filters (shiftable spatial kernel q_M x q_M with q_N,
+    Algorithm 1, p_N, truncated q_N) on random shapes against the oracle's
+    general direct form."""
+    bf = cuda_lib
+    i, kind, H, W, r, M, N = case
+    f = synth.rectangles(H, W, seed=9000 + i)
+    ft = torch.from_numpy(f).cuda()
+    f64 = f.astype(np.float64)
+    if kind in ("spatial", "alg1"):
+        got = bf.bf_spatial_forward(ft, r, M, 0.0, 1.0, N)
+        ref = oracle.bilateral_general(f64, r, spatial=oracle.SPATIAL_QM, M=M,
+                                       range_kind=oracle.RANGE_COSN if N else oracle.RANGE_NONE,
+                                       gamma=math.pi / 2, N=N)
+    elif kind == "poly":
+        got = bf.bf_poly_forward(ft, r, 0.0, 1.0, N)
+        ref = oracle.bilateral_general(f64, r, range_kind=oracle.RANGE_POLY, N=N)
+    else:
+        tol = [1e-6, 1e-3, 1e-2][M]
+        K = bf.bf_trunc_harmonics(N, r, tol)
+        got = bf.bf_forward(ft, r, 0.0, 1.0, N, opts=bf._opts(trunc_tol=tol))
+        ref = oracle.bilateral_general(f64, r, range_kind=oracle.RANGE_TRUNC, gamma=math.pi / 2,
+                                       N=N, K_keep=K)
+    torch.cuda.synchronize()
+    assert _rel(got.cpu().numpy(), ref).max() <= TOL, case
