@@ -8,7 +8,8 @@
   chunked pass and the single-pass kernel);
 - gamma from sigma_r: dL/dsigma_r against the oracle's direct form;
 - the variant filters (shiftable spatial kernel, Algorithm 1, p_N, truncated
-  q_N) against the oracle's general direct form.
+  q_N) against the oracle's general direct form;
+- explicit launch shapes (strip widths, band heights) and the Kahan batch.
 The cases are drawn from fixed seeds, so every run checks the same ones."""
 import math
 
@@ -186,3 +187,61 @@ def test_random_variant(cuda_lib, case):
                                        N=N, K_keep=K)
     torch.cuda.synchronize()
     assert _rel(got.cpu().numpy(), ref).max() <= TOL, case
+
+
+def _shape_cases(n=12, seed=59):
+    g = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        tw = int(g.choice([64, 96, 128, 160, 224, 256]))
+        r = int(g.integers(0, min((tw - 16) // 2, 64) + 1))   # r <= BF_R_MAX
+        out.append((i, int(g.choice([5, 60, 150, 233])), int(g.choice([9, 100, 190, 300])), r,
+                    int(g.choice([4, 11, 25, 41, 52])), tw, int(g.choice([16, 32, 77, 300]))))
+    return out
+
+
+@pytest.mark.parametrize("case", _shape_cases(), ids=lambda c: "shape%d" % c[0])
+def test_random_launch_shapes(cuda_lib, case):
+    """Explicit strip widths (multiples of 32 up to 256, the tuner's knobs)
+    and band heights: forward with saved quads and the adjoint against the
+    oracle."""
+    bf = cuda_lib
+    i, H, W, r, N, tw, th = case
+    f = synth.rectangles(H, W, seed=9500 + i)
+    w = synth.weights((H, W), seed=i)
+    ft = torch.from_numpy(f).cuda()
+    o = bf._opts(save=True, tile_w=tw, tile_h=th)
+    sv = torch.empty((H, W, 4), device="cuda")
+    out = bf.bf_forward(ft, r, 0.0, 1.0, N, opts=o, saved=sv)
+    gi = torch.empty_like(ft)
+    ws = torch.empty((bf.bf_backward_workspace_bytes(H, W, r, 0.0, 1.0, N, o) // 4 + 1,),
+                     device="cuda")
+    bf.bf_backward(ft, out, torch.from_numpy(w).cuda(), sv, r, 0.0, 1.0, N, grad_img=gi,
+                   workspace=ws, opts=o)
+    torch.cuda.synchronize()
+    f64 = f.astype(np.float64)
+    assert _rel(out.cpu().numpy(), oracle.bilateral(f64, r, math.pi / 2, N)).max() <= TOL, case
+    gref, _ = oracle.bilateral_grad(f64, w.astype(np.float64), r, math.pi / 2, N)
+    assert np.abs(gi.cpu().numpy() - gref).max() <= 1e-3 * np.abs(gref).max(), case
+
+
+@pytest.mark.parametrize("seed", [61, 67])
+def test_random_kahan_batch(cuda_lib, seed):
+    """The Kahan batch (single-pass kernel over a tile queue) on random uneven
+    images against the oracle."""
+    bf = cuda_lib
+    g = np.random.default_rng(seed)
+    specs = [(int(g.choice([1, 30, 120, 200])), int(g.choice([3, 64, 150, 280])),
+              int(g.choice([0, 2, 7, 20])), float(g.uniform(0.08, 0.4))) for _ in range(6)]
+    imgs = [torch.from_numpy(synth.rectangles(H, W, seed=seed + k)).cuda()
+            for k, (H, W, r, s) in enumerate(specs)]
+    outs = [torch.full_like(im, SENT) for im in imgs]
+    descs = bf.make_descs(imgs, outs, [s[2] for s in specs], [s[3] for s in specs])
+    o = bf._opts(kahan=True)
+    ws = torch.empty(((bf.bf_batch_workspace_bytes(descs, o) + 3) // 4,), device="cuda")
+    bf.bf_batch(descs, ws, opts=o)
+    torch.cuda.synchronize()
+    for k, (H, W, r, s) in enumerate(specs):
+        ref = oracle.bilateral(imgs[k].cpu().numpy().astype(np.float64), r, math.pi / 2,
+                               oracle.resolve_N(s, 1.0))
+        assert _rel(outs[k].cpu().numpy(), ref).max() <= TOL, (seed, k, specs[k])
