@@ -121,3 +121,40 @@ def test_batch_launch_needs_a_prepared_table(cuda_lib):
     for s, im, o in zip(specs, imgs, outs):
         ref = bf.bf_forward(im, s["r"], s["sigma_r"])
         assert torch.max(torch.abs(o - ref)).item() <= 2e-4
+
+
+@pytest.mark.parametrize("H,W,r,N", [(300, 410, 10, 41), (96, 128, 4, 50), (700, 900, 45, 11)])
+def test_step_graph_replay(cuda_lib, H, W, r, N):
+    """The forward with saved quads and the adjoint (dL/df and dL/dsigma_r)
+    captured into one CUDA graph and replayed equal the eager calls bit for
+    bit: one harmonic chunk, two chunks with their workspace accumulators,
+    and 256-thread strips."""
+    bf = cuda_lib
+    f = torch.from_numpy(synth.rectangles(H, W, seed=H)).cuda()
+    g = torch.from_numpy(synth.weights((H, W), seed=2)).cuda()
+    sigma = 0.15
+    opts = bf._opts(save=True, gamma_mode=bf.GAMMA_FROM_SIGMA)
+    out = torch.empty_like(f)
+    sv = torch.empty((H, W, 4), device="cuda")
+    gi = torch.empty_like(f)
+    gs = torch.zeros((1,), device="cuda")
+    ws = torch.empty((bf.bf_backward_workspace_bytes(H, W, r, sigma, 1.0, N, opts) // 4 + 1,),
+                     device="cuda")
+    s = torch.cuda.Stream()
+
+    def step():
+        bf.bf_forward(f, r, sigma, 1.0, N, out=out, opts=opts, saved=sv, stream=s)
+        bf.bf_backward(f, out, g, sv, r, sigma, 1.0, N, grad_img=gi, grad_sigma=gs,
+                       workspace=ws, opts=opts, stream=s)
+    with torch.cuda.stream(s):
+        step()  # eager (also sets the kernels' attributes)
+    s.synchronize()
+    ref = (out.clone(), gi.clone(), gs.clone())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        step()
+    for _ in range(2):
+        out.fill_(-1.0); gi.fill_(-1.0); gs.fill_(-1.0)
+        graph.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(out, ref[0]) and torch.equal(gi, ref[1]) and torch.equal(gs, ref[2])
