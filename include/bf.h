@@ -144,14 +144,20 @@ int bf_trunc_harmonics(int N, int r, float trunc_tol);
 double bf_gamma(float sigma_r, float T, int N, int gamma_mode);
 
 /* Bytes of the `saved` buffer bf_forward fills for bf_backward: H * W
-   quads of 4 floats, pixel-major, (f - T/2, 1 / den, out - T/2,
-   dnum_s - out * dden_s), where dnum_s, dden_s are num and den of Eq.
-   filter2 differentiated with respect to the centre value f(x) (divided by
-   gamma). f and out are stored shifted by the range midpoint T/2: the filter
-   commutes with a constant shift of the range, and the adjoint, run on the
-   shifted values, rounds against terms half as large (out = quad.z + T/2 up
-   to one rounding). The adjoint reads one 16-byte quad per pixel instead of
-   several planes. The buffer must be 16-byte aligned. */
+   quads of 4 floats, (f - T/2, 1 / den, out - T/2, dnum_s - out * dden_s),
+   where dnum_s, dden_s are num and den of Eq. filter2 differentiated with
+   respect to the centre value f(x) (divided by gamma).
+   - Layout: pixel (y, x)'s quad sits at index ((y + (x mod 128)) mod H) * W
+     + x when H >= 128, and at y * W + x below; [B][...] per image for the
+     3-D calls. The rows are sheared so that the anti-diagonals the filter
+     sweeps (one pixel per lane, row + column fixed across a warp) are
+     contiguous.
+   - f and out are stored shifted by the range midpoint T/2: the filter
+     commutes with a constant shift of the range, and the adjoint, run on
+     the shifted values, rounds against terms half as large (out = quad.z +
+     T/2 up to one rounding).
+   The adjoint reads one 16-byte quad per pixel instead of several planes.
+   The buffer must be 16-byte aligned. */
 size_t bf_saved_bytes(int H, int W);
 
 /*

@@ -78,15 +78,13 @@ __global__ void __launch_bounds__(256, 1) bf_bwd_strip_kernel(BwdParams p) {
         const bool ml = col_in && rho > y0 && l >= 0 && l < p.H;
         float fe = 0.f, ae = 0.f, be = 0.f, fl = 0.f, al = 0.f, bl = 0.f;
         if (me) {
-            const size_t q = (size_t)e * p.W + c;
-            const float4 sv = __ldg(p.sv + q);
+            const float4 sv = __ldg(p.sv + quad_index(e, c, p.H, p.W));
             fe = sv.x;
             ae = __ldg(p.gout + (size_t)e * p.ld + c) * sv.y;
             be = -ae * sv.z;
         }
         if (ml) {
-            const size_t q = (size_t)l * p.W + c;
-            const float4 sv = __ldg(p.sv + q);
+            const float4 sv = __ldg(p.sv + quad_index(l, c, p.H, p.W));
             fl = sv.x;
             al = __ldg(p.gout + (size_t)l * p.ld + c) * sv.y;
             bl = -al * sv.z;
@@ -111,7 +109,7 @@ __global__ void __launch_bounds__(256, 1) bf_bwd_strip_kernel(BwdParams p) {
             if (i < p.K) vrow[i * NT + j] = V[i];
         __syncthreads();
         if (is_out) {
-            const size_t o = (size_t)rho * p.W + c;    // compact (saved quads)
+            const size_t o = quad_index(rho, c, p.H, p.W);  // saved quads (sheared)
             const size_t op = (size_t)rho * p.ld + c;  // row-pitched (dL/dout, dL/dimg)
             const float4 svc = __ldg(p.sv + o);
             const float fc = svc.x;

@@ -14,6 +14,18 @@ namespace bf {
 // K = N / 2 + 1 <= 33 for N <= 64.
 constexpr int KCAP = BF_N_MAX / 2 + 1;
 
+// Index of pixel (row, col)'s quad in the saved buffer of an H x W image. The
+// rows are sheared by (col mod 128) and wrapped at H (for H >= 128; plain
+// row-major below): the skewed-strip engine reads and writes one pixel per
+// lane on an anti-diagonal (row + col fixed across a warp), and in this
+// layout those pixels are consecutive, so a warp's quad loads and stores
+// are contiguous instead of one row each.
+__host__ __device__ __forceinline__ int quad_index(int row, int col, int H, int W) {
+    int rr = row + (col & (H >= 128 ? 127 : 0));
+    if (rr >= H) rr -= H;
+    return rr * W + col;
+}
+
 // Everything one filter launch needs, passed by value as the kernel
 // parameter (a_k sits in the constant parameter bank, no __constant__
 // symbol, so concurrent launches with different N never race).

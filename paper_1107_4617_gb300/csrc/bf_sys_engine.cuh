@@ -211,8 +211,8 @@ struct Bases {
 
 // Masked loads leave neutral values (f = 0; in the adjoint g = 0, so the
 // plane weights alpha, beta are 0); the forward masks its own weights.
-// Forward: q = element offset in the row-pitched image. Adjoint: q = offset
-// in the compact saved quads, qg = offset in the row-pitched dL/dout.
+// Forward: q = element offset in the row-pitched image. Adjoint: q = index
+// in the saved quads (quad_index), qg = offset in the row-pitched dL/dout.
 template <bool BWD, typename Tin>
 __device__ __forceinline__ void load_px(Px<BWD>& v, const Bases<Tin>& b, bool on, int q, int qg) {
     if constexpr (!BWD) {
@@ -234,8 +234,8 @@ __device__ __forceinline__ float pix_f(const Px<BWD>& v) {
 }
 
 // Masks and element offsets of one step's five pixels (entering and leaving
-// row of the own and the second column, centre): in the row-pitched image for
-// the forward, in the compact saved quads for the adjoint.
+// row of the own and the second column, centre) in the row-pitched image
+// buffers (the forward's image, the adjoint's dL/dout).
 struct Geo {
     bool m0, m1, m2, m3, out;
     int q0, q1, q2, q3, qo;
@@ -281,9 +281,10 @@ __device__ __forceinline__ void sys_tile(const SysParams& p, int bx, int by, siz
     const int r = p.r;
     const int W = p.W;
     const int ld = PITCH ? p.ld : W;      // row pitch of the image buffers
-    const int dld = ld - W;               // extra elements per row past a compact one
-    // row stride of the offsets Geo carries: the image (forward) or the quads (adjoint)
-    const int st = BWD ? W : ld;
+    // row stride of the offsets Geo carries: the row-pitched image buffers
+    // (the forward's image, the adjoint's dL/dout); the saved quads are
+    // addressed by quad_index (sheared rows, compact)
+    const int st = ld;
     const int x0 = bx * p.Tw;
     const int cw = x0 - r + j;            // own column
     const int c2 = cw - 2 * r - 1;        // column leaving the horizontal window
@@ -346,20 +347,25 @@ __device__ __forceinline__ void sys_tile(const SysParams& p, int bx, int by, siz
     Px<BWD> vA[5], vB[5];
     // a warp is first active at step 32 w; start its prefetch chain there
     Geo gA = geometry(w * 32), gB = gA;
-    // the adjoint's dL/dout offsets: the quads' offsets plus the pitched rows'
-    // extra elements (entering row e, leaving row e - 2r - 1, centre row e - r)
+    // the adjoint's quad offsets (sheared, compact) of the step's pixels:
+    // entering row e, leaving row e - 2r - 1, centre row e - r; its dL/dout
+    // offsets are Geo's (row-pitched)
+    auto quad_at = [&](int row, int col) { return quad_index(row, col, p.H, W); };
     auto load_step = [&](const Geo& gg, int t, Px<BWD> (&v)[5]) {
-        int de = 0, dl = 0, dc = 0;
         if constexpr (BWD) {
-            de = (e0 + t) * dld;
-            dl = de - (2 * r + 1) * dld;
-            dc = de - r * dld;
+            const int e = e0 + t, el = e - 2 * r - 1;
+            load_px<BWD, Tin>(v[0], b, gg.m0, quad_at(e, cw), gg.q0);
+            load_px<BWD, Tin>(v[1], b, gg.m1, quad_at(e, c2), gg.q1);
+            load_px<BWD, Tin>(v[2], b, gg.m2, quad_at(el, cw), gg.q2);
+            load_px<BWD, Tin>(v[3], b, gg.m3, quad_at(el, c2), gg.q3);
+            load_px<BWD, Tin>(v[4], b, gg.out, quad_at(e - r, co), gg.qo);
+        } else {
+            load_px<BWD, Tin>(v[0], b, gg.m0, gg.q0, 0);
+            load_px<BWD, Tin>(v[1], b, gg.m1, gg.q1, 0);
+            load_px<BWD, Tin>(v[2], b, gg.m2, gg.q2, 0);
+            load_px<BWD, Tin>(v[3], b, gg.m3, gg.q3, 0);
+            load_px<BWD, Tin>(v[4], b, gg.out, gg.qo, 0);
         }
-        load_px<BWD, Tin>(v[0], b, gg.m0, gg.q0, gg.q0 + de);
-        load_px<BWD, Tin>(v[1], b, gg.m1, gg.q1, gg.q1 + de);
-        load_px<BWD, Tin>(v[2], b, gg.m2, gg.q2, gg.q2 + dl);
-        load_px<BWD, Tin>(v[3], b, gg.m3, gg.q3, gg.q3 + dl);
-        load_px<BWD, Tin>(v[4], b, gg.out, gg.qo, gg.qo + dc);
     };
     load_step(gA, w * 32, vA);
     __syncthreads();
@@ -387,7 +393,7 @@ __device__ __forceinline__ void sys_tile(const SysParams& p, int bx, int by, siz
                     if constexpr (!BWD) {
                         prefetch_l2(b.img + ef * ld + cw);
                     } else {
-                        prefetch_l2(b.bsv + ef * W + cw);
+                        prefetch_l2(b.bsv + quad_at(ef, cw));
                         prefetch_l2(b.gout + ef * ld + cw);
                     }
                 }
@@ -670,16 +676,10 @@ __device__ __forceinline__ void sys_tile(const SysParams& p, int bx, int by, siz
                 }
             }
             if (gc.out) {
-                // compact buffers (quads, chunk accumulators) and row-pitched ones
-                size_t o, op;
-                if constexpr (!PITCH) {
-                    o = (size_t)gc.qo + zo;
-                    op = o;
-                } else {
-                    const int ro = e0 + t - r;   // the centre's row
-                    o = BWD ? (size_t)gc.qo + zo : (size_t)ro * W + co + zo;
-                    op = BWD ? (size_t)gc.qo + (size_t)ro * dld + zp : (size_t)gc.qo + zp;
-                }
+                // compact buffers (saved quads, chunk accumulators; sheared
+                // rows) and row-pitched ones (out, den, dL/dimg)
+                const size_t o = (size_t)quad_at(e0 + t - r, co) + zo;
+                const size_t op = (size_t)gc.qo + zp;
                 float num = NUM.x + NUM.y, den = DEN.x + DEN.y;
                 // chunked harmonics: partial sums live in the output buffers
                 // between chunks (acc: 0 single, 1 first, 2 middle, 3 last)

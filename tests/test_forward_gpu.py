@@ -12,6 +12,7 @@ import pytest
 import torch
 
 import oracle
+from _quads import rowmajor
 from paper_1107_4617_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -42,7 +43,7 @@ def run_fwd(bf, img_np, r, sigma_r=0.2, T=1.0, N=0, kahan=False, dtype=torch.flo
         assert np.all(b[:guard] == 12345.0) and np.all(b[guard + H * W:] == 12345.0), "guard band written"
     res = out.cpu().numpy()
     # saved quads as planes: (f - T/2, 1/den, out - T/2, dnum_s - out dden_s)
-    return (res, np.moveaxis(sv.cpu().numpy(), 2, 0)) if saved else res
+    return (res, np.moveaxis(rowmajor(sv), 2, 0)) if saved else res
 
 
 def oracle_ref(img_np, r, sigma_r, T, N, gamma=None):
