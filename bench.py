@@ -51,9 +51,9 @@ def hbm_peak_gbs():
         return 6800.0, "fallback 6.8 TB/s"
 # kernels the bench's two launches run: N = 41 -> harmonics 1, 3, .., 41 in 10
 # pairs and a half pair (template <KP, BWD, SAVE, KAHAN, WMAX, Tin, HALF, SEED,
-# FORM, PITCH>), 128-thread strips
-FWD_KERNEL = "bf_sys_kernel<11, 0, 1, 0, 128, float, 1, 1, 0, 0> (forward, saved buffers)"
-ADJ_KERNEL = "bf_sys_kernel<11, 1, 0, 0, 128, float, 1, 1, 0, 0> (adjoint)"
+# FORM, PITCH>), 128-thread strips, form 8 (the combine negates the box sums)
+FWD_KERNEL = "bf_sys_kernel<11, 0, 1, 0, 128, float, 1, 1, 8, 0> (forward, saved buffers)"
+ADJ_KERNEL = "bf_sys_kernel<11, 1, 0, 0, 128, float, 1, 1, 8, 0> (adjoint)"
 # N = 40: harmonics 2, 4, .., 40 in 10 pairs, the constant harmonic apart (SEED 2);
 # the adjoint takes form 8 (the combine negates the box sums)
 FWD_KERNEL_N40 = "bf_sys_kernel<10, 0, 1, 0, 128, float, 0, 2, 0, 0> (forward, saved buffers)"

@@ -22,26 +22,25 @@ namespace bf {
 // combine negates the box sums instead of the centre's sines. The forms
 // compute the same values; they differ only in instruction schedule, and
 // the fastest one differs between instantiations by up to 1.9x. Each entry
-// was measured on a GB300 at 4096^2, r = 10 (median of 12-16 launches with
-// L2 flushed, every N = 2..43): the fastest of forms 0-7, then bit 3 where
-// it was at least 2 % faster (a previous entry is kept unless another is at
-// least 2 % faster), on 128-thread strips; the 64-thread kernels take the
-// same forms.
+// was measured on a GB300 at 4096^2, r = 10 (median of 12 launches with L2
+// flushed, every N = 2..43, all sixteen forms; a previous entry is kept
+// unless another is at least 2 % faster), on 128-thread strips; the
+// 64-thread kernels take the same forms.
 constexpr unsigned char kFirstForm[3][2][11][2] = {
     // plain forward
     {
-        {{6, 0}, {6, 5}, {6, 5}, {5, 5}, {0, 5}, {4, 4}, {0, 5}, {0, 5}, {0, 0}, {0, 0}, {0, 0}},
-        {{5, 6}, {5, 6}, {6, 5}, {4, 5}, {5, 5}, {2, 5}, {0, 6}, {0, 0}, {1, 1}, {0, 0}, {0, 0}},
+        {{14, 0}, {6, 5}, {6, 5}, {5, 5}, {11, 5}, {2, 4}, {0, 5}, {0, 5}, {0, 0}, {0, 0}, {0, 0}},
+        {{5, 12}, {5, 6}, {6, 5}, {5, 5}, {5, 5}, {1, 5}, {0, 1}, {0, 0}, {1, 1}, {9, 0}, {0, 0}},
     },
     // forward with saved quads
     {
-        {{13, 0}, {13, 14}, {5, 5}, {0, 5}, {0, 5}, {9, 12}, {8, 0}, {9, 0}, {9, 0}, {1, 1}, {8, 0}},
-        {{5, 13}, {5, 12}, {5, 13}, {3, 5}, {2, 5}, {1, 0}, {8, 5}, {0, 0}, {0, 0}, {0, 8}, {0, 8}},
+        {{13, 0}, {13, 13}, {5, 13}, {0, 5}, {0, 11}, {9, 12}, {8, 13}, {9, 0}, {9, 0}, {1, 9}, {8, 8}},
+        {{13, 13}, {5, 12}, {4, 13}, {3, 8}, {2, 15}, {1, 0}, {8, 1}, {0, 0}, {0, 0}, {0, 8}, {0, 8}},
     },
     // adjoint
     {
-        {{0, 0}, {6, 6}, {8, 6}, {6, 6}, {6, 13}, {12, 5}, {0, 14}, {8, 6}, {0, 0}, {8, 0}, {8, 0}},
-        {{0, 6}, {6, 5}, {2, 6}, {5, 6}, {5, 2}, {0, 6}, {0, 6}, {9, 0}, {0, 0}, {8, 8}, {0, 1}},
+        {{15, 0}, {6, 6}, {15, 13}, {15, 5}, {6, 13}, {1, 5}, {0, 6}, {8, 6}, {0, 0}, {8, 0}, {8, 8}},
+        {{4, 6}, {6, 5}, {5, 6}, {15, 1}, {0, 5}, {0, 13}, {14, 13}, {8, 0}, {0, 0}, {8, 8}, {0, 1}},
     },
 };
 
