@@ -290,7 +290,8 @@ bf_status bf_backward_noalloc(const void* img, const float* out, const float* gr
  *             CTAs; BF16 input, Kahan, trunc_tol and BF_GAMMA_FROM_SIGMA give
  *             BF_ERR_UNSUPPORTED.
  *   saved     NULL, or device buffer of bf_saved_bytes(H, W) (16-byte aligned)
- *             receiving the quads (f, 1/den, out, dnum_s - out dden_s) for
+ *             receiving the quads (f, 1/den, out, dnum_s - out dden_s),
+ *             row-major (not sheared, not shifted by T/2), for
  *             bf_spatial_backward.
  * r = 0 (a 1 x 1 window) is exact: out = img, saved quads (f, 1, f, 0).
  * Errors: BF_ERR_INVALID_ARG, BF_ERR_UNSUPPORTED (other M, N, r), BF_ERR_CUDA.
@@ -335,7 +336,8 @@ int bf_poly_resolve_N(float sigma_r, float T);
  *   opts      NULL or defaults (tile_h honoured); BF16 input, Kahan,
  *             trunc_tol or BF_GAMMA_FROM_SIGMA give BF_ERR_UNSUPPORTED.
  *   saved     NULL, or device buffer of bf_saved_bytes(H, W) (16-byte aligned)
- *             receiving the quads (f, 1/den, out, dnum_s - out dden_s) for
+ *             receiving the quads (f, 1/den, out, dnum_s - out dden_s),
+ *             row-major (not sheared, not shifted by T/2), for
  *             bf_poly_backward.
  * r = 0 (a 1 x 1 window) is exact: out = img, saved quads (f, 1, f, 0), and
  * bf_poly_backward returns grad_out.
