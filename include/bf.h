@@ -291,7 +291,7 @@ bf_status bf_backward_noalloc(const void* img, const float* out, const float* gr
  *             BF_ERR_UNSUPPORTED.
  *   saved     NULL, or device buffer of bf_saved_bytes(H, W) (16-byte aligned)
  *             receiving the quads (f, 1/den, out, dnum_s - out dden_s),
- *             row-major (not sheared, not shifted by T/2), for
+ *             not shifted by T/2, in the sheared layout of bf_forward's, for
  *             bf_spatial_backward.
  * r = 0 (a 1 x 1 window) is exact: out = img, saved quads (f, 1, f, 0).
  * Errors: BF_ERR_INVALID_ARG, BF_ERR_UNSUPPORTED (other M, N, r), BF_ERR_CUDA.
@@ -337,7 +337,7 @@ int bf_poly_resolve_N(float sigma_r, float T);
  *             trunc_tol or BF_GAMMA_FROM_SIGMA give BF_ERR_UNSUPPORTED.
  *   saved     NULL, or device buffer of bf_saved_bytes(H, W) (16-byte aligned)
  *             receiving the quads (f, 1/den, out, dnum_s - out dden_s),
- *             row-major (not sheared, not shifted by T/2), for
+ *             not shifted by T/2, in the sheared layout of bf_forward's, for
  *             bf_poly_backward.
  * r = 0 (a 1 x 1 window) is exact: out = img, saved quads (f, 1, f, 0), and
  * bf_poly_backward returns grad_out.

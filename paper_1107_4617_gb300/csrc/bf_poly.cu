@@ -104,12 +104,15 @@ __global__ void __launch_bounds__(WMAX, 2) poly_kernel(Params p) {
     // and dL/dout instead
     float4 nq[5];
     float ng[5];
-    auto load_one = [&](int k, bool on, size_t q) {
+    // pixel (row, col): the image and dL/dout at row * W + col, its saved quad
+    // at quad_index (rows sheared, so the diagonal a warp reads is contiguous)
+    auto load_one = [&](int k, bool on, int row, int col) {
         if constexpr (MODE == ADJ) {
-            nq[k] = on ? __ldg(p.bsv + q) : make_float4(0.f, 0.f, 0.f, 0.f);
-            ng[k] = on ? __ldg(p.gout + q) : 0.f;
+            nq[k] = on ? __ldg(p.bsv + quad_index(row, col, p.H, W))
+                       : make_float4(0.f, 0.f, 0.f, 0.f);
+            ng[k] = on ? __ldg(p.gout + (size_t)row * W + col) : 0.f;
         } else {
-            nq[k].x = on ? __ldg(p.img + q) : 0.f;
+            nq[k].x = on ? __ldg(p.img + (size_t)row * W + col) : 0.f;
         }
     };
     auto load_step = [&](int tt) {
@@ -119,11 +122,11 @@ __global__ void __launch_bounds__(WMAX, 2) poly_kernel(Params p) {
         const bool in_e = act && e >= 0 && e < p.H;
         const bool in_l = act && tau >= 2 * r + 1 && l >= 0 && l < p.H;
         const bool out = act && tau >= 2 * r && out_lane;
-        load_one(0, in_e && own_in, (size_t)e * W + cw);
-        load_one(1, in_e && sec_in, (size_t)e * W + c2);
-        load_one(2, in_l && own_in, (size_t)l * W + cw);
-        load_one(3, in_l && sec_in, (size_t)l * W + c2);
-        load_one(4, out, (size_t)rho * W + co);
+        load_one(0, in_e && own_in, e, cw);
+        load_one(1, in_e && sec_in, e, c2);
+        load_one(2, in_l && own_in, l, cw);
+        load_one(3, in_l && sec_in, l, c2);
+        load_one(4, out, rho, co);
     };
     load_step(w * 32);  // a warp is first active at step 32 w
     __syncthreads();
@@ -233,7 +236,8 @@ __global__ void __launch_bounds__(WMAX, 2) poly_kernel(Params p) {
                     p.out[o] = ov;
                     if constexpr (MODE == FWD_SAVE) {
                         const float dn = DN.x + DN.y, dd = DD.x + DD.y;
-                        p.sv[o] = make_float4(fc, 1.0f / den, ov, fmaf(-ov * p.invT, dd, dn));
+                        p.sv[quad_index(rho, co, p.H, W)] =
+                            make_float4(fc, 1.0f / den, ov, fmaf(-ov * p.invT, dd, dn));
                     }
                 }
             }
@@ -370,7 +374,7 @@ extern "C" bf_status bf_poly_forward(const void* img, int H, int W, int r, float
         // a 1 x 1 window: p_N(0) = 1 with slope 0, so out = f and the quads
         // are (f, 1, f, 0)
         cudaError_t e = unit_window(static_cast<const float*>(img), out,
-                                    static_cast<float4*>(saved), (size_t)H * W, s);
+                                    static_cast<float4*>(saved), H, W, s);
         return e == cudaSuccess ? BF_OK : set_cuda_error(e);
     }
     p.img = static_cast<const float*>(img);

@@ -238,12 +238,15 @@ __global__ void __launch_bounds__(WMAX, 2) spk_kernel(Params p) {
     float4 nq[5];
     float ng[5];
     float npart = 0.f;  // adjoint over a later combo range: the earlier ranges' dL/df
-    auto load_one = [&](int k, bool on, size_t q) {
+    // pixel (row, col): the image and dL/dout at row * W + col, its saved quad
+    // at quad_index (rows sheared, so the diagonal a warp reads is contiguous)
+    auto load_one = [&](int k, bool on, int row, int col) {
         if constexpr (MODE == ADJ) {
-            nq[k] = on ? __ldg(p.bsv + q) : make_float4(0.f, 0.f, 0.f, 0.f);
-            ng[k] = on ? __ldg(p.gout + q) : 0.f;
+            nq[k] = on ? __ldg(p.bsv + quad_index(row, col, p.H, W))
+                       : make_float4(0.f, 0.f, 0.f, 0.f);
+            ng[k] = on ? __ldg(p.gout + (size_t)row * W + col) : 0.f;
         } else {
-            nq[k].x = on ? __ldg(p.img + q) : 0.f;
+            nq[k].x = on ? __ldg(p.img + (size_t)row * W + col) : 0.f;
         }
     };
     auto load_step = [&](int tt) {
@@ -253,11 +256,11 @@ __global__ void __launch_bounds__(WMAX, 2) spk_kernel(Params p) {
         const bool in_e = act && e >= 0 && e < p.H;
         const bool in_l = act && tau >= 2 * r + 1 && l >= 0 && l < p.H;
         const bool out = act && tau >= 2 * r && out_lane;
-        load_one(0, in_e && own_in, (size_t)e * W + cw);
-        load_one(1, in_e && sec_in, (size_t)e * W + c2);
-        load_one(2, in_l && own_in, (size_t)l * W + cw);
-        load_one(3, in_l && sec_in, (size_t)l * W + c2);
-        load_one(4, out, (size_t)rho * W + co);
+        load_one(0, in_e && own_in, e, cw);
+        load_one(1, in_e && sec_in, e, c2);
+        load_one(2, in_l && own_in, l, cw);
+        load_one(3, in_l && sec_in, l, c2);
+        load_one(4, out, rho, co);
         if constexpr (MODE == ADJ && C0 > 0) npart = out ? p.gimg[(size_t)rho * W + co] : 0.f;
     };
     load_step(w * 32);  // a warp is first active at step 32 w
@@ -301,7 +304,7 @@ __global__ void __launch_bounds__(WMAX, 2) spk_kernel(Params p) {
                 const int ef = e + 8;
                 if (own_in && ef >= 0 && ef < p.H) {
                     if constexpr (MODE == ADJ) {
-                        prefetch_l2(p.bsv + (size_t)ef * W + cw);
+                        prefetch_l2(p.bsv + quad_index(ef, cw, p.H, W));
                         prefetch_l2(p.gout + (size_t)ef * W + cw);
                     } else {
                         prefetch_l2(p.img + (size_t)ef * W + cw);
@@ -479,7 +482,8 @@ __global__ void __launch_bounds__(WMAX, 2) spk_kernel(Params p) {
                     p.out[o] = ov;
                     if constexpr (MODE == FWD_SAVE) {
                         const float dn = DN.x + DN.y, dd = DD.x + DD.y;
-                        p.sv[o] = make_float4(fc, 1.0f / den, ov, fmaf(-ov, dd, dn));
+                        p.sv[quad_index(rho, co, p.H, W)] =
+                            make_float4(fc, 1.0f / den, ov, fmaf(-ov, dd, dn));
                     }
                 }
             }
@@ -604,12 +608,15 @@ __global__ void __launch_bounds__(WMAX, 2) spk_plane_kernel(Params p) {
     // is f) and dL/dout instead
     float4 nq[5];
     float ng[5];
-    auto load_one = [&](int k, bool on, size_t q) {
+    // pixel (row, col): the image and dL/dout at row * W + col, its saved quad
+    // at quad_index (rows sheared, so the diagonal a warp reads is contiguous)
+    auto load_one = [&](int k, bool on, int row, int col) {
         if constexpr (MODE == ADJ) {
-            nq[k] = on ? __ldg(p.bsv + q) : make_float4(0.f, 0.f, 0.f, 0.f);
-            ng[k] = on ? __ldg(p.gout + q) : 0.f;
+            nq[k] = on ? __ldg(p.bsv + quad_index(row, col, p.H, W))
+                       : make_float4(0.f, 0.f, 0.f, 0.f);
+            ng[k] = on ? __ldg(p.gout + (size_t)row * W + col) : 0.f;
         } else {
-            nq[k].x = on ? __ldg(p.img + q) : 0.f;
+            nq[k].x = on ? __ldg(p.img + (size_t)row * W + col) : 0.f;
         }
     };
     auto load_step = [&](int tt) {
@@ -619,11 +626,11 @@ __global__ void __launch_bounds__(WMAX, 2) spk_plane_kernel(Params p) {
         const bool in_e = act && e >= 0 && e < p.H;
         const bool in_l = act && tau >= 2 * r + 1 && l >= 0 && l < p.H;
         const bool out = act && tau >= 2 * r && out_lane;
-        load_one(0, in_e && own_in, (size_t)e * W + cw);
-        load_one(1, in_e && sec_in, (size_t)e * W + c2);
-        load_one(2, in_l && own_in, (size_t)l * W + cw);
-        load_one(3, in_l && sec_in, (size_t)l * W + c2);
-        load_one(4, out, (size_t)rho * W + co);
+        load_one(0, in_e && own_in, e, cw);
+        load_one(1, in_e && sec_in, e, c2);
+        load_one(2, in_l && own_in, l, cw);
+        load_one(3, in_l && sec_in, l, c2);
+        load_one(4, out, rho, co);
     };
     load_step(w * 32);  // a warp is first active at step 32 w
     __syncthreads();
@@ -787,7 +794,8 @@ __global__ void __launch_bounds__(WMAX, 2) spk_plane_kernel(Params p) {
                     const float ov = num / den;
                     p.out[o] = ov;
                     if constexpr (MODE == FWD_SAVE)
-                        p.sv[o] = make_float4(fc, 1.0f / den, ov, fmaf(-ov, dd, dn));
+                        p.sv[quad_index(rho, co, p.H, W)] =
+                            make_float4(fc, 1.0f / den, ov, fmaf(-ov, dd, dn));
                 }
             }
         }
@@ -1021,7 +1029,7 @@ extern "C" bf_status bf_spatial_forward(const void* img, int H, int W, int r, in
         // out = f. The strip's hand-off would telescope over all lanes with
         // signed terms here and lose digits to no purpose.
         cudaError_t e = unit_window(static_cast<const float*>(img), out,
-                                    static_cast<float4*>(saved), (size_t)H * W, s);
+                                    static_cast<float4*>(saved), H, W, s);
         return e == cudaSuccess ? BF_OK : set_cuda_error(e);
     }
     cudaError_t e = spk::dispatch(p, mode, M, N, gx, gy, s);

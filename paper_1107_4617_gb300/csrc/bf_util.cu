@@ -71,19 +71,23 @@ __global__ void finish_kernel(int* keys) {
 
 }  // namespace util
 
-__global__ void unit_window_quads(const float* img, float* out, float4* sv, size_t n) {
+// out = f and the quads (f, 1, f, 0), pixel (y, x)'s at quad_index(y, x, H, W)
+__global__ void unit_window_quads(const float* img, float* out, float4* sv, int H, int W) {
+    const size_t n = (size_t)H * W;
     const size_t stride = (size_t)gridDim.x * blockDim.x;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += stride) {
         const float f = img[i];
+        const int y = (int)(i / (size_t)W), x = (int)(i - (size_t)y * W);
         out[i] = f;
-        sv[i] = make_float4(f, 1.f, f, 0.f);
+        sv[quad_index(y, x, H, W)] = make_float4(f, 1.f, f, 0.f);
     }
 }
 
-cudaError_t unit_window(const float* img, float* out, float4* sv, size_t n, cudaStream_t s) {
+cudaError_t unit_window(const float* img, float* out, float4* sv, int H, int W, cudaStream_t s) {
+    const size_t n = (size_t)H * W;
     if (!sv) return cudaMemcpyAsync(out, img, sizeof(float) * n, cudaMemcpyDeviceToDevice, s);
     const size_t want = (n + 255) / 256, cap = (size_t)8 * sm_count();
-    unit_window_quads<<<(unsigned)(want < cap ? want : cap), 256, 0, s>>>(img, out, sv, n);
+    unit_window_quads<<<(unsigned)(want < cap ? want : cap), 256, 0, s>>>(img, out, sv, H, W);
     return cudaGetLastError();
 }
 

@@ -6,6 +6,7 @@ import pytest
 import torch
 
 import oracle
+from _quads import rowmajor
 from paper_1107_4617_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -57,7 +58,7 @@ def test_poly_order_from_sigma(cuda_lib):
 
 
 @pytest.mark.parametrize("H,W,r,N,T", [(60, 80, 3, 3, 1.0), (70, 90, 5, 6, 1.0), (50, 140, 4, 8, 1.0),
-                                       (64, 64, 6, 5, 2.0)])
+                                       (64, 64, 6, 5, 2.0), (150, 170, 5, 6, 1.0)])
 def test_poly_adjoint_vs_central_differences(cuda_lib, H, W, r, N, T):
     """dL/df of the p_N filter through the autograd wrapper against FP64
     central differences of the oracle at sampled pixels (within 1e-3)."""
@@ -89,17 +90,17 @@ def test_poly_adjoint_vs_central_differences(cuda_lib, H, W, r, N, T):
 
 def test_unit_window_closed_form(cuda_lib):
     """r = 0 (a 1 x 1 window): out = f, saved quads (f, 1, f, 0), dL/df = dL/dout,
-    on an image wider than one strip."""
+    on an image wider than one strip and taller than 128 rows (sheared quads)."""
     bf = cuda_lib
-    f = synth.sinusoids(70, 300, seed=11)
+    f = synth.sinusoids(140, 300, seed=11)
     ft = torch.from_numpy(f).cuda()
-    sv = torch.empty((70, 300, 4), device="cuda")
+    sv = torch.empty((140, 300, 4), device="cuda")
     out = bf.bf_poly_forward(ft, 0, 0.0, 1.0, 6, saved=sv)
-    g = torch.from_numpy(synth.weights((70, 300), seed=2)).cuda()
+    g = torch.from_numpy(synth.weights((140, 300), seed=2)).cuda()
     gi = bf.bf_poly_backward(g, sv, 0, 0.0, 1.0, 6)
     torch.cuda.synchronize()
     assert np.array_equal(out.cpu().numpy(), f)
-    assert np.array_equal(sv.cpu().numpy(), np.stack([f, np.ones_like(f), f, np.zeros_like(f)], -1))
+    assert np.array_equal(rowmajor(sv), np.stack([f, np.ones_like(f), f, np.zeros_like(f)], -1))
     assert torch.equal(gi, g)
 
 

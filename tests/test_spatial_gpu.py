@@ -9,6 +9,7 @@ import pytest
 import torch
 
 import oracle
+from _quads import rowmajor
 from paper_1107_4617_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -75,21 +76,22 @@ def test_edges_and_ragged_tiles(cuda_lib, H, W, r):
 def test_short_phase_period(cuda_lib, M, N, r):
     """Small windows, whose phase period 2 (2r + 1) can be shorter than the
     spatial harmonic b. r = 0: a 1 x 1 window weighs the centre alone, so out =
-    f, the saved quad is (f, 1, f, 0) and the adjoint returns dL/dout."""
+    f, the saved quad is (f, 1, f, 0) and the adjoint returns dL/dout. 130
+    rows, so the saved quads are sheared."""
     bf = cuda_lib
-    f = synth.sinusoids(70, 300, seed=M + r)
+    f = synth.sinusoids(130, 300, seed=M + r)
     ft = torch.from_numpy(f).cuda()
-    sv = torch.empty((70, 300, 4), device="cuda")
+    sv = torch.empty((130, 300, 4), device="cuda")
     got = bf.bf_spatial_forward(ft, r, M, 0.0, 1.0, N, saved=sv)
     torch.cuda.synchronize()
     want = ref(f, r, M, N)
     assert rel_err(got.cpu().numpy(), want).max() <= TOL
-    s = sv.cpu().numpy()
+    s = rowmajor(sv)
     assert np.array_equal(s[..., 0], f) and np.allclose(s[..., 2], got.cpu().numpy())
     if r == 0:
         assert np.array_equal(got.cpu().numpy(), f)
         assert np.array_equal(s, np.stack([f, np.ones_like(f), f, np.zeros_like(f)], -1))
-        g = torch.from_numpy(synth.weights((70, 300), seed=3)).cuda()
+        g = torch.from_numpy(synth.weights((130, 300), seed=3)).cuda()
         gi = bf.bf_spatial_backward(g, sv, r, M, 0.0, 1.0, N)
         torch.cuda.synchronize()
         assert torch.equal(gi, g)
@@ -122,7 +124,7 @@ def fd_grad(f, w, r, M, N, y, x, h=1e-4):
 
 
 @pytest.mark.parametrize("H,W,r,M,N", [(64, 90, 3, 2, 4), (80, 70, 5, 1, 3), (50, 140, 4, 2, 0),
-                                       (33, 41, 2, 4, 0), (96, 200, 5, 2, 2)])
+                                       (33, 41, 2, 4, 0), (96, 200, 5, 2, 2), (150, 170, 4, 2, 4)])
 def test_spatial_adjoint_vs_central_differences(cuda_lib, H, W, r, M, N):
     """dL/df of Algorithm 2 with the spatial kernel (and of Algorithm 1 for
     N = 0), through the autograd wrapper, against FP64 central differences
@@ -145,12 +147,13 @@ def test_spatial_adjoint_vs_central_differences(cuda_lib, H, W, r, M, N):
 
 def test_spatial_saved_quads(cuda_lib):
     """The forward's saved quads: f and out exactly as read and written, 1/den
-    equal to the oracle's normaliser's reciprocal."""
+    equal to the oracle's normaliser's reciprocal. 150 rows: pixel (y, x)'s
+    quad sits at ((y + (x mod 128)) mod H) W + x."""
     bf = cuda_lib
-    f = synth.rectangles(70, 90, seed=4)
-    sv = torch.empty((70, 90, 4), device="cuda")
+    f = synth.rectangles(150, 90, seed=4)
+    sv = torch.empty((150, 90, 4), device="cuda")
     out = bf.bf_spatial_forward(torch.from_numpy(f).cuda(), 3, 2, 0.0, 1.0, 4, saved=sv)
-    q = sv.cpu().numpy()
+    q = rowmajor(sv)
     got = out.cpu().numpy()
     r_, den = oracle.bilateral_general(f.astype(np.float64), 3, spatial=oracle.SPATIAL_QM, M=2,
                                        range_kind=oracle.RANGE_COSN, gamma=G1, N=4,
