@@ -693,8 +693,8 @@ def main():
                     help="with --kernels-only: time N = ORDER instead of the headline's "
                          "N = 41 (profiler captures of the even-order kernels)")
     ap.add_argument("--profile-workload", default=None,
-                    choices=["spatial_M2_N4", "spatial_M2_N4_fb", "alg1_M2", "poly_N6",
-                             "trunc_1e-3"],
+                    choices=["spatial_M2_N4", "spatial_M2_N4_fb", "alg1_M2", "alg1_M2_fb",
+                             "poly_N6", "poly_N6_fb", "trunc_1e-3"],
                     help="launch only this 4096^2 r=10 workload's kernel, warmup + steps "
                          "times (profiler captures of the extra workloads)")
     ap.add_argument("--bands", action="store_true",
@@ -754,8 +754,16 @@ def main():
                 bf.bf_spatial_backward(g, saved, R, 2, 0.0, 1.0, 4, grad_img=gimg, stream=stream)
         elif pw == "alg1_M2":
             call = lambda: bf.bf_spatial_forward(img, R, 2, 0.0, 1.0, 0, out=out, stream=stream)
+        elif pw == "alg1_M2_fb":
+            def call():
+                bf.bf_spatial_forward(img, R, 2, 0.0, 1.0, 0, out=out, saved=saved, stream=stream)
+                bf.bf_spatial_backward(g, saved, R, 2, 0.0, 1.0, 0, grad_img=gimg, stream=stream)
         elif pw == "poly_N6":
             call = lambda: bf.bf_poly_forward(img, R, 0.0, 1.0, 6, out=out, stream=stream)
+        elif pw == "poly_N6_fb":
+            def call():
+                bf.bf_poly_forward(img, R, 0.0, 1.0, 6, out=out, saved=saved, stream=stream)
+                bf.bf_poly_backward(g, saved, R, 0.0, 1.0, 6, grad_img=gimg, stream=stream)
         else:
             to = bf._opts(save=True, trunc_tol=1e-3)
             call = lambda: bf.bf_forward(img, R, SIGMA, T_RANGE, N, out=out, opts=to, saved=saved,
