@@ -8,9 +8,8 @@
 namespace bf {
 
 // Rows per band so that a grid of gx strips is one wave of the CTAs of `kern`
-// (threads per CTA, dynamic shared bytes) resident per SM, at most max_per_sm
-// of them (0: no cap); at least 32 rows.
-int wave_band_rows(const void* kern, int threads, size_t smem, int H, int gx, int max_per_sm);
+// (threads per CTA, dynamic shared bytes) resident per SM; at least 32 rows.
+int wave_band_rows(const void* kern, int threads, size_t smem, int H, int gx);
 
 // r = 0 (a 1 x 1 window) for the variant filters, whose kernels are 1 with
 // slope 0 at the origin: out = img (H x W FP32 values) and, if sv is given,

@@ -257,9 +257,9 @@ static cudaError_t launch(const Params& p, int mode, int gx, int gy, cudaStream_
                                          (int)smem);
     if (e != cudaSuccess) return e;
     Params q = p;
-    // the adjoint (five saved quads per step) runs best at two CTAs per SM
-    if (q.Hb <= 0)
-        q.Hb = wave_band_rows((const void*)kern, WMAX, smem, q.H, gx, mode == ADJ ? 2 : 0);
+    // one wave of as many CTAs as fit per SM (the adjoint's sheared quad loads
+    // coalesce, so it no longer gains from fewer resident CTAs)
+    if (q.Hb <= 0) q.Hb = wave_band_rows((const void*)kern, WMAX, smem, q.H, gx);
     gy = (q.H + q.Hb - 1) / q.Hb;
     kern<<<dim3(gx, gy), WMAX, smem, s>>>(q);
     return cudaGetLastError();

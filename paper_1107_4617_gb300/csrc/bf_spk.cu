@@ -814,15 +814,15 @@ constexpr bool use_combo_sum() {
 }
 
 template <typename K>
-static cudaError_t launch_one(K kern, size_t smem, const Params& p, int gx, bool adj,
-                              cudaStream_t s) {
+static cudaError_t launch_one(K kern, size_t smem, const Params& p, int gx, cudaStream_t s) {
     if (p.r < 1) return cudaErrorInvalidValue;  // r = 0 has its closed form
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
     Params q = p;
-    // the adjoint (five saved quads per step) runs best at two CTAs per SM
-    if (q.Hb <= 0) q.Hb = wave_band_rows((const void*)kern, WMAX, smem, q.H, gx, adj ? 2 : 0);
+    // one wave of as many CTAs as fit per SM (the adjoint's sheared quad loads
+    // coalesce, so it no longer gains from fewer resident CTAs)
+    if (q.Hb <= 0) q.Hb = wave_band_rows((const void*)kern, WMAX, smem, q.H, gx);
     const int gy = (q.H + q.Hb - 1) / q.Hb;
     kern<<<dim3(gx, gy), WMAX, smem, s>>>(q);
     return cudaGetLastError();
@@ -846,18 +846,17 @@ static cudaError_t launch(const Params& p, int mode, int gx, int gy, cudaStream_
         if (mode == FWD || mode == FWD_SAVE) {
             const size_t smem = sizeof(float4) * 2 * (size_t)D::NS * (WMAX + 1) + tab;
             return mode == FWD_SAVE
-                       ? launch_one(spk_kernel<M, N, FWD_SAVE>, smem, p, gx, false, s)
-                       : launch_one(spk_kernel<M, N, FWD>, smem, p, gx, false, s);
+                       ? launch_one(spk_kernel<M, N, FWD_SAVE>, smem, p, gx, s)
+                       : launch_one(spk_kernel<M, N, FWD>, smem, p, gx, s);
         }
         constexpr int H = adjoint_split<M, N>();
         cudaError_t e = launch_one(spk_kernel<M, N, ADJ, 0, H>,
-                                   sizeof(float4) * 2 * (size_t)H * (WMAX + 1) + tab, p, gx, true,
-                                   s);
+                                   sizeof(float4) * 2 * (size_t)H * (WMAX + 1) + tab, p, gx, s);
         if constexpr (H < D::NS) {
             if (e == cudaSuccess)
                 e = launch_one(spk_kernel<M, N, ADJ, H, D::NS>,
                                sizeof(float4) * 2 * (size_t)(D::NS - H) * (WMAX + 1) + tab, p, gx,
-                               true, s);
+                               s);
         }
         return e;
     } else {
@@ -866,7 +865,7 @@ static cudaError_t launch(const Params& p, int mode, int gx, int gy, cudaStream_
         auto kern = mode == ADJ ? spk_plane_kernel<M, N, ADJ>
                                 : (mode == FWD_SAVE ? spk_plane_kernel<M, N, FWD_SAVE>
                                                     : spk_plane_kernel<M, N, FWD>);
-        return launch_one(kern, smem, p, gx, mode == ADJ, s);
+        return launch_one(kern, smem, p, gx, s);
     }
 }
 

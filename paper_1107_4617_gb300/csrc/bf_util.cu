@@ -91,12 +91,11 @@ cudaError_t unit_window(const float* img, float* out, float4* sv, int H, int W, 
     return cudaGetLastError();
 }
 
-int wave_band_rows(const void* kern, int threads, size_t smem, int H, int gx, int max_per_sm) {
+int wave_band_rows(const void* kern, int threads, size_t smem, int H, int gx) {
     int occ = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem) != cudaSuccess ||
         occ < 1)
         occ = 1;
-    if (max_per_sm > 0 && occ > max_per_sm) occ = max_per_sm;
     int nb = occ * sm_count() / (gx > 0 ? gx : 1);  // rounding up would start a second wave
     if (nb < 1) nb = 1;
     int hb = (H + nb - 1) / nb;
