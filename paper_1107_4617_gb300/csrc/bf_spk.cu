@@ -482,8 +482,9 @@ __global__ void __launch_bounds__(WMAX, 2) spk_kernel(Params p) {
                     p.out[o] = ov;
                     if constexpr (MODE == FWD_SAVE) {
                         const float dn = DN.x + DN.y, dd = DD.x + DD.y;
-                        p.sv[quad_index(rho, co, p.H, W)] =
-                            make_float4(fc, 1.0f / den, ov, fmaf(-ov, dd, dn));
+                        // streaming store: the adjoint reads the quads after the whole forward
+                        __stcs(p.sv + quad_index(rho, co, p.H, W),
+                            make_float4(fc, 1.0f / den, ov, fmaf(-ov, dd, dn)));
                     }
                 }
             }
@@ -794,8 +795,9 @@ __global__ void __launch_bounds__(WMAX, 2) spk_plane_kernel(Params p) {
                     const float ov = num / den;
                     p.out[o] = ov;
                     if constexpr (MODE == FWD_SAVE)
-                        p.sv[quad_index(rho, co, p.H, W)] =
-                            make_float4(fc, 1.0f / den, ov, fmaf(-ov, dd, dn));
+                        // streaming store: the adjoint reads the quads after the whole forward
+                        __stcs(p.sv + quad_index(rho, co, p.H, W),
+                            make_float4(fc, 1.0f / den, ov, fmaf(-ov, dd, dn)));
                 }
             }
         }
