@@ -25,6 +25,11 @@
 namespace bf {
 namespace poly {
 
+// L2 prefetch of one line (no registers held, nothing returned)
+__device__ __forceinline__ void prefetch_l2(const void* ptr) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(ptr));
+}
+
 constexpr int WMAX = 128;
 constexpr int NMAX = 8;
 constexpr int PCAP = 2 * NMAX + 1;  // psi_m, m = 0..2N
@@ -153,6 +158,19 @@ __global__ void __launch_bounds__(WMAX, 2) poly_kernel(Params p) {
             for (int k = 0; k < 5; ++k) { q[k] = nq[k]; gq[k] = MODE == ADJ ? ng[k] : 0.f; }
             const float fc = q[4].x;
             load_step(t + 1);
+            // pull the entering row of the step 8 ahead into L2 (inside the
+            // band's rows only); the other four streams re-read recent rows
+            {
+                const int ef = e + 8;
+                if (own_in && ef >= 0 && ef < p.H && ef < y0 - r + span) {
+                    if constexpr (MODE == ADJ) {
+                        prefetch_l2(p.bsv + quad_index(ef, cw, p.H, W));
+                        prefetch_l2(p.gout + (size_t)ef * W + cw);
+                    } else {
+                        prefetch_l2(p.img + (size_t)ef * W + cw);
+                    }
+                }
+            }
             // + own enter, - second enter, - own leave, + second leave
             auto accumulate = [&](int k, float wgt) {
                 const float u = fmaf(q[k].x, p.invT, -0.5f);
