@@ -256,7 +256,7 @@ __global__ void __launch_bounds__(WMAX, 2) poly_kernel(Params p) {
                         const float dn = DN.x + DN.y, dd = DD.x + DD.y;
                         // streaming store: the adjoint reads the quads after the whole forward
                         __stcs(p.sv + quad_index(rho, co, p.H, W),
-                            make_float4(fc, 1.0f / den, ov, fmaf(-ov * p.invT, dd, dn)));
+                               make_float4(fc, 1.0f / den, ov, fmaf(-ov * p.invT, dd, dn)));
                     }
                 }
             }

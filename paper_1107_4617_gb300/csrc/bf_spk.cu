@@ -484,7 +484,7 @@ __global__ void __launch_bounds__(WMAX, 2) spk_kernel(Params p) {
                         const float dn = DN.x + DN.y, dd = DD.x + DD.y;
                         // streaming store: the adjoint reads the quads after the whole forward
                         __stcs(p.sv + quad_index(rho, co, p.H, W),
-                            make_float4(fc, 1.0f / den, ov, fmaf(-ov, dd, dn)));
+                               make_float4(fc, 1.0f / den, ov, fmaf(-ov, dd, dn)));
                     }
                 }
             }
@@ -794,10 +794,11 @@ __global__ void __launch_bounds__(WMAX, 2) spk_plane_kernel(Params p) {
                 } else {
                     const float ov = num / den;
                     p.out[o] = ov;
-                    if constexpr (MODE == FWD_SAVE)
+                    if constexpr (MODE == FWD_SAVE) {
                         // streaming store: the adjoint reads the quads after the whole forward
                         __stcs(p.sv + quad_index(rho, co, p.H, W),
-                            make_float4(fc, 1.0f / den, ov, fmaf(-ov, dd, dn)));
+                               make_float4(fc, 1.0f / den, ov, fmaf(-ov, dd, dn)));
+                    }
                 }
             }
         }
