@@ -160,6 +160,11 @@ double bf_gamma(float sigma_r, float T, int N, int gamma_mode);
    The buffer must be 16-byte aligned. */
 size_t bf_saved_bytes(int H, int W);
 
+/* Index, in quads, of pixel (y, x)'s quad in the saved buffer of an H x W
+   image (the layout above; add b * H * W for image b of a 3-D call). Host
+   only; (size_t)-1 when H or W < 1 or (y, x) lies outside the image. */
+size_t bf_saved_index(int y, int x, int H, int W);
+
 /*
  * Forward filter (Algorithm 2 with M = 1, box window, range kernel q_N).
  *   img     device, H x W, dtype opts->in_dtype (FP32 or BF16).
@@ -294,7 +299,8 @@ bf_status bf_backward_noalloc(const void* img, const float* out, const float* gr
  *             not shifted by T/2, in the sheared layout of bf_forward's, for
  *             bf_spatial_backward.
  * r = 0 (a 1 x 1 window) is exact: out = img, saved quads (f, 1, f, 0).
- * Errors: BF_ERR_INVALID_ARG, BF_ERR_UNSUPPORTED (other M, N, r), BF_ERR_CUDA.
+ * Errors: BF_ERR_INVALID_ARG, BF_ERR_UNSUPPORTED (other M, N, r; H * W >= 2^31,
+ * checked first), BF_ERR_CUDA.
  */
 bf_status bf_spatial_forward(const void* img, int H, int W, int r, int M, float sigma_r, float T,
                              int N, float* out, const bf_opts* opts, void* saved, void* stream);
@@ -341,8 +347,8 @@ int bf_poly_resolve_N(float sigma_r, float T);
  *             bf_poly_backward.
  * r = 0 (a 1 x 1 window) is exact: out = img, saved quads (f, 1, f, 0), and
  * bf_poly_backward returns grad_out.
- * Errors: BF_ERR_INVALID_ARG, BF_ERR_UNSUPPORTED (N > 8, r > 56),
- * BF_ERR_CUDA.
+ * Errors: BF_ERR_INVALID_ARG, BF_ERR_UNSUPPORTED (N > 8, r > 56; H * W >=
+ * 2^31, checked first), BF_ERR_CUDA.
  */
 bf_status bf_poly_forward(const void* img, int H, int W, int r, float sigma_r, float T, int N,
                           float* out, const bf_opts* opts, void* saved, void* stream);

@@ -21,7 +21,7 @@ __all__ = [
     "BfError", "BfOpts", "BfDesc", "load", "lib_path",
     "bf_forward", "bf_backward", "bf_forward3d", "bf_backward3d", "bf_batch", "bf_batch_prepare",
     "bf_batch_launch", "bf_backward3d_workspace_bytes",
-    "bf_resolve_N", "bf_coeffs", "bf_trunc_harmonics", "bf_gamma", "bf_saved_bytes", "bf_backward_workspace_bytes",
+    "bf_resolve_N", "bf_coeffs", "bf_trunc_harmonics", "bf_gamma", "bf_saved_bytes", "bf_saved_index", "bf_backward_workspace_bytes",
     "bf_batch_workspace_bytes", "bf_status_string", "bf_last_cuda_error", "bilateral",
     "bf_spatial_forward", "bf_spatial_backward", "bilateral_spatial", "bf_poly_forward", "bf_poly_backward", "bilateral_poly", "bf_poly_resolve_N", "bf_check_range",
     "GAMMA_FIXED", "GAMMA_FROM_SIGMA", "F32", "BF16", "N_MAX", "R_MAX",
@@ -90,6 +90,7 @@ def load():
             "bf_trunc_harmonics": (c_int, [c_int, c_int, c_float]),
             "bf_gamma": (ctypes.c_double, [c_float, c_float, c_int, c_int]),
             "bf_saved_bytes": (c_size, [c_int, c_int]),
+            "bf_saved_index": (c_size, [c_int, c_int, c_int, c_int]),
             "bf_forward": (c_int, [vp, c_int, c_int, c_int, c_float, c_float, c_int, vp, P_opts,
                                    vp, vp]),
             "bf_backward_workspace_bytes": (c_size, [c_int, c_int, c_int, c_float, c_float, c_int,
@@ -255,6 +256,12 @@ def bf_gamma(sigma_r: float, T: float, N: int, gamma_mode: int = GAMMA_FIXED) ->
 
 def bf_saved_bytes(H: int, W: int) -> int:
     return int(load().bf_saved_bytes(int(H), int(W)))
+
+
+def bf_saved_index(y: int, x: int, H: int, W: int) -> int:
+    """Index, in quads, of pixel (y, x)'s quad in a saved buffer; -1 outside the image."""
+    i = int(load().bf_saved_index(int(y), int(x), int(H), int(W)))
+    return -1 if i == ctypes.c_size_t(-1).value else i
 
 
 def bf_backward_workspace_bytes(H: int, W: int, r: int, sigma_r: float = 0.2, T: float = 1.0,

@@ -26,6 +26,7 @@
 // vertical-walker / horizontal-window tile organisation as the forward
 // kernel; it is never stored.
 #include "bf_internal.cuh"
+#include "bf_quads.cuh"
 
 namespace bf {
 
@@ -78,13 +79,13 @@ __global__ void __launch_bounds__(256, 1) bf_bwd_strip_kernel(BwdParams p) {
         const bool ml = col_in && rho > y0 && l >= 0 && l < p.H;
         float fe = 0.f, ae = 0.f, be = 0.f, fl = 0.f, al = 0.f, bl = 0.f;
         if (me) {
-            const float4 sv = __ldg(p.sv + quad_index(e, c, p.H, p.W));
+            const float4 sv = __ldg(p.sv + quad_index64(e, c, p.H, p.W));
             fe = sv.x;
             ae = __ldg(p.gout + (size_t)e * p.ld + c) * sv.y;
             be = -ae * sv.z;
         }
         if (ml) {
-            const float4 sv = __ldg(p.sv + quad_index(l, c, p.H, p.W));
+            const float4 sv = __ldg(p.sv + quad_index64(l, c, p.H, p.W));
             fl = sv.x;
             al = __ldg(p.gout + (size_t)l * p.ld + c) * sv.y;
             bl = -al * sv.z;
@@ -109,7 +110,7 @@ __global__ void __launch_bounds__(256, 1) bf_bwd_strip_kernel(BwdParams p) {
             if (i < p.K) vrow[i * NT + j] = V[i];
         __syncthreads();
         if (is_out) {
-            const size_t o = quad_index(rho, c, p.H, p.W);  // saved quads (sheared)
+            const size_t o = quad_index64(rho, c, p.H, p.W);  // saved quads (sheared)
             const size_t op = (size_t)rho * p.ld + c;  // row-pitched (dL/dout, dL/dimg)
             const float4 svc = __ldg(p.sv + o);
             const float fc = svc.x;

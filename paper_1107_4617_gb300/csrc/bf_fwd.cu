@@ -20,6 +20,7 @@
 //  The window is truncated at the image border: pixels outside the image
 //  contribute zero planes (their rotation seed is zero).
 #include "bf_internal.cuh"
+#include "bf_quads.cuh"
 
 namespace bf {
 
@@ -144,7 +145,7 @@ __device__ __forceinline__ void fwd_tile(const FwdParams& p, int bx, int by, flo
                 dden += ak * (sc.zc * h.w - sc.zs * h.z);
                 rotate(sc.zc, sc.zs, sc.wc, sc.ws);
             }
-            const size_t o = quad_index(rho, c, p.H, p.W);  // saved quads (sheared)
+            const size_t o = quad_index64(rho, c, p.H, p.W);  // saved quads (sheared)
             const size_t op = (size_t)rho * p.ld + c;  // row-pitched (out, den)
             const float ov = num / den;
             p.out[op] = ov;

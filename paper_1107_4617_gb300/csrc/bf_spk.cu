@@ -1013,6 +1013,8 @@ extern "C" bf_status bf_spatial_forward(const void* img, int H, int W, int r, in
                                         float sigma_r, float T, int N, float* out,
                                         const bf_opts* opts, void* saved, void* stream) {
     BF_TRACE("bf_spatial_forward");
+    // the saved quads are indexed in 32 bits here (quad_index)
+    if ((long long)H * W >= 0x7fffffffLL) return BF_ERR_UNSUPPORTED;
     if (!img || !out) return BF_ERR_INVALID_ARG;
     if ((const void*)out == img) return BF_ERR_INVALID_ARG;
     if (saved && ((uintptr_t)saved & 15)) return BF_ERR_INVALID_ARG;
@@ -1043,6 +1045,8 @@ extern "C" bf_status bf_spatial_backward(const float* grad_out, const void* save
                                          int r, int M, float sigma_r, float T, int N,
                                          float* grad_img, const bf_opts* opts, void* stream) {
     BF_TRACE("bf_spatial_backward");
+    // the saved quads are indexed in 32 bits here (quad_index)
+    if ((long long)H * W >= 0x7fffffffLL) return BF_ERR_UNSUPPORTED;
     if (!grad_out || !saved || !grad_img) return BF_ERR_INVALID_ARG;
     if ((uintptr_t)saved & 15) return BF_ERR_INVALID_ARG;
     // neighbours' dL/dout and quads are read while dL/dimg is written

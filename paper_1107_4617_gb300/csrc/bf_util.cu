@@ -5,6 +5,7 @@
 #include <math.h>
 
 #include "bf_internal.cuh"
+#include "bf_quads.cuh"
 #include "bf_launch.cuh"
 #include "bf_trace.cuh"
 
@@ -71,7 +72,7 @@ __global__ void finish_kernel(int* keys) {
 
 }  // namespace util
 
-// out = f and the quads (f, 1, f, 0), pixel (y, x)'s at quad_index(y, x, H, W)
+// out = f and the quads (f, 1, f, 0), pixel (y, x)'s at quad_index64(y, x, H, W)
 __global__ void unit_window_quads(const float* img, float* out, float4* sv, int H, int W) {
     const size_t n = (size_t)H * W;
     const size_t stride = (size_t)gridDim.x * blockDim.x;
@@ -79,7 +80,7 @@ __global__ void unit_window_quads(const float* img, float* out, float4* sv, int 
         const float f = img[i];
         const int y = (int)(i / (size_t)W), x = (int)(i - (size_t)y * W);
         out[i] = f;
-        sv[quad_index(y, x, H, W)] = make_float4(f, 1.f, f, 0.f);
+        sv[quad_index64(y, x, H, W)] = make_float4(f, 1.f, f, 0.f);
     }
 }
 
@@ -105,6 +106,11 @@ int wave_band_rows(const void* kern, int threads, size_t smem, int H, int gx) {
 }  // namespace bf
 
 using namespace bf;
+
+extern "C" size_t bf_saved_index(int y, int x, int H, int W) {
+    if (H < 1 || W < 1 || y < 0 || y >= H || x < 0 || x >= W) return (size_t)-1;
+    return quad_index64(y, x, H, W);
+}
 
 extern "C" bf_status bf_check_range(const void* img, int H, int W, int in_dtype, float* minmax,
                                     void* stream) {

@@ -96,6 +96,67 @@ def test_sizes():
     assert bf.bf_saved_bytes(0, 5) == 0
 
 
+def _sheared(H, W):
+    """The saved-quad layout as include/bf.h states it, written out."""
+    ys, xs = np.meshgrid(np.arange(H, dtype=np.int64), np.arange(W, dtype=np.int64),
+                         indexing="ij")
+    if H >= 128:
+        return ((ys + (xs % 128)) % H) * W + xs
+    return ys * W + xs
+
+
+@pytest.mark.parametrize("H,W", [(1, 1), (5, 300), (127, 130), (128, 1), (128, 129), (200, 64),
+                                 (300, 257), (1000, 3)])
+def test_saved_index_is_the_documented_layout(H, W):
+    """bf_saved_index gives the header's formula at every pixel, and the map is
+    one-to-one onto [0, H W): every quad slot belongs to exactly one pixel."""
+    got = np.array([[bf.bf_saved_index(y, x, H, W) for x in range(W)] for y in range(H)],
+                   dtype=np.int64)
+    np.testing.assert_array_equal(got, _sheared(H, W))
+    assert np.array_equal(np.sort(got.ravel()), np.arange(H * W))
+
+
+def test_saved_index_past_2_31_pixels_and_bad_arguments():
+    H, W = 50000, 50000  # 2.5e9 pixels: the index needs 64 bits
+    for y, x in [(H - 1, W - 1), (H - 100, 127), (H - 100, 99), (0, W - 1), (H // 2, 12345)]:
+        want = ((y + (x % 128)) % H) * W + x
+        assert bf.bf_saved_index(y, x, H, W) == want
+    assert bf.bf_saved_index(H - 1, 0, H, W) == (H - 1) * W > 2 ** 31  # column 0: no shear
+    for args in [(-1, 0, 4, 4), (0, -1, 4, 4), (4, 0, 4, 4), (0, 4, 4, 4), (0, 0, 0, 4),
+                 (0, 0, 4, 0)]:
+        assert bf.bf_saved_index(*args) == -1
+
+
+def test_rowmajor_helper_inverts_the_library_layout():
+    """The GPU tests read saved quads through tests/_quads.rowmajor; placing each
+    pixel's coordinates at bf_saved_index and un-shearing returns them in place."""
+    from _quads import rowmajor
+    for H, W in [(70, 90), (150, 170), (300, 257)]:
+        sv = np.zeros((H * W, 4), np.float32)
+        for y in range(H):
+            for x in range(W):
+                sv[bf.bf_saved_index(y, x, H, W)] = (y, x, 1, 0)
+        back = rowmajor(sv.reshape(H, W, 4))
+        ys, xs = np.meshgrid(np.arange(H), np.arange(W), indexing="ij")
+        assert np.array_equal(back[..., 0], ys) and np.array_equal(back[..., 1], xs)
+
+
+def test_variants_reject_images_of_2_31_pixels_first():
+    """bf_spatial_* and bf_poly_* index their saved quads in 32 bits: an image of
+    2^31 or more pixels is BF_ERR_UNSUPPORTED (2), checked before any other
+    argument (the pointers here are null and never read)."""
+    lib = bf.load()
+    H = W = 46341  # 46341^2 > 2^31 - 1
+    assert lib.bf_spatial_forward(None, H, W, 1, 2, 0.0, 1.0, 4, None, None, None, None) == 2
+    assert lib.bf_spatial_backward(None, None, H, W, 1, 2, 0.0, 1.0, 4, None, None, None) == 2
+    assert lib.bf_poly_forward(None, H, W, 1, 0.0, 1.0, 3, None, None, None, None) == 2
+    assert lib.bf_poly_backward(None, None, H, W, 1, 0.0, 1.0, 3, None, None, None) == 2
+    # one pixel row fewer fits: the null pointers are then the error (1)
+    assert lib.bf_spatial_forward(None, 46340, 46340, 1, 2, 0.0, 1.0, 4, None, None, None,
+                                  None) == 1
+    assert lib.bf_poly_forward(None, 46340, 46340, 1, 0.0, 1.0, 3, None, None, None, None) == 1
+
+
 def test_argument_checks_return_before_any_launch():
     lib = bf.load()
     o = bf.BfOpts()
