@@ -8,6 +8,7 @@ limit of q_N (Eq. approx2). The gradient is pinned by central differences of
 the oracle's own forward and by the closed form of the linear N = 0 case.
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -426,3 +427,54 @@ def test_gauss_filter_brute_force():
                     eta += wgt
             ref[y, x] = num / eta
     np.testing.assert_allclose(oracle.bilateral_gauss(f, r, sig), ref, rtol=0, atol=1e-13)
+
+
+# ---- stored fixtures (tests/golden) ----------------------------------------
+
+_GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _golden(name):
+    return np.loadtxt(os.path.join(_GOLDEN, name), comments="#")
+
+
+def _golden_fp32(name):
+    """Stored FP32 values (9 significant digits round-trip through FP32 only)."""
+    return _golden(name).astype(np.float32).astype(np.float64)
+
+
+def _golden_header(name, key):
+    for line in open(os.path.join(_GOLDEN, name)):
+        if line.startswith("# " + key):
+            return float(line.split("=")[1])
+    raise KeyError(key)
+
+
+@pytest.mark.parametrize("r,N", [(2, 3), (1, 4), (3, 41), (2, 50)])
+def test_golden_outputs_reproduce(r, N):
+    """The oracle on the stored 24 x 20 image gives the stored outputs (written
+    by tests/golden/make_golden.py): a change to the oracle's arithmetic shows
+    here. The stored values also match the Python brute force of Eq. filter2."""
+    f = _golden_fp32("img_24x20.txt")
+    want = _golden("out_r%d_N%d.txt" % (r, N))
+    assert f.shape == want.shape == (24, 20)
+    np.testing.assert_allclose(oracle.bilateral(f, r, GAMMA1, N), want, rtol=1e-13, atol=1e-15)
+    np.testing.assert_allclose(brute_force(f, r, GAMMA1, N), want, rtol=1e-12, atol=1e-14)
+
+
+@pytest.mark.parametrize("r,N", [(2, 3), (3, 41)])
+def test_golden_gradients_reproduce(r, N):
+    """The oracle's direct-form dL/df and dL/dgamma on the stored image and
+    weights give the stored values; dL/dgamma also against FP64 central
+    differences of the brute force in gamma."""
+    f = _golden_fp32("img_24x20.txt")
+    g = _golden_fp32("weights_24x20.txt")
+    name = "grad_r%d_N%d.txt" % (r, N)
+    gf, gg = oracle.bilateral_grad(f, g, r, GAMMA1, N)
+    np.testing.assert_allclose(gf, _golden(name), rtol=1e-12, atol=1e-14)
+    want_gg = _golden_header(name, "dL/dgamma")
+    assert abs(gg - want_gg) <= 1e-12 * max(1.0, abs(want_gg))
+    h = 1e-6
+    fd = (np.sum(g * brute_force(f, r, GAMMA1 + h, N))
+          - np.sum(g * brute_force(f, r, GAMMA1 - h, N))) / (2 * h)
+    assert abs(fd - want_gg) <= 1e-6 * max(1.0, abs(want_gg)), (fd, want_gg)
